@@ -1,0 +1,368 @@
+"""Seeded synthetic inputs for the thermoelastic solve (meshes, fields, masks).
+
+This module builds *inputs* only: node coordinates, tetrahedral cells, per-cell
+material ids, nodal temperatures, nodal body forces and Dirichlet masks.  It
+holds none of the method's arithmetic (no element integrals, no near-nullspace,
+no solver), so both the CUDA path and the CPU oracle may consume what it makes.
+
+The paper's turbocharger and steam-turbine meshes are proprietary; these
+generators stand in for them with the same structure: multi-material bodies,
+a thermal-strain load, rotating bladed parts, P1 and P2 Lagrange tetrahedra
+and clamped boundaries (Sec. 4-5 of the paper).
+
+Conventions
+-----------
+* ``coords``: float64 ``[n_nodes, 3]``.
+* ``cells``: int32 ``[n_cells, 4]`` (P1) or ``[n_cells, 10]`` (P2).  P2 local
+  order: vertices 0-3, then mid-edge nodes of edges (01, 02, 03, 12, 13, 23).
+* All cells are positively oriented: det[x1-x0, x2-x0, x3-x0] > 0.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+P2_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+
+
+@dataclass
+class Problem:
+    """One thermoelastic load case on one mesh (all host arrays)."""
+
+    name: str
+    coords: np.ndarray            # [n,3] f64
+    cells: np.ndarray             # [m,4|10] i32
+    cell_material: np.ndarray     # [m] i32
+    mat_props: np.ndarray         # [n_mat,3] f64: E, nu, alpha
+    T: np.ndarray | None          # [n] f64 nodal temperature
+    T_ref: float
+    body_force: np.ndarray | None  # [n,3] f64 nodal body force density
+    dirichlet_mask: np.ndarray    # [n] u8
+    u_dirichlet: np.ndarray | None  # [n,3] f64
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.coords.shape[0])
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cells.shape[0])
+
+    @property
+    def n_dof(self) -> int:
+        return 3 * self.n_nodes
+
+    @property
+    def nodes_per_cell(self) -> int:
+        return int(self.cells.shape[1])
+
+
+# ----------------------------------------------------------------------------
+# Structured boxes split into Kuhn (Freudenthal) tetrahedra
+# ----------------------------------------------------------------------------
+
+def box_kuhn(nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 1.0,
+             lz: float = 1.0, origin=(0.0, 0.0, 0.0)):
+    """Box [0,lx]x[0,ly]x[0,lz] with nx*ny*nz hexes, each split into 6 tets.
+
+    Every hex is cut along its main diagonal into the 6 Kuhn tetrahedra (one
+    per permutation of the axes), which conform across neighbouring hexes.
+    Nodes are numbered lexicographically (x fastest), which keeps matrix
+    bandwidth small.  Returns (coords [n,3] f64, cells [6*nx*ny*nz, 4] i32).
+    """
+    xs = origin[0] + np.linspace(0.0, lx, nx + 1)
+    ys = origin[1] + np.linspace(0.0, ly, ny + 1)
+    zs = origin[2] + np.linspace(0.0, lz, nz + 1)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    coords = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float64)
+
+    sx, sy, sz = 1, nx + 1, (nx + 1) * (ny + 1)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    v0 = (i * sx + j * sy + k * sz).ravel().astype(np.int64)
+    step = (sx, sy, sz)
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        a, b, c = perm
+        p1 = v0 + step[a]
+        p2 = p1 + step[b]
+        p3 = p2 + step[c]
+        # sign of the permutation decides the orientation; swap to keep det > 0
+        inversions = sum(1 for s in range(3) for t in range(s + 1, 3) if perm[s] > perm[t])
+        if inversions % 2 == 0:
+            tets.append(np.stack([v0, p1, p2, p3], axis=1))
+        else:
+            tets.append(np.stack([v0, p1, p3, p2], axis=1))
+    # hex-major cell order (the 6 tets of one hex are adjacent in memory)
+    cells = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return coords, cells
+
+
+def jitter_interior(coords: np.ndarray, h: float, amount: float, seed: int,
+                    fixed_mask: np.ndarray | None = None) -> np.ndarray:
+    """Move interior nodes by a seeded uniform offset of at most amount*h per axis."""
+    rng = np.random.default_rng(seed)
+    lo, hi = coords.min(axis=0), coords.max(axis=0)
+    on_bnd = np.any(np.isclose(coords, lo) | np.isclose(coords, hi), axis=1)
+    if fixed_mask is not None:
+        on_bnd |= fixed_mask.astype(bool)
+    d = rng.uniform(-amount * h, amount * h, size=coords.shape)
+    out = coords.copy()
+    out[~on_bnd] += d[~on_bnd]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# P2 meshes: add one node at the midpoint of every edge
+# ----------------------------------------------------------------------------
+
+def p1_to_p2(coords: np.ndarray, cells: np.ndarray):
+    """Quadratic (10-node) tets from linear ones by adding mid-edge nodes.
+
+    Returns (coords2, cells2, n_vertices).  Edge nodes are numbered after the
+    vertex nodes in order of their (sorted) vertex pair.
+    """
+    n = coords.shape[0]
+    c = cells.astype(np.int64)
+    pairs = np.stack([np.stack([c[:, a], c[:, b]], axis=1) for a, b in P2_EDGES], axis=1)
+    pairs = np.sort(pairs, axis=2).reshape(-1, 2)
+    keys = pairs[:, 0] * n + pairs[:, 1]
+    uniq, inv = np.unique(keys, return_inverse=True)
+    ea, eb = uniq // n, uniq % n
+    mid = 0.5 * (coords[ea] + coords[eb])
+    coords2 = np.concatenate([coords, mid], axis=0)
+    edge_nodes = (n + inv).reshape(-1, 6)
+    cells2 = np.concatenate([c, edge_nodes], axis=1).astype(np.int32)
+    return coords2, cells2, n
+
+
+def renumber_nodes(coords: np.ndarray, cells: np.ndarray, order: np.ndarray):
+    """Apply a node permutation: new node k is old node order[k]."""
+    inv = np.empty_like(order)
+    inv[order] = np.arange(order.size, dtype=order.dtype)
+    return coords[order], inv[cells].astype(np.int32), inv
+
+
+def spatial_order(coords: np.ndarray, h: float) -> np.ndarray:
+    """Lexicographic (z, y, x) order on a lattice of spacing h/2.
+
+    Used to interleave P2 edge nodes with vertices so that a block row's
+    neighbours stay close in memory.
+    """
+    q = np.round((coords - coords.min(axis=0)) / (0.5 * h)).astype(np.int64)
+    return np.lexsort((q[:, 0], q[:, 1], q[:, 2]))
+
+
+# ----------------------------------------------------------------------------
+# Fields
+# ----------------------------------------------------------------------------
+
+def fourier_temperature(coords: np.ndarray, seed: int, n_modes: int = 8,
+                        scale=(4.0, 1.0, 1.0)) -> np.ndarray:
+    """Smooth random field: mean of n_modes cosines, so max |T| <= 1.
+
+    T(x) = (1/n_modes) * sum_m cos(pi * k_m . (x/scale) + phi_m), with integer
+    wave vectors k_m drawn from {0..3}^3 without the zero vector and phases
+    uniform on [0, 2pi), all from numpy default_rng(seed): first the n_modes
+    wave vectors (redrawing a zero vector), then the n_modes phases.
+    """
+    rng = np.random.default_rng(seed)
+    ks = []
+    while len(ks) < n_modes:
+        k = rng.integers(0, 4, size=3)
+        if np.any(k != 0):
+            ks.append(k)
+    phis = rng.uniform(0.0, 2.0 * np.pi, size=n_modes)
+    xt = coords / np.asarray(scale, dtype=np.float64)
+    T = np.zeros(coords.shape[0])
+    for k, ph in zip(ks, phis):
+        T += np.cos(np.pi * (xt @ k.astype(np.float64)) + ph)
+    return T / n_modes
+
+
+def cell_centroids(coords: np.ndarray, cells: np.ndarray) -> np.ndarray:
+    return coords[cells[:, :4]].mean(axis=1)
+
+
+# ----------------------------------------------------------------------------
+# The named workloads
+# ----------------------------------------------------------------------------
+
+def unit_cube_problem(n: int = 10, degree: int = 1) -> Problem:
+    """Unit cube, n^3 hexes -> 6 tets each; E=1, nu=0.3, alpha=1e-3.
+
+    T = sin(pi x) cos(pi y) (1 + z), T_ref = 0, clamped on x = 0, traction
+    free elsewhere, no body force.  n=10, degree=1 gives 6,000 tets, 1,331
+    nodes and 3,993 DOF.
+    """
+    coords, cells = box_kuhn(n, n, n)
+    if degree == 2:
+        coords, cells, _ = p1_to_p2(coords, cells)
+        coords, cells, _ = renumber_nodes(coords, cells, spatial_order(coords, 1.0 / n))
+    x, y, z = coords.T
+    T = np.sin(np.pi * x) * np.cos(np.pi * y) * (1.0 + z)
+    mask = (x <= 1e-12).astype(np.uint8)
+    return Problem(
+        name=f"cube{n}_p{degree}", coords=coords, cells=cells,
+        cell_material=np.zeros(cells.shape[0], np.int32),
+        mat_props=np.array([[1.0, 0.3, 1e-3]]), T=T, T_ref=0.0, body_force=None,
+        dirichlet_mask=mask, u_dirichlet=None,
+        meta={"hexes": (n, n, n), "degree": degree})
+
+
+def slab_box_problem(nx: int = 256, ny: int = 64, nz: int = 64, seed: int = 2024,
+                     degree: int = 1, slab_width: float = 0.5) -> Problem:
+    """Box [0,4]x[0,1]^2, two materials in alternating x-slabs, random T.
+
+    Slab index floor(x_c / slab_width) mod 2 of the cell centroid selects E=1
+    (even) or E=10 (odd); nu=0.3, alpha=1e-3 for both.  T is the seeded
+    8-mode Fourier field of amplitude 1 on x~=(x/4, y, z), T_ref = 0.
+    Clamped on x=0.  256x64x64 gives 6,291,456 tets, 1,085,825 nodes and
+    3,257,475 DOF.
+    """
+    coords, cells = box_kuhn(nx, ny, nz, 4.0, 1.0, 1.0)
+    if degree == 2:
+        coords, cells, _ = p1_to_p2(coords, cells)
+        coords, cells, _ = renumber_nodes(coords, cells,
+                                          spatial_order(coords, min(4.0 / nx, 1.0 / ny, 1.0 / nz)))
+    xc = cell_centroids(coords, cells)[:, 0]
+    mat = (np.floor(xc / slab_width).astype(np.int64) % 2).astype(np.int32)
+    T = fourier_temperature(coords, seed)
+    mask = (coords[:, 0] <= 1e-12).astype(np.uint8)
+    return Problem(
+        name=f"slabbox{nx}x{ny}x{nz}_p{degree}", coords=coords, cells=cells,
+        cell_material=mat, mat_props=np.array([[1.0, 0.3, 1e-3], [10.0, 0.3, 1e-3]]),
+        T=T, T_ref=0.0, body_force=None, dirichlet_mask=mask, u_dirichlet=None,
+        meta={"hexes": (nx, ny, nz), "degree": degree, "seed": seed})
+
+
+def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
+                        n_blades: int = 48, n_r_blade: int = 6, degree: int = 2,
+                        seed: int = 7, omega: float = 1.0, rho: float = 1.0,
+                        jitter: float = 0.15) -> Problem:
+    """Synthetic turbine disc: annulus r in [0.2, 1], thickness 0.1, plus blades.
+
+    A structured polar hex grid (n_r radial, n_blades*n_theta_per_blade
+    angular, n_z axial layers) covers the annulus.  Every blade pitch has 3 of
+    its n_theta_per_blade angular cells extruded radially from r=1 to r=1.3
+    with n_r_blade layers (straight-sided rectangular blades of width
+    3/8 of the pitch, about 0.05 at r=1 for 48 blades).  Hexes are split into
+    Kuhn tets, interior nodes jittered by up to jitter*h (seeded), then made
+    P2 if degree == 2.  T = 300 + 500 r^2 + 10 N(0,1) smoothed by one
+    neighbour average (seed), T_ref = 300.  Centrifugal body force
+    rho omega^2 (x, y, 0) about z.  Clamped at the bore r = 0.2.
+    Material: E=1, nu=0.3, alpha=1e-5.
+    """
+    n_t = n_blades * n_theta_per_blade
+    r_in, r_out, r_tip, thick = 0.2, 1.0, 1.3, 0.1
+    r_nodes = np.concatenate([np.linspace(r_in, r_out, n_r + 1),
+                              np.linspace(r_out, r_tip, n_r_blade + 1)[1:]])
+    n_rr = r_nodes.size
+    z_nodes = np.linspace(-0.5 * thick, 0.5 * thick, n_z + 1)
+    t_nodes = np.arange(n_t) * (2.0 * np.pi / n_t)
+    # node lattice (z, theta, r) -> id; theta periodic
+    idx = -np.ones((n_z + 1, n_t, n_rr), np.int64)
+    # which hexes exist: annulus all; blade layers only for blade columns
+    in_blade_col = (np.arange(n_t) % n_theta_per_blade) < 3
+    hex_exists = np.zeros((n_z, n_t, n_rr - 1), bool)
+    hex_exists[:, :, :n_r] = True
+    hex_exists[:, in_blade_col, n_r:] = True
+    node_used = np.zeros((n_z + 1, n_t, n_rr), bool)
+    for dz in (0, 1):
+        for dt in (0, 1):
+            for dr in (0, 1):
+                sl = hex_exists
+                zz, tt, rr = np.nonzero(sl)
+                node_used[zz + dz, (tt + dt) % n_t, rr + dr] = True
+    idx[node_used] = np.arange(node_used.sum())
+    zz, tt, rr = np.nonzero(node_used)
+    R = r_nodes[rr]
+    coords = np.stack([R * np.cos(t_nodes[tt]), R * np.sin(t_nodes[tt]), z_nodes[zz]], axis=1)
+    # hexes -> Kuhn tets in local (r, theta, z) lattice axes
+    hz, ht, hr = np.nonzero(hex_exists)
+
+    def corner(dr, dt, dz):
+        return idx[hz + dz, (ht + dt) % n_t, hr + dr]
+
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        off = [0, 0, 0]
+        verts = [corner(*off)]
+        for ax in perm:
+            off[ax] += 1
+            verts.append(corner(*off))
+        tets.append(np.stack(verts, axis=1))
+    cells = np.stack(tets, axis=1).reshape(-1, 4)
+    # orient positively
+    x = coords[cells]
+    det = np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), x[:, 3] - x[:, 0])
+    neg = det < 0
+    cells[neg] = cells[neg][:, [0, 1, 3, 2]]
+    # seeded jitter of interior nodes (not on the bore, rim faces or blade surfaces)
+    rng = np.random.default_rng(seed)
+    h = min(thick / n_z, (r_out - r_in) / n_r, 2 * np.pi * r_in / n_t)
+    cnt = np.zeros(coords.shape[0], np.int64)
+    np.add.at(cnt, cells.ravel(), 1)
+    # interior nodes of a Kuhn lattice touch 24 tets
+    interior = cnt == 24
+    d = rng.uniform(-jitter * h, jitter * h, size=coords.shape)
+    coords = coords.copy()
+    coords[interior] += d[interior]
+    cells = cells.astype(np.int32)
+    if degree == 2:
+        coords, cells, _ = p1_to_p2(coords, cells)
+    # locality: order by (theta sector, z, r)
+    th = np.mod(np.arctan2(coords[:, 1], coords[:, 0]), 2 * np.pi)
+    rad = np.hypot(coords[:, 0], coords[:, 1])
+    qt = np.floor(th / (2 * np.pi / n_t) * 2 + 0.25).astype(np.int64)
+    qr = np.round(rad / (0.5 * h)).astype(np.int64)
+    qz = np.round((coords[:, 2] + 0.5 * thick) / (0.25 * h)).astype(np.int64)
+    order = np.lexsort((qr, qz, qt))
+    coords, cells, _ = renumber_nodes(coords, cells, order)
+    rad = np.hypot(coords[:, 0], coords[:, 1])
+    # temperature: radial profile plus smoothed seeded noise
+    noise = np.random.default_rng(seed + 1).standard_normal(coords.shape[0]) * 10.0
+    sm = np.zeros_like(noise)
+    deg_ = np.zeros_like(noise)
+    cv = cells[:, :4]
+    for a in range(4):
+        for b in range(4):
+            np.add.at(sm, cv[:, a], noise[cv[:, b]])
+            np.add.at(deg_, cv[:, a], 1.0)
+    sm_full = noise.copy()
+    has = deg_ > 0
+    sm_full[has] = sm[has] / deg_[has]
+    T = 300.0 + 500.0 * rad ** 2 + sm_full
+    body = rho * omega ** 2 * np.stack([coords[:, 0], coords[:, 1], np.zeros(coords.shape[0])], axis=1)
+    mask = (rad <= r_in + 1e-9).astype(np.uint8)
+    return Problem(
+        name=f"disc{n_blades}b_p{degree}", coords=coords, cells=cells,
+        cell_material=np.zeros(cells.shape[0], np.int32),
+        mat_props=np.array([[1.0, 0.3, 1e-5]]), T=T, T_ref=300.0, body_force=body,
+        dirichlet_mask=mask, u_dirichlet=None,
+        meta={"n_r": n_r, "n_theta": n_t, "n_z": n_z, "degree": degree, "seed": seed,
+              "omega": omega})
+
+
+def mesh_quality(coords: np.ndarray, cells: np.ndarray):
+    """Minimum volume and minimum dihedral angle (degrees) over the vertex tets."""
+    x = coords[cells[:, :4]]
+    e1, e2, e3 = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]
+    vol = np.einsum("ij,ij->i", np.cross(e1, e2), e3) / 6.0
+    faces = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
+    normals = []
+    for f in faces:
+        p = x[:, list(f)]
+        nrm = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+        # point the normal outward (away from the opposite vertex)
+        opp = x[:, [k for k in range(4) if k not in f][0]]
+        s = np.sign(np.einsum("ij,ij->i", nrm, p[:, 0] - opp))
+        normals.append(nrm * s[:, None] / np.linalg.norm(nrm, axis=1)[:, None])
+    ang = []
+    for a in range(4):
+        for b in range(a + 1, 4):
+            c = -np.einsum("ij,ij->i", normals[a], normals[b])
+            ang.append(np.degrees(np.arccos(np.clip(c, -1, 1))))
+    return float(vol.min()), float(np.min(ang))
