@@ -1,0 +1,189 @@
+/*
+ * thermoamg.h -- C ABI of the GB300 (sm_103a) thermoelastic solver.
+ *
+ * The library solves the steady linear-elastic part of the paper's
+ * thermomechanical model (Sec. 3: Eqs. elasticity_bvp, u-dbc and the weak
+ * form wf_elastic with the thermal strain eps_T = alpha (T - T_ref) I) on
+ * P1/P2 Lagrange tetrahedra, by conjugate gradients (Sec. 2.1, "Iterative
+ * solvers") preconditioned with a smoothed-aggregation AMG V-cycle whose
+ * near-nullspace is the six rigid-body modes (Sec. 2.1, "Multigrid
+ * preconditioned iterative solvers"; Sec. 5.1, "Solver configuration":
+ * Chebyshev smoothing with estimated lambda_max, controlled coarsening and a
+ * direct coarsest-grid solve).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: TAM_OK (0) or a negative TAM_ERR_*
+ *    code.  tam_last_error() gives a message for the calling thread's last
+ *    failure.  No entry point aborts the process.
+ *  - Array arguments are DEVICE pointers unless the name ends in _host.  They
+ *    are owned by the caller and only read (const) or written in place.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls documented as "synchronising"
+ *    wait for it before returning.
+ *  - Node ids and cell ids are int32.  Vectors of displacement DOFs are
+ *    node-major: dof = 3*node + component.
+ *  - Handles (tam_matrix, tam_amg) own device memory allocated by the library
+ *    (stream-ordered from the device's default memory pool) and release it in
+ *    *_destroy.  A handle must be used from one host thread at a time.
+ */
+#ifndef THERMOAMG_H
+#define THERMOAMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TAM_OK = 0,
+  TAM_ERR_INVALID_ARG = -1,        /* bad pointer, size, index or parameter       */
+  TAM_ERR_CUDA = -2,               /* a CUDA runtime call failed                  */
+  TAM_ERR_OOM = -3,                /* device allocation failed                    */
+  TAM_ERR_DEGENERATE_CELL = -4,    /* a cell has non-positive or non-finite volume */
+  TAM_ERR_NOT_CONVERGED = -5,      /* max_iter reached before the tolerance        */
+  TAM_ERR_BREAKDOWN = -6,          /* CG: p^T K p <= 0                            */
+  TAM_ERR_INDEFINITE_PRECOND = -7, /* CG: r^T M^-1 r <= 0 (bad Chebyshev bounds)  */
+  TAM_ERR_NAN = -8,                /* NaN/Inf met in the solve                    */
+  TAM_ERR_INTERNAL = -9,           /* internal capacity/consistency check failed   */
+  TAM_ERR_UNSUPPORTED = -10        /* valid request this build does not support    */
+};
+
+typedef struct tam_matrix_s* tam_matrix; /* assembled 3x3-block sparse K (+ metadata) */
+typedef struct tam_amg_s* tam_amg;       /* SA-AMG hierarchy bound to one tam_matrix  */
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char* tam_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Assembly (Sec. 3, Eq. wf_elastic, steady, traction free; Eq. u-dbc).
+ *
+ * Builds the block-CSR pattern of K from the cell-node incidence, evaluates
+ * the element stiffness int C:eps(u):eps(v), the thermal load
+ * int C:eps_T(T_h):eps(v) and the body load int f_h.v on every cell
+ * (T_h, f_h: nodal interpolants in the same P1/P2 space), scatters them,
+ * then eliminates the Dirichlet nodes symmetrically: the load is lifted by
+ * -K_{:,D} u_D, rows and columns of Dirichlet nodes are zeroed, their
+ * diagonal block becomes I and their load entries u_D.
+ *
+ *  n_nodes, coords[n_nodes*3]      node coordinates (float64, xyz per node)
+ *  n_cells, nodes_per_cell          4 (P1) or 10 (P2; vertices 0-3 then the
+ *                                   mid-edge nodes of edges 01,02,03,12,13,23)
+ *  cells[n_cells*nodes_per_cell]    node ids (int32), positively oriented
+ *  cell_material[n_cells]           material id in [0, n_mat)
+ *  mat_props[n_mat*3]               E, nu, alpha per material (float64)
+ *  T[n_nodes] (may be NULL)         nodal temperature; NULL = T_ref everywhere
+ *  T_ref                            reference temperature
+ *  body_force[n_nodes*3] (NULL = 0) nodal body-force density
+ *  dirichlet_mask[n_nodes]          uint8, nonzero = all 3 components fixed
+ *  u_dirichlet[n_nodes*3] (NULL = 0) prescribed displacement on masked nodes
+ *  K_out                            receives the new matrix handle
+ *  rhs_out[n_nodes*3]               receives the load vector (written)
+ * Synchronising (the pattern size is read back).  Errors: INVALID_ARG for
+ * bad sizes/pointers, DEGENERATE_CELL if any cell volume is <= 0 or not
+ * finite (no handle is returned), OOM, CUDA.
+ */
+int fem_assemble_elasticity(int n_nodes, const double* coords, int n_cells, int nodes_per_cell,
+                            const int* cells, const int* cell_material, int n_mat,
+                            const double* mat_props, const double* T, double T_ref,
+                            const double* body_force, const unsigned char* dirichlet_mask,
+                            const double* u_dirichlet, tam_matrix* K_out, double* rhs_out,
+                            void* stream);
+
+/* Sizes of K: block rows (= n_nodes), stored 3x3 blocks, block size (3). */
+int tam_matrix_info(tam_matrix K, int* n_block_rows, long long* nnzb, int* block_size);
+
+/* Copies K in block-CSR form: row_ptr[n+1], col_idx[nnzb] (sorted per row),
+ * vals[nnzb*9] (row-major 3x3 blocks).  Device pointers; synchronising. */
+int tam_matrix_export_bsr(tam_matrix K, int* row_ptr, int* col_idx, double* vals, void* stream);
+
+/* y = K x (x, y: [3n] float64 device vectors, must not overlap). */
+int tam_matrix_spmv(tam_matrix K, const double* x, double* y, void* stream);
+
+/* Releases K (an AMG built on K must be destroyed first). */
+int tam_matrix_destroy(tam_matrix K);
+
+/* ------------------------------------------------------------------------
+ * Smoothed-aggregation AMG (Sec. 2.1 and Sec. 5.1).  The paper fixes the
+ * method (SA-AMG with the rigid-body near-nullspace, Chebyshev smoothing
+ * with estimated lambda_max, controllable coarsening, a larger coarsest grid
+ * for robustness) but not its constants; these are the knobs.
+ */
+typedef struct amg_params {
+  double strength_theta;   /* block (i,j) strong if |A_ij|_F >= theta sqrt(|A_ii|_F |A_jj|_F); default 0 */
+  int smoother_degree;     /* Chebyshev degree, pre and post; default 2                               */
+  double cheb_lo;          /* smoothing interval [cheb_lo, cheb_hi] * lambda_max(D^-1 A); 0.1       */
+  double cheb_hi;          /* 1.1                                                                    */
+  int eig_iters;           /* Lanczos steps for lambda_max(D^-1 A); default 10                        */
+  int coarse_max_dofs;     /* stop coarsening at or below this many DOFs; default 2000                */
+  int max_levels;          /* including the finest; default 10                                       */
+  int use_rotations;       /* 1: six rigid-body modes; 0: three translations only; default 1         */
+  int level_precision;     /* 0: FP64 hierarchy (the only value this build accepts)                   */
+} amg_params;
+
+/* Fills *p with the defaults above. */
+int amg_params_default(amg_params* p);
+
+/* Builds the hierarchy for K.  coords[n*3] (device) gives the rigid-body
+ * modes (translations and rotations about the node centroid; zero on
+ * Dirichlet nodes).  Per level: Lanczos estimate of lambda_max(D^-1 A),
+ * strength graph, aggregation (distance-2 maximal independent set by
+ * SplitMix64 priority), tentative prolongator by modified Gram-Schmidt,
+ * P = (I - 4/(3 lambda) D^-1 A) P_tent, R = P^T, A_c = R A P; the coarsest
+ * operator is inverted densely.  K must outlive the handle.  Synchronising.
+ * Errors: INVALID_ARG, OOM, CUDA, INTERNAL. */
+int amg_setup(tam_matrix K, const double* coords, const amg_params* params, tam_amg* amg_out,
+              void* stream);
+
+/* Level sizes: n_levels, and per level (arrays of length >= n_levels, host
+ * memory, each may be NULL): block rows, stored blocks, block size, the
+ * lambda_max estimate; op_complexity = sum nnz(A_l) / nnz(A_0) in scalars. */
+int amg_info(tam_amg amg, int* n_levels, long long* level_rows_host, long long* level_nnzb_host,
+             int* level_block_host, double* level_lambda_host, double* op_complexity);
+
+/* Aggregate id of every block row of `level` (-1 = not aggregated) into
+ * agg[n_rows] (device int32).  Synchronising. */
+int amg_level_aggregates(tam_amg amg, int level, int* agg, void* stream);
+
+/* Block-CSR export of one operator of `level`: which = 0 A_level, 1 P
+ * (prolongator to level+1), 2 R = P^T, 3 tentative prolongator.  Call first
+ * with row_ptr == NULL to get the sizes (host ints), then with device arrays
+ * row_ptr[n_rows+1], col_idx[nnzb], vals[nnzb*br*bc].  Synchronising. */
+int amg_level_export(tam_amg amg, int level, int which, int* n_rows, int* n_cols, int* br, int* bc,
+                     long long* nnzb, int* row_ptr, int* col_idx, double* vals, void* stream);
+
+/* z = M^-1 r: one V-cycle (the preconditioner), r and z [3n] device. */
+int amg_vcycle(tam_amg amg, const double* r, double* z, void* stream);
+
+/* Preconditioned CG on K x = b from the initial guess in x.  Stops when the
+ * recursively updated residual satisfies ||r||_2 <= max(rtol ||b||_2, atol)
+ * or after max_iter iterations.  iters_out and final_rel_resid_out (host,
+ * may be NULL) receive the iteration count and ||b - K x||_2 / ||b||_2
+ * (recomputed at the end).  Synchronising (once per check interval).
+ * Errors: NOT_CONVERGED (x holds the last iterate), BREAKDOWN,
+ * INDEFINITE_PRECOND, NAN, INVALID_ARG, CUDA. */
+int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double atol, int max_iter,
+                  int* iters_out, double* final_rel_resid_out, void* stream);
+
+/* Releases the hierarchy. */
+int amg_destroy(tam_amg amg);
+
+/* ------------------------------------------------------------------------
+ * One-call host-buffer path: copies the mesh and fields from host memory
+ * (pinned memory gives the fastest copies), assembles, builds the AMG, solves
+ * to rtol and copies the displacement back into u_host[n_nodes*3].  Same
+ * argument meaning as fem_assemble_elasticity / amg_pcg_solve; params may be
+ * NULL (defaults).  Synchronising; all device memory is released on return.
+ */
+int tam_solve_elasticity_host(int n_nodes, const double* coords_host, int n_cells,
+                              int nodes_per_cell, const int* cells_host,
+                              const int* cell_material_host, int n_mat,
+                              const double* mat_props_host, const double* T_host, double T_ref,
+                              const double* body_force_host,
+                              const unsigned char* dirichlet_mask_host,
+                              const double* u_dirichlet_host, const amg_params* params,
+                              double rtol, int max_iter, double* u_host, int* iters_out,
+                              double* final_rel_resid_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THERMOAMG_H */

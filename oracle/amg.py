@@ -12,8 +12,9 @@ readings taken here are:
   ||A_ij||_F >= theta sqrt(||A_ii||_F ||A_jj||_F); a node with no strong
   neighbour (e.g. a Dirichlet node) is isolated and joins no aggregate.
 * aggregation: roots form the distance-2 maximal independent set of the
-  strength graph chosen greedily by decreasing priority (SplitMix64 of
-  (level << 32 | node), ties by node id); a non-root joins the adjacent root
+  strength graph chosen greedily by decreasing priority (top 30 bits of
+  SplitMix64(level << 32 | node), ties broken by the larger node id); a
+  non-root joins the adjacent root
   of largest priority; a node left over joins the aggregate of its
   already-attached neighbour of largest priority.  Aggregates are numbered by
   increasing root id.
@@ -62,7 +63,8 @@ def splitmix64(x):
 
 
 def node_priority(n, level):
-    return splitmix64((U64(level) << U64(32)) | np.arange(n, dtype=U64))
+    """30-bit node priority: top 30 bits of SplitMix64(level << 32 | node)."""
+    return splitmix64((U64(level) << U64(32)) | np.arange(n, dtype=U64)) >> U64(34)
 
 
 def lanczos_start(n_dof, level):

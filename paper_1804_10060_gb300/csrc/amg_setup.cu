@@ -1,0 +1,769 @@
+// Smoothed-aggregation AMG setup (paper Sec. 2.1 "Multigrid preconditioned
+// iterative solvers" and Sec. 5.1 "Solver configuration").
+//
+// Per level: point-Jacobi diagonal, Lanczos estimate of lambda_max(D^-1 A)
+// (the paper stresses that Chebyshev smoothing needs an adequate estimate),
+// strength graph, aggregation by a distance-2 maximal independent set,
+// tentative prolongator by modified Gram-Schmidt of the near-nullspace (the
+// six rigid-body modes on the finest level), prolongator smoothing
+// P = (I - 4/(3 lambda) D^-1 A) P_tent, R = P^T and the Galerkin product
+// A_c = R A P.  The coarsest operator is inverted densely (Gauss-Jordan).
+#include <algorithm>
+#include <cmath>
+
+#include "handles.cuh"
+
+namespace tam {
+namespace {
+
+constexpr int TPB = 256;
+
+// ---------------------------------------------------------------------------
+// Diagonal, rigid-body modes
+// ---------------------------------------------------------------------------
+__global__ void point_dinv_kernel(const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const double* __restrict__ v, int n, int bs, double* __restrict__ dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int slot = bsearch_i32(ci, rp[i], rp[i + 1], i);
+  for (int r = 0; r < bs; ++r) {
+    double d = slot >= 0 ? v[(size_t)slot * bs * bs + r * bs + r] : 0.0;
+    dinv[(size_t)i * bs + r] = d != 0.0 ? 1.0 / d : 0.0;
+  }
+}
+
+__global__ void centroid_kernel(const double* __restrict__ X, int n, GridReduce gr, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double v[3] = {0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int d = 0; d < 3; ++d) v[d] += X[3 * (size_t)i + d];
+  double tot[3];
+  if (grid_reduce<3>(gr, v, tot, sh) && threadIdx.x == 0)
+    for (int d = 0; d < 3; ++d) out[d] = tot[d] / n;
+}
+
+// B[(3i + r) * k + col]: translations, then rotations about x, y, z through c.
+__global__ void rigid_modes_kernel(const double* __restrict__ X, const unsigned char* __restrict__ dmask, int n,
+                                   const double* __restrict__ c, int k, double* __restrict__ B) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double m[3][6] = {};
+  if (!dmask[i]) {
+    double dx = X[3 * (size_t)i] - c[0], dy = X[3 * (size_t)i + 1] - c[1], dz = X[3 * (size_t)i + 2] - c[2];
+    m[0][0] = m[1][1] = m[2][2] = 1.0;
+    m[1][3] = -dz; m[2][3] = dy;
+    m[0][4] = dz;  m[2][4] = -dx;
+    m[0][5] = -dy; m[1][5] = dx;
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < k; ++q) B[(3 * (size_t)i + r) * k + q] = m[r][q];
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos estimate of lambda_max(D^-1 A) on S = D^-1/2 A D^-1/2
+// ---------------------------------------------------------------------------
+struct LanczosWork {
+  double* v;      // current Lanczos vector
+  double* vp;     // previous
+  double* u;      // s .* v (SpMV input)
+  double* w;      // work
+  const double* s;  // D^-1/2
+  double* ab;     // alpha[0..k), beta[k..2k)
+  int* m;         // number of completed steps (breakdown stops early)
+  long long N;
+};
+
+__global__ void lanczos_init_kernel(const double* __restrict__ dinv, long long N, int level, double* __restrict__ s,
+                                    double* __restrict__ v, GridReduce gr, double* __restrict__ norm2) {
+  __shared__ double sh[32];
+  double acc[1] = {0.0};
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x) {
+    double di = dinv[k];
+    double sk = di > 0.0 ? sqrt(di) : 0.0;
+    s[k] = sk;
+    uint64_t z = splitmix64(((uint64_t)(level + 1) << 40) | (uint64_t)k);
+    double vk = sk > 0.0 ? (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5 : 0.0;
+    v[k] = vk;
+    acc[0] += vk * vk;
+  }
+  double tot[1];
+  if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) *norm2 = tot[0];
+}
+
+__global__ void lanczos_normalize_kernel(long long N, double* __restrict__ v, const double* __restrict__ s,
+                                         double* __restrict__ u, double* __restrict__ vp, const double* __restrict__ norm2) {
+  double inv = 1.0 / sqrt(*norm2);
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x) {
+    double vk = v[k] * inv;
+    v[k] = vk;
+    u[k] = s[k] * vk;
+    vp[k] = 0.0;
+  }
+}
+
+// SpMV epilogue: w = s .* (A u), alpha_j = w . v
+template <int BR>
+struct EpiLanczos {
+  double* w;
+  const double* s;
+  const double* v;
+  int n_rows;
+  GridReduce gr;
+  double* alpha_out;
+  const int* done;
+  __device__ bool skip() const { return *done; }
+  __device__ void operator()(int row, const double (&acc)[BR], double* sh) const {
+    double dot[1] = {0.0};
+    if (row < n_rows)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        size_t i = (size_t)row * BR + r;
+        double wi = s[i] * acc[r];
+        w[i] = wi;
+        dot[0] += wi * v[i];
+      }
+    double tot[1];
+    if (grid_reduce<1>(gr, dot, tot, sh) && threadIdx.x == 0) *alpha_out = tot[0];
+  }
+};
+
+__global__ void lanczos_orth_kernel(LanczosWork L, int j, GridReduce gr, const int* __restrict__ done) {
+  __shared__ double sh[32];
+  if (*done) return;
+  const double a = L.ab[j];
+  const int K = 0;  // unused
+  (void)K;
+  const double bprev = j > 0 ? L.ab[64 + j - 1] : 0.0;
+  double acc[1] = {0.0};
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += (long long)gridDim.x * blockDim.x) {
+    double wk = L.w[k] - a * L.v[k] - bprev * L.vp[k];
+    L.w[k] = wk;
+    acc[0] += wk * wk;
+  }
+  double tot[1];
+  if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) L.ab[64 + j] = sqrt(tot[0]);
+}
+
+__global__ void lanczos_advance_kernel(LanczosWork L, int j, int* __restrict__ done) {
+  if (*done) return;
+  const double a = L.ab[j], b = L.ab[64 + j];
+  if (!(b > 1e-14 * fabs(a))) {
+    // breakdown: the Krylov space is invariant; keep the j+1 steps done so far
+    if (blockIdx.x == 0 && threadIdx.x == 0) { *L.m = j + 1; }
+    return;
+  }
+  const double inv = 1.0 / b;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < L.N; k += (long long)gridDim.x * blockDim.x) {
+    double vn = L.w[k] * inv;
+    L.vp[k] = L.v[k];
+    L.v[k] = vn;
+    L.u[k] = L.s[k] * vn;
+  }
+}
+
+__global__ void lanczos_mark_done_kernel(const LanczosWork L, int j, int* __restrict__ done) {
+  // runs after advance: if breakdown was recorded at step j, stop the remaining steps
+  if (*L.m == j + 1) *done = 1;
+}
+
+// Largest eigenvalue of the symmetric tridiagonal (alpha, beta) of order m by
+// bisection with Sturm sequence counts; then Chebyshev/omega constants.
+__global__ void tridiag_lmax_kernel(const double* __restrict__ ab, const int* __restrict__ m_ptr, int kmax,
+                                    double cheb_lo, double cheb_hi, int degree, double* __restrict__ consts) {
+  int m = *m_ptr;
+  if (m <= 0 || m > kmax) m = kmax;
+  const double* a = ab;
+  const double* b = ab + 64;
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  // count of eigenvalues < x
+  auto count_below = [&](double x) {
+    int c = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+      double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+      q = a[i] - x - (i > 0 ? bb / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0.0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(fabs(hi), fabs(lo)); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= m) hi = mid; else lo = mid;
+  }
+  const double lam = 0.5 * (lo + hi);
+  consts[0] = lam;
+  consts[1] = 4.0 / (3.0 * lam);
+  const double l0 = cheb_lo * lam, l1 = cheb_hi * lam;
+  const double theta = 0.5 * (l1 + l0), delta = 0.5 * (l1 - l0), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  consts[2] = 0.0;
+  consts[3] = 1.0 / theta;
+  for (int i = 1; i < degree; ++i) {
+    double rn = 1.0 / (2.0 * sigma - rho);
+    consts[2 + 2 * i] = rn * rho;
+    consts[3 + 2 * i] = 2.0 * rn / delta;
+    rho = rn;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Strength graph and aggregation
+// ---------------------------------------------------------------------------
+__global__ void block_norms_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                                   int n, int bb, double* __restrict__ nrm, double* __restrict__ dnrm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double dn = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    double s = 0.0;
+    for (int e = 0; e < bb; ++e) {
+      double x = v[(size_t)p * bb + e];
+      s += x * x;
+    }
+    s = sqrt(s);
+    nrm[p] = s;
+    if (ci[p] == i) dn = s;
+  }
+  dnrm[i] = dn;
+}
+
+__global__ void strength_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ nrm,
+                                const double* __restrict__ dnrm, int n, double theta, unsigned char* __restrict__ strong,
+                                unsigned char* __restrict__ isolated) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cnt = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    bool st = (j != i) && nrm[p] > 0.0 && nrm[p] >= theta * sqrt(dnrm[i] * dnrm[j]);
+    strong[p] = st;
+    cnt += st;
+  }
+  isolated[i] = cnt == 0;
+}
+
+__device__ __forceinline__ unsigned long long prio30(int level, int i) {
+  return splitmix64(((uint64_t)(unsigned)level << 32) | (uint64_t)(unsigned)i) >> 34;
+}
+
+enum : unsigned char { ST_UND = 0, ST_ROOT = 1, ST_OUT = 2 };
+
+__device__ __forceinline__ unsigned long long mis_tuple(unsigned char st, int level, int i) {
+  if (st == ST_OUT) return 0ull;
+  unsigned long long s = st == ST_ROOT ? 2ull : 1ull;
+  return (s << 62) | (prio30(level, i) << 32) | (unsigned)i;
+}
+
+__global__ void mis_init_kernel(const unsigned char* __restrict__ isolated, int n, unsigned char* __restrict__ state) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) state[i] = isolated[i] ? ST_OUT : ST_UND;
+}
+
+__global__ void mis_round1_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
+                                  const unsigned char* __restrict__ state, int n, int level, unsigned long long* __restrict__ m1) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long m = mis_tuple(state[i], level, i);
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (strong[p]) {
+      int j = ci[p];
+      unsigned long long t = mis_tuple(state[j], level, j);
+      m = t > m ? t : m;
+    }
+  m1[i] = m;
+}
+
+__global__ void mis_round2_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
+                                  unsigned char* __restrict__ state, const unsigned long long* __restrict__ m1, int n,
+                                  int level, int* __restrict__ undecided) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] != ST_UND) return;
+  unsigned long long m = m1[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (strong[p]) {
+      unsigned long long t = m1[ci[p]];
+      m = t > m ? t : m;
+    }
+  const unsigned long long mine = mis_tuple(ST_UND, level, i);
+  if (m == mine) state[i] = ST_ROOT;
+  else if ((m >> 62) == 2ull) state[i] = ST_OUT;
+  else atomicAdd(undecided, 1);
+}
+
+__global__ void root_flag_kernel(const unsigned char* __restrict__ state, const unsigned char* __restrict__ isolated, int n,
+                                 int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = (state[i] == ST_ROOT && !isolated[i]) ? 1 : 0;
+}
+
+// phase 2: roots keep their id; others join the adjacent root of largest key
+__global__ void agg_phase2_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
+                                  const unsigned char* __restrict__ state, const unsigned char* __restrict__ isolated,
+                                  const int* __restrict__ root_id, int n, int level, int* __restrict__ agg2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (isolated[i]) { agg2[i] = -1; return; }
+  if (state[i] == ST_ROOT) { agg2[i] = root_id[i]; return; }
+  unsigned long long best = 0;
+  int bj = -1;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (strong[p] && state[j] == ST_ROOT) {
+      unsigned long long key = (prio30(level, j) << 32) | (unsigned)j;
+      if (bj < 0 || key > best) { best = key; bj = j; }
+    }
+  }
+  agg2[i] = bj >= 0 ? root_id[bj] : -1;
+}
+
+// phase 3: left-over nodes join the aggregate of the attached neighbour of largest key
+__global__ void agg_phase3_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
+                                  const unsigned char* __restrict__ isolated, const int* __restrict__ agg2, int n, int level,
+                                  int* __restrict__ agg3, int* __restrict__ fail) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = agg2[i];
+  if (a < 0 && !isolated[i]) {
+    unsigned long long best = 0;
+    int bj = -1;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      int j = ci[p];
+      if (strong[p] && agg2[j] >= 0) {
+        unsigned long long key = (prio30(level, j) << 32) | (unsigned)j;
+        if (bj < 0 || key > best) { best = key; bj = j; }
+      }
+    }
+    if (bj >= 0) a = agg2[bj];
+    else atomicExch(fail, 1);
+  }
+  agg3[i] = a;
+}
+
+// ---------------------------------------------------------------------------
+// Tentative prolongator
+// ---------------------------------------------------------------------------
+__global__ void has_agg_kernel(const int* __restrict__ agg, int n, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) cnt[i] = agg[i] >= 0 ? 1 : 0;
+}
+
+__global__ void ptent_pattern_kernel(const int* __restrict__ agg, const int* __restrict__ rp, int n, int* __restrict__ ci,
+                                     const double* __restrict__ B, int bs, int k, double* __restrict__ v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || agg[i] < 0) return;
+  int p = rp[i];
+  ci[p] = agg[i];
+  for (int r = 0; r < bs; ++r)
+    for (int q = 0; q < k; ++q) v[(size_t)p * bs * k + r * k + q] = B[((size_t)i * bs + r) * k + q];
+}
+
+__global__ void agg_count_kernel(const int* __restrict__ agg, int n, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && agg[i] >= 0) atomicAdd(&cnt[agg[i]], 1);
+}
+
+__global__ void agg_fill_kernel(const int* __restrict__ agg, int n, const int* __restrict__ ap, int* __restrict__ cursor,
+                                int* __restrict__ mem) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && agg[i] >= 0) mem[ap[agg[i]] + atomicAdd(&cursor[agg[i]], 1)] = i;
+}
+
+// warp per aggregate: members sorted by rank (node ids are unique)
+__global__ void agg_sort_kernel(const int* __restrict__ ap, int n_agg, const int* __restrict__ mem, int* __restrict__ out) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n_agg) return;
+  int s = ap[w], e = ap[w + 1];
+  for (int p = s + lane; p < e; p += 32) {
+    int key = mem[p], rank = 0;
+    for (int q = s; q < e; ++q) rank += mem[q] < key;
+    out[s + rank] = key;
+  }
+}
+
+// warp per aggregate: modified Gram-Schmidt in place on the P_tent blocks
+// (rows: member nodes in increasing id, bs rows each; columns: k modes).
+__global__ void ptent_qr_kernel(const int* __restrict__ ap, const int* __restrict__ mem, int n_agg,
+                                const int* __restrict__ prp, double* __restrict__ pv, int bs, int k, double droptol,
+                                double* __restrict__ Bc) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n_agg) return;
+  const int s = ap[w], e = ap[w + 1];
+  const int rows = (e - s) * bs;
+  double R[6][6];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) R[a][b] = 0.0;
+  auto elem = [&](int row, int col) -> double& {
+    int node = mem[s + row / bs];
+    return pv[(size_t)prp[node] * bs * k + (row % bs) * k + col];
+  };
+  for (int c = 0; c < k; ++c) {
+    double nn = 0.0;
+    for (int r = lane; r < rows; r += 32) { double x = elem(r, c); nn += x * x; }
+    const double norm0 = sqrt(warp_sum(nn));
+    for (int j = 0; j < c; ++j) {
+      double d = 0.0;
+      for (int r = lane; r < rows; r += 32) d += elem(r, j) * elem(r, c);
+      d = warp_sum(d);
+      R[j][c] = d;
+      for (int r = lane; r < rows; r += 32) elem(r, c) -= d * elem(r, j);
+      __syncwarp();
+    }
+    double n2 = 0.0;
+    for (int r = lane; r < rows; r += 32) { double x = elem(r, c); n2 += x * x; }
+    const double nv = sqrt(warp_sum(n2));
+    const bool keep = norm0 > 0.0 && nv > droptol * norm0;
+    R[c][c] = keep ? nv : 0.0;
+    const double inv = keep ? 1.0 / nv : 0.0;
+    for (int r = lane; r < rows; r += 32) elem(r, c) *= inv;
+    __syncwarp();
+  }
+  if (lane == 0)
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) Bc[((size_t)w * k + a) * k + b] = R[a][b];
+}
+
+// P = (I - omega D^-1 A) P_tent, in place on the values of A*P_tent
+__global__ void smooth_prolongator_kernel(const int* __restrict__ rp, const int* __restrict__ ci, double* __restrict__ v,
+                                          int n, int bs, int k, const double* __restrict__ dinv,
+                                          const double* __restrict__ consts, const int* __restrict__ agg,
+                                          const int* __restrict__ ptrp, const double* __restrict__ ptv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double omega = consts[1];
+  const int a = agg[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const bool diag = ci[p] == a;
+    for (int r = 0; r < bs; ++r) {
+      const double sc = -omega * dinv[(size_t)i * bs + r];
+      for (int q = 0; q < k; ++q) {
+        size_t o = (size_t)p * bs * k + r * k + q;
+        double val = sc * v[o];
+        if (diag) val += ptv[(size_t)ptrp[i] * bs * k + r * k + q];
+        v[o] = val;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: dense Gauss-Jordan inverse (SPD, no pivoting)
+// ---------------------------------------------------------------------------
+__global__ void bsr_to_dense_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                                    int n, int bs, double* __restrict__ D, int N) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    for (int r = 0; r < bs; ++r)
+      for (int c = 0; c < bs; ++c) D[(size_t)(i * bs + r) * N + j * bs + c] = v[(size_t)p * bs * bs + r * bs + c];
+  }
+}
+
+__global__ void dense_inactive_kernel(double* __restrict__ D, int N, unsigned char* __restrict__ inactive) {
+  int i = blockIdx.x;
+  __shared__ int nz;
+  if (threadIdx.x == 0) nz = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x)
+    if (D[(size_t)i * N + j] != 0.0) nz = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    inactive[i] = nz ? 0 : 1;
+    if (!nz) D[(size_t)i * N + i] = 1.0;
+  }
+}
+
+__global__ void gj_pivot_kernel(double* __restrict__ D, int N, int k, double* __restrict__ colk, double* __restrict__ pivinv,
+                                int* __restrict__ bad) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double p = D[(size_t)k * N + k];
+  if (t == 0) {
+    if (!(p > 0.0)) atomicExch(bad, 1);
+    *pivinv = 1.0 / p;
+  }
+  if (t != k) {
+    colk[t] = D[(size_t)t * N + k];
+    D[(size_t)k * N + t] /= p;
+  }
+}
+
+__global__ void gj_update_kernel(double* __restrict__ D, int N, int k, const double* __restrict__ colk,
+                                 const double* __restrict__ pivinv) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  if (j >= N) return;
+  const double inv = *pivinv;
+  if (i == k) {
+    if (j == k) D[(size_t)k * N + k] = inv;
+    return;
+  }
+  const double f = colk[i];
+  if (j == k) D[(size_t)i * N + k] = -f * inv;
+  else D[(size_t)i * N + j] -= f * D[(size_t)k * N + j];
+}
+
+__global__ void dense_zero_inactive_kernel(double* __restrict__ D, int N, const unsigned char* __restrict__ inactive) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  if (j >= N) return;
+  if (inactive[i] || inactive[j]) D[(size_t)i * N + j] = 0.0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host orchestration
+// ---------------------------------------------------------------------------
+static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s) {
+  const long long N = (long long)L.n_rows * L.bs;
+  const int k = std::min(std::max(H->prm.eig_iters, 1), 64);
+  DBuf<double> v(N, s), vp(N, s), u(N, s), w(N, s), sv(N, s), ab(128, s), nrm(1, s);
+  DBuf<int> mdone(2, s);
+  ab.zero();
+  TAM_CUDA(cudaMemsetAsync(mdone.p, 0, 2 * sizeof(int), s));
+  GridReduce gr{H->partials.p, H->ticket.p};
+  const unsigned g = std::min<unsigned>(grid_for(N, TPB), (unsigned)H->max_grid);
+  lanczos_init_kernel<<<g, TPB, 0, s>>>(L.dinv.p, N, level, sv.p, v.p, gr, nrm.p);
+  TAM_LAUNCH_CHECK();
+  lanczos_normalize_kernel<<<g, TPB, 0, s>>>(N, v.p, sv.p, u.p, vp.p, nrm.p);
+  TAM_LAUNCH_CHECK();
+  LanczosWork LW{v.p, vp.p, u.p, w.p, sv.p, ab.p, mdone.p, N};
+  int* done = mdone.p + 1;
+  TAM_CUDA(cudaMemcpyAsync(mdone.p, &k, sizeof(int), cudaMemcpyHostToDevice, s));
+  for (int j = 0; j < k; ++j) {
+    if (L.bs == 3) {
+      EpiLanczos<3> epi{w.p, sv.p, v.p, L.n_rows, gr, ab.p + j, done};
+      sell_spmv<3, 3>(*L.AS, u.p, epi, s);
+    } else {
+      EpiLanczos<6> epi{w.p, sv.p, v.p, L.n_rows, gr, ab.p + j, done};
+      sell_spmv<6, 6>(*L.AS, u.p, epi, s);
+    }
+    lanczos_orth_kernel<<<g, TPB, 0, s>>>(LW, j, gr, done);
+    TAM_LAUNCH_CHECK();
+    if (j + 1 < k) {
+      lanczos_advance_kernel<<<g, TPB, 0, s>>>(LW, j, done);
+      TAM_LAUNCH_CHECK();
+      lanczos_mark_done_kernel<<<1, 1, 0, s>>>(LW, j, done);
+      TAM_LAUNCH_CHECK();
+    }
+  }
+  const int deg = std::max(H->prm.smoother_degree, 1);
+  L.consts = DBuf<double>(2 + 2 * (size_t)deg, s);
+  tridiag_lmax_kernel<<<1, 1, 0, s>>>(ab.p, mdone.p, k, H->prm.cheb_lo, H->prm.cheb_hi, deg, L.consts.p);
+  TAM_LAUNCH_CHECK();
+  L.lambda_host = read_back_double(L.consts.p, s);
+  TAM_CHECK(std::isfinite(L.lambda_host) && L.lambda_host > 0.0, TAM_ERR_INTERNAL,
+            "amg_setup: lambda_max estimate is not positive");
+}
+
+static int aggregate(Level& L, int level, double theta, cudaStream_t s) {
+  const Bsr& A = *L.A;
+  const int n = A.n_rows;
+  DBuf<double> nrm((size_t)A.nnzb, s), dnrm(n, s);
+  DBuf<unsigned char> strong((size_t)A.nnzb, s), isolated(n, s), state(n, s);
+  block_norms_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, A.vals.p, n, (int)A.block_elems(),
+                                                      nrm.p, dnrm.p);
+  TAM_LAUNCH_CHECK();
+  strength_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, nrm.p, dnrm.p, n, theta, strong.p,
+                                                   isolated.p);
+  TAM_LAUNCH_CHECK();
+  mis_init_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(isolated.p, n, state.p);
+  TAM_LAUNCH_CHECK();
+  DBuf<unsigned long long> m1(n, s);
+  DBuf<int> und(1, s);
+  for (int it = 0; it < 1000; ++it) {
+    und.zero();
+    mis_round1_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, n, level, m1.p);
+    TAM_LAUNCH_CHECK();
+    mis_round2_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, m1.p, n, level,
+                                                       und.p);
+    TAM_LAUNCH_CHECK();
+    if (read_back_int(und.p, s) == 0) break;
+    TAM_CHECK(it < 999, TAM_ERR_INTERNAL, "amg_setup: MIS-2 did not terminate");
+  }
+  DBuf<int> root_id((size_t)n + 1, s);
+  root_flag_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(state.p, isolated.p, n, root_id.p);
+  TAM_LAUNCH_CHECK();
+  exclusive_scan_i32(root_id.p, root_id.p, n, s);
+  const int n_agg = read_back_int(root_id.p + n, s);
+  DBuf<int> agg2(n, s), fail(1, s);
+  fail.zero();
+  agg_phase2_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, isolated.p, root_id.p,
+                                                     n, level, agg2.p);
+  TAM_LAUNCH_CHECK();
+  L.agg = DBuf<int>(n, s);
+  agg_phase3_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, isolated.p, agg2.p, n, level,
+                                                     L.agg.p, fail.p);
+  TAM_LAUNCH_CHECK();
+  TAM_CHECK(read_back_int(fail.p, s) == 0, TAM_ERR_INTERNAL, "amg_setup: aggregation left a node unassigned");
+  return n_agg;
+}
+
+// P_tent and the coarse near-nullspace Bc [n_agg*k, k]
+static void tentative(Level& L, const double* B, double droptol, DBuf<double>& Bc, cudaStream_t s) {
+  const int n = L.n_rows, bs = L.bs, k = L.kdim, na = L.n_agg;
+  Bsr& Pt = L.Pt;
+  Pt.n_rows = n;
+  Pt.n_cols = na;
+  Pt.br = bs;
+  Pt.bc = k;
+  Pt.row_ptr = DBuf<int>((size_t)n + 1, s);
+  has_agg_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(L.agg.p, n, Pt.row_ptr.p);
+  TAM_LAUNCH_CHECK();
+  exclusive_scan_i32(Pt.row_ptr.p, Pt.row_ptr.p, n, s);
+  Pt.nnzb = read_back_int(Pt.row_ptr.p + n, s);
+  Pt.col_idx = DBuf<int>((size_t)Pt.nnzb, s);
+  Pt.vals = DBuf<double>((size_t)Pt.nnzb * bs * k, s);
+  ptent_pattern_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(L.agg.p, Pt.row_ptr.p, n, Pt.col_idx.p, B, bs, k, Pt.vals.p);
+  TAM_LAUNCH_CHECK();
+  DBuf<int> ap((size_t)na + 1, s), cursor(na, s), mem((size_t)std::max<long long>(Pt.nnzb, 1), s),
+      sorted((size_t)std::max<long long>(Pt.nnzb, 1), s);
+  ap.zero();
+  cursor.zero();
+  agg_count_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(L.agg.p, n, ap.p);
+  TAM_LAUNCH_CHECK();
+  exclusive_scan_i32(ap.p, ap.p, na, s);
+  agg_fill_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(L.agg.p, n, ap.p, cursor.p, mem.p);
+  TAM_LAUNCH_CHECK();
+  agg_sort_kernel<<<grid_for((long long)na * 32, TPB), TPB, 0, s>>>(ap.p, na, mem.p, sorted.p);
+  TAM_LAUNCH_CHECK();
+  Bc = DBuf<double>((size_t)na * k * k, s);
+  ptent_qr_kernel<<<grid_for((long long)na * 32, TPB), TPB, 0, s>>>(ap.p, sorted.p, na, Pt.row_ptr.p, Pt.vals.p, bs,
+                                                                    k, 1e-10, Bc.p);
+  TAM_LAUNCH_CHECK();
+  (void)droptol;
+}
+
+static void coarse_inverse(tam_amg_s* H, const Level& L, cudaStream_t s) {
+  const int N = L.n_rows * L.bs;
+  TAM_CHECK(N <= 12000, TAM_ERR_UNSUPPORTED, "amg_setup: coarsest level too large for the dense solve");
+  H->n_coarse = N;
+  H->coarse_inv = DBuf<double>((size_t)N * N, s);
+  H->coarse_inv.zero();
+  const Bsr& A = *L.A;
+  bsr_to_dense_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, A.vals.p, L.n_rows, L.bs,
+                                                              H->coarse_inv.p, N);
+  TAM_LAUNCH_CHECK();
+  DBuf<unsigned char> inactive(N, s);
+  dense_inactive_kernel<<<N, 128, 0, s>>>(H->coarse_inv.p, N, inactive.p);
+  TAM_LAUNCH_CHECK();
+  DBuf<double> colk(N, s), pinv(1, s);
+  DBuf<int> bad(1, s);
+  bad.zero();
+  dim3 ug(grid_for(N, TPB), N);
+  for (int k = 0; k < N; ++k) {
+    gj_pivot_kernel<<<grid_for(N, TPB), TPB, 0, s>>>(H->coarse_inv.p, N, k, colk.p, pinv.p, bad.p);
+    gj_update_kernel<<<ug, TPB, 0, s>>>(H->coarse_inv.p, N, k, colk.p, pinv.p);
+  }
+  TAM_LAUNCH_CHECK();
+  dense_zero_inactive_kernel<<<ug, TPB, 0, s>>>(H->coarse_inv.p, N, inactive.p);
+  TAM_LAUNCH_CHECK();
+  TAM_CHECK(read_back_int(bad.p, s) == 0, TAM_ERR_INTERNAL, "amg_setup: coarsest operator is not positive definite");
+}
+
+static void alloc_level_vectors(Level& L, cudaStream_t s) {
+  size_t N = (size_t)L.n_rows * L.bs;
+  L.b = DBuf<double>(N, s);
+  L.xa = DBuf<double>(N, s);
+  L.xb = DBuf<double>(N, s);
+  L.d = DBuf<double>(N, s);
+  L.t = DBuf<double>(N, s);
+  L.y = DBuf<double>(N, s);
+}
+
+tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& prm, cudaStream_t s) {
+  TAM_CHECK(prm.level_precision == 0, TAM_ERR_UNSUPPORTED, "amg_setup: only the FP64 hierarchy is built");
+  TAM_CHECK(prm.smoother_degree >= 1 && prm.smoother_degree <= 8 && prm.eig_iters >= 1 && prm.eig_iters <= 64 &&
+                prm.max_levels >= 1 && prm.max_levels <= 20 && prm.coarse_max_dofs >= 1 &&
+                prm.cheb_hi > prm.cheb_lo && prm.cheb_lo > 0 && prm.strength_theta >= 0,
+            TAM_ERR_INVALID_ARG, "amg_setup: parameter out of range");
+  auto H = new tam_amg_s();
+  try {
+    H->K = K;
+    H->prm = prm;
+    const int n0 = K->n_nodes;
+    H->max_grid = 8 * 1024;
+    {
+      unsigned g0 = sell_grid(K->S);
+      H->max_grid = std::max<int>(H->max_grid, (int)g0);
+    }
+    H->partials = DBuf<double>((size_t)H->max_grid * 4, s);
+    H->ticket = DBuf<unsigned int>(1, s);
+    H->ticket.zero();
+    GridReduce gr{H->partials.p, H->ticket.p};
+    const int k = prm.use_rotations ? 6 : 3;
+    // near-nullspace of the finest level
+    DBuf<double> cen(3, s);
+    centroid_kernel<<<std::min<unsigned>(grid_for(n0, TPB), 1024), TPB, 0, s>>>(coords, n0, gr, cen.p);
+    TAM_LAUNCH_CHECK();
+    DBuf<double> B((size_t)n0 * 3 * k, s);
+    rigid_modes_kernel<<<grid_for(n0, TPB), TPB, 0, s>>>(coords, K->dmask.p, n0, cen.p, k, B.p);
+    TAM_LAUNCH_CHECK();
+    H->levels.reserve(prm.max_levels);  // references into `levels` stay valid while it grows
+    H->levels.emplace_back();
+    H->levels[0].A = &K->A;
+    H->levels[0].AS = &K->S;
+    for (int lev = 0;; ++lev) {
+      Level& L = H->levels[lev];
+      L.n_rows = L.A->n_rows;
+      L.bs = L.A->br;
+      L.kdim = k;
+      L.dinv = DBuf<double>((size_t)L.n_rows * L.bs, s);
+      point_dinv_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.A->row_ptr.p, L.A->col_idx.p, L.A->vals.p, L.n_rows,
+                                                                L.bs, L.dinv.p);
+      TAM_LAUNCH_CHECK();
+      lanczos_lambda(H, L, lev, s);
+      alloc_level_vectors(L, s);
+      const bool last = (long long)L.n_rows * L.bs <= prm.coarse_max_dofs || lev == prm.max_levels - 1;
+      if (!last) L.n_agg = aggregate(L, lev, prm.strength_theta, s);
+      if (last || L.n_agg == 0 || L.n_agg >= L.n_rows) {
+        L.n_agg = 0;
+        L.agg.reset();
+        coarse_inverse(H, L, s);
+        break;
+      }
+      DBuf<double> Bc;
+      tentative(L, B.p, 1e-10, Bc, s);
+      // P = (I - omega D^-1 A) P_tent, computed on the pattern of A P_tent
+      bsr_spgemm(*L.A, L.Pt, L.P, s);
+      smooth_prolongator_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p,
+                                                                        L.n_rows, L.bs, k, L.dinv.p, L.consts.p,
+                                                                        L.agg.p, L.Pt.row_ptr.p, L.Pt.vals.p);
+      TAM_LAUNCH_CHECK();
+      bsr_transpose(L.P, L.R, s);
+      {
+        Bsr AP;
+        bsr_spgemm(*L.A, L.P, AP, s);
+        H->levels.emplace_back();
+        Level& C = H->levels[lev + 1];
+        bsr_spgemm(L.R, AP, C.A_own, s);
+        C.A = &C.A_own;
+        C.AS = &C.AS_own;
+        bsr_to_sell(C.A_own, C.AS_own, s);
+      }
+      bsr_to_sell(L.P, L.PS, s);
+      bsr_to_sell(L.R, L.RS, s);
+      B = std::move(Bc);
+    }
+    H->r = DBuf<double>((size_t)n0 * 3, s);
+    H->z = DBuf<double>((size_t)n0 * 3, s);
+    H->p = DBuf<double>((size_t)n0 * 3, s);
+    H->q = DBuf<double>((size_t)n0 * 3, s);
+    H->sc = DBuf<PcgScalars>(1, s);
+    TAM_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete H;
+    throw;
+  }
+  return H;
+}
+
+}  // namespace tam

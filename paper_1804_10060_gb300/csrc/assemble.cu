@@ -1,0 +1,433 @@
+// Assembly of the thermoelastic system (paper Sec. 3, Eq. wf_elastic, steady,
+// traction free, with the Dirichlet condition of Eq. u-dbc).
+//
+//   K[(a,i),(b,j)] = int lambda d_i phi_a d_j phi_b + mu d_j phi_a d_i phi_b
+//                        + mu delta_ij grad phi_a . grad phi_b
+//   f[(a,i)]       = int (3 lambda + 2 mu) alpha (T_h - T_ref) d_i phi_a + int f_h,i phi_a
+//
+// (isotropic C, eps_T = alpha (T - T_ref) I, so C:eps_T = (3 lambda + 2 mu) alpha (T - T_ref) I).
+//
+// Pipeline: cell-node incidence (count, scan, fill) -> block-CSR pattern, one
+// warp per node (gather, bitonic sort, unique) -> element kernels with FP64
+// atomic scatter -> Dirichlet rows.  Dirichlet couplings never enter the
+// pattern: an element block K_ab with a free row a and a Dirichlet column b
+// is lifted straight into the load (f_a -= K_ab u_b) and rows of Dirichlet
+// nodes become identity rows -- the symmetric elimination of Eq. u-dbc.
+#include "handles.cuh"
+
+namespace tam {
+namespace {
+
+constexpr int PAT_WARPS = 4;
+constexpr int PAT_CAP = 1024;  // candidate node ids per row (incident cells x nodes per cell + 1)
+
+__global__ void validate_kernel(const int* __restrict__ cells, long long n_entries, int npc, int n_nodes,
+                                const int* __restrict__ mat, int n_cells, int n_mat, int* __restrict__ bad) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_entries) {
+    int v = cells[t];
+    if (v < 0 || v >= n_nodes) atomicExch(bad, 1);
+  }
+  if (t < n_cells) {
+    int m = mat[t];
+    if (m < 0 || m >= n_mat) atomicExch(bad, 2);
+  }
+}
+
+__global__ void incidence_count_kernel(const int* __restrict__ cells, long long n_entries, int* __restrict__ cnt) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_entries) atomicAdd(&cnt[cells[t]], 1);
+}
+
+__global__ void incidence_fill_kernel(const int* __restrict__ cells, long long n_entries, int npc,
+                                      const int* __restrict__ ptr, int* __restrict__ cursor,
+                                      int* __restrict__ inc) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_entries) return;
+  int v = cells[t];
+  inc[ptr[v] + atomicAdd(&cursor[v], 1)] = (int)(t / npc);
+}
+
+// One warp per node: candidate columns = self + all nodes of incident cells,
+// minus Dirichlet nodes (a Dirichlet row keeps only its diagonal).
+template <bool FILL>
+__global__ void __launch_bounds__(PAT_WARPS * 32)
+pattern_kernel(int n_nodes, int npc, const int* __restrict__ cells, const int* __restrict__ inc_ptr,
+               const int* __restrict__ inc, const unsigned char* __restrict__ dmask,
+               int* __restrict__ row_cnt, const int* __restrict__ row_ptr, int* __restrict__ col_idx,
+               int* __restrict__ overflow) {
+  __shared__ int buf_all[PAT_WARPS][PAT_CAP];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * PAT_WARPS + wid;
+  if (i >= n_nodes) return;
+  int* buf = buf_all[wid];
+  const bool di = dmask[i] != 0;
+  const int s = inc_ptr[i], e = inc_ptr[i + 1];
+  const int n_cand = di ? 1 : 1 + (e - s) * npc;
+  if (n_cand > PAT_CAP) {
+    if (lane == 0) {
+      atomicExch(overflow, 1);
+      if (!FILL) row_cnt[i] = 1;
+    }
+    return;
+  }
+  if (lane == 0) buf[0] = i;
+  if (!di) {
+    for (int t = lane; t < (e - s) * npc; t += 32) {
+      int c = inc[s + t / npc];
+      int j = cells[(size_t)c * npc + (t % npc)];
+      buf[1 + t] = dmask[j] ? 0x7fffffff : j;
+    }
+  }
+  const int n2 = next_pow2(n_cand);
+  for (int t = n_cand + lane; t < n2; t += 32) buf[t] = 0x7fffffff;
+  __syncwarp();
+  warp_bitonic_sort<false>(buf, nullptr, n2);
+  const int cnt = warp_unique_sorted(buf, n2);
+  __syncwarp();
+  if (!FILL) {
+    if (lane == 0) row_cnt[i] = cnt;
+  } else {
+    const int r0 = row_ptr[i];
+    for (int t = lane; t < cnt; t += 32) col_idx[r0 + t] = buf[t];
+  }
+}
+
+__device__ __forceinline__ void lame(double E, double nu, double& lam, double& mu) {
+  mu = E / (2.0 * (1.0 + nu));
+  lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+}
+
+// Gradients of the barycentric coordinates and the volume of a tet.
+__device__ __forceinline__ bool tet_geometry(const double* __restrict__ X, const int* v, double g[4][3], double& vol) {
+  double x0 = X[3 * v[0]], y0 = X[3 * v[0] + 1], z0 = X[3 * v[0] + 2];
+  double a[3][3];  // rows: edge vectors x_k - x_0
+  for (int k = 0; k < 3; ++k) {
+    a[k][0] = X[3 * v[k + 1]] - x0;
+    a[k][1] = X[3 * v[k + 1] + 1] - y0;
+    a[k][2] = X[3 * v[k + 1] + 2] - z0;
+  }
+  // cofactors: grad l_{k+1} = (row k of inverse of the matrix with columns a_k)
+  double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+  double c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+  double c02 = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+  double det = a[0][0] * c00 + a[0][1] * c01 + a[0][2] * c02;
+  vol = det / 6.0;
+  if (!(vol > 0.0) || !isfinite(vol)) return false;
+  double id = 1.0 / det;
+  // grad l1 = (a1 x a2)/det, grad l2 = (a2 x a0)/det, grad l3 = (a0 x a1)/det
+  g[1][0] = c00 * id; g[1][1] = c01 * id; g[1][2] = c02 * id;
+  g[2][0] = (a[2][1] * a[0][2] - a[2][2] * a[0][1]) * id;
+  g[2][1] = (a[2][2] * a[0][0] - a[2][0] * a[0][2]) * id;
+  g[2][2] = (a[2][0] * a[0][1] - a[2][1] * a[0][0]) * id;
+  g[3][0] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) * id;
+  g[3][1] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) * id;
+  g[3][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) * id;
+  for (int d = 0; d < 3; ++d) g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+  return true;
+}
+
+struct AsmArgs {
+  const double* coords;
+  const int* cells;
+  const int* mat;
+  const double* props;
+  const double* T;
+  double T_ref;
+  const double* body;
+  const unsigned char* dmask;
+  const double* ud;
+  const int* row_ptr;
+  const int* col_idx;
+  double* vals;
+  double* rhs;
+  int n_cells;
+  int* bad_cell;
+};
+
+// Scatter one 3x3 block (row node na, col node nb) or lift it into the load.
+__device__ __forceinline__ void scatter_block(const AsmArgs& A, int na, int nb, const double k[9]) {
+  if (A.dmask[nb]) {
+    if (A.ud) {
+      const double* u = A.ud + 3 * (size_t)nb;
+      for (int r = 0; r < 3; ++r)
+        atomicAdd(&A.rhs[3 * (size_t)na + r], -(k[3 * r] * u[0] + k[3 * r + 1] * u[1] + k[3 * r + 2] * u[2]));
+    }
+    return;
+  }
+  int slot = bsearch_i32(A.col_idx, A.row_ptr[na], A.row_ptr[na + 1], nb);
+  double* dst = A.vals + (size_t)slot * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) atomicAdd(dst + e, k[e]);
+}
+
+// P1: constant gradients, one thread per cell.
+__global__ void __launch_bounds__(128) assemble_p1_kernel(AsmArgs A) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.n_cells) return;
+  int v[4];
+  for (int a = 0; a < 4; ++a) v[a] = A.cells[4 * (size_t)c + a];
+  double g[4][3], vol;
+  if (!tet_geometry(A.coords, v, g, vol)) {
+    atomicExch(A.bad_cell, 1);
+    return;
+  }
+  const int m = A.mat[c];
+  double lam, mu;
+  lame(A.props[3 * m], A.props[3 * m + 1], lam, mu);
+  const double alpha = A.props[3 * m + 2];
+  // thermal: int (T_h - T_ref) d_i phi_a = vol (mean vertex T - T_ref) g_a[i]
+  double cT = 0.0;
+  if (A.T) cT = (3.0 * lam + 2.0 * mu) * alpha * vol * (0.25 * (A.T[v[0]] + A.T[v[1]] + A.T[v[2]] + A.T[v[3]]) - A.T_ref);
+  double fsum[3] = {0, 0, 0};
+  if (A.body)
+    for (int b = 0; b < 4; ++b)
+      for (int d = 0; d < 3; ++d) fsum[d] += A.body[3 * (size_t)v[b] + d];
+  for (int a = 0; a < 4; ++a) {
+    const int na = v[a];
+    if (A.dmask[na]) continue;
+    for (int b = 0; b < 4; ++b) {
+      double gg = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
+      double k[9];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          k[3 * i + j] = vol * (lam * g[a][i] * g[b][j] + mu * g[a][j] * g[b][i] + (i == j ? mu * gg : 0.0));
+      scatter_block(A, na, v[b], k);
+    }
+    // body: int f_h phi_a = vol/20 (sum_b f_b + f_a) (P1 mass matrix vol (1 + delta_ab)/20)
+    for (int i = 0; i < 3; ++i) {
+      double f = cT * g[a][i];
+      if (A.body) f += vol / 20.0 * (fsum[i] + A.body[3 * (size_t)na + i]);
+      atomicAdd(&A.rhs[3 * (size_t)na + i], f);
+    }
+  }
+}
+
+// P2 quadrature.  Stiffness integrand is degree 2: 4-point rule with
+// barycentric points (A,B,B,B) and permutations, A = (5+3 sqrt5)/20,
+// B = (5-sqrt5)/20, equal weights 1/4.  Loads are degree 3 (thermal) and 4
+// (body): Keast's 11-point degree-4 rule (weights normalised to sum 1).
+__constant__ double c_q4[4][4] = {
+    {0.5854101966249685, 0.1381966011250105, 0.1381966011250105, 0.1381966011250105},
+    {0.1381966011250105, 0.5854101966249685, 0.1381966011250105, 0.1381966011250105},
+    {0.1381966011250105, 0.1381966011250105, 0.5854101966249685, 0.1381966011250105},
+    {0.1381966011250105, 0.1381966011250105, 0.1381966011250105, 0.5854101966249685}};
+__constant__ double c_k11[11][5] = {  // l0, l1, l2, l3, weight
+    {0.25, 0.25, 0.25, 0.25, -0.078933333333333333},
+    {0.7857142857142857, 0.0714285714285714, 0.0714285714285714, 0.0714285714285714, 0.045733333333333333},
+    {0.0714285714285714, 0.7857142857142857, 0.0714285714285714, 0.0714285714285714, 0.045733333333333333},
+    {0.0714285714285714, 0.0714285714285714, 0.7857142857142857, 0.0714285714285714, 0.045733333333333333},
+    {0.0714285714285714, 0.0714285714285714, 0.0714285714285714, 0.7857142857142857, 0.045733333333333333},
+    {0.3994035761667992, 0.3994035761667992, 0.1005964238332008, 0.1005964238332008, 0.149333333333333333},
+    {0.3994035761667992, 0.1005964238332008, 0.3994035761667992, 0.1005964238332008, 0.149333333333333333},
+    {0.3994035761667992, 0.1005964238332008, 0.1005964238332008, 0.3994035761667992, 0.149333333333333333},
+    {0.1005964238332008, 0.3994035761667992, 0.3994035761667992, 0.1005964238332008, 0.149333333333333333},
+    {0.1005964238332008, 0.3994035761667992, 0.1005964238332008, 0.3994035761667992, 0.149333333333333333},
+    {0.1005964238332008, 0.1005964238332008, 0.3994035761667992, 0.3994035761667992, 0.149333333333333333}};
+__constant__ int c_edge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+__device__ __forceinline__ double p2_phi(int a, const double* l) {
+  if (a < 4) return l[a] * (2.0 * l[a] - 1.0);
+  return 4.0 * l[c_edge[a - 4][0]] * l[c_edge[a - 4][1]];
+}
+
+__device__ __forceinline__ void p2_grad(int a, const double* l, const double g[4][3], double out[3]) {
+  if (a < 4) {
+    double s = 4.0 * l[a] - 1.0;
+    for (int d = 0; d < 3; ++d) out[d] = s * g[a][d];
+  } else {
+    int p = c_edge[a - 4][0], q = c_edge[a - 4][1];
+    for (int d = 0; d < 3; ++d) out[d] = 4.0 * (l[q] * g[p][d] + l[p] * g[q][d]);
+  }
+}
+
+constexpr int P2_WARPS = 4;
+
+// P2: one warp per cell.  Lane 0 computes the geometry; the 4x10 gradient
+// table goes to shared memory; lanes then take the 100 (a,b) blocks.
+__global__ void __launch_bounds__(P2_WARPS * 32) assemble_p2_kernel(AsmArgs A) {
+  __shared__ double sg[P2_WARPS][4][10][3];
+  __shared__ double sgeo[P2_WARPS][4][3];
+  __shared__ double svol[P2_WARPS];
+  __shared__ int sv[P2_WARPS][10];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * P2_WARPS + wid;
+  if (c >= A.n_cells) return;
+  if (lane < 10) sv[wid][lane] = A.cells[10 * (size_t)c + lane];
+  __syncwarp();
+  int ok = 1;
+  if (lane == 0) {
+    double g[4][3], vol;
+    ok = tet_geometry(A.coords, sv[wid], g, vol) ? 1 : 0;
+    for (int k = 0; k < 4; ++k)
+      for (int d = 0; d < 3; ++d) sgeo[wid][k][d] = g[k][d];
+    svol[wid] = vol;
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) {
+    if (lane == 0) atomicExch(A.bad_cell, 1);
+    return;
+  }
+  __syncwarp();
+  double g[4][3];
+  for (int k = 0; k < 4; ++k)
+    for (int d = 0; d < 3; ++d) g[k][d] = sgeo[wid][k][d];
+  const double vol = svol[wid];
+  for (int t = lane; t < 40; t += 32) {
+    int q = t / 10, a = t % 10;
+    double gr[3];
+    p2_grad(a, c_q4[q], g, gr);
+    for (int d = 0; d < 3; ++d) sg[wid][q][a][d] = gr[d];
+  }
+  __syncwarp();
+  const int m = A.mat[c];
+  double lam, mu;
+  lame(A.props[3 * m], A.props[3 * m + 1], lam, mu);
+  const double alpha = A.props[3 * m + 2];
+  const double w = 0.25 * vol;
+  for (int p = lane; p < 100; p += 32) {
+    const int a = p / 10, b = p % 10;
+    const int na = sv[wid][a];
+    if (A.dmask[na]) continue;
+    double k[9];
+    for (int e = 0; e < 9; ++e) k[e] = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      const double* ga = sg[wid][q][a];
+      const double* gb = sg[wid][q][b];
+      double gg = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          k[3 * i + j] += w * (lam * ga[i] * gb[j] + mu * ga[j] * gb[i] + (i == j ? mu * gg : 0.0));
+    }
+    scatter_block(A, na, sv[wid][b], k);
+  }
+  // loads: lane a < 10 integrates its node's thermal and body terms
+  if (lane < 10) {
+    const int a = lane, na = sv[wid][a];
+    if (!A.dmask[na]) {
+      const double kT = (3.0 * lam + 2.0 * mu) * alpha;
+      double f[3] = {0, 0, 0};
+      for (int q = 0; q < 11; ++q) {
+        const double* l = c_k11[q];
+        const double wq = l[4] * vol;
+        double Th = 0.0, fh[3] = {0, 0, 0};
+        for (int cidx = 0; cidx < 10; ++cidx) {
+          double ph = p2_phi(cidx, l);
+          int nc = sv[wid][cidx];
+          if (A.T) Th += ph * A.T[nc];
+          if (A.body)
+            for (int d = 0; d < 3; ++d) fh[d] += ph * A.body[3 * (size_t)nc + d];
+        }
+        double gr[3];
+        p2_grad(a, l, g, gr);
+        double pa = p2_phi(a, l);
+        for (int d = 0; d < 3; ++d) {
+          if (A.T) f[d] += wq * kT * (Th - A.T_ref) * gr[d];
+          if (A.body) f[d] += wq * pa * fh[d];
+        }
+      }
+      for (int d = 0; d < 3; ++d) atomicAdd(&A.rhs[3 * (size_t)na + d], f[d]);
+    }
+  }
+}
+
+// Dirichlet (and cell-less) rows: identity diagonal block, load = u_D.
+__global__ void dirichlet_rows_kernel(int n, const unsigned char* __restrict__ dmask,
+                                      const int* __restrict__ inc_ptr, const double* __restrict__ ud,
+                                      const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
+                                      double* __restrict__ vals, double* __restrict__ rhs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool orphan = inc_ptr[i + 1] == inc_ptr[i];
+  if (!dmask[i] && !orphan) return;
+  int slot = bsearch_i32(col_idx, row_ptr[i], row_ptr[i + 1], i);
+  double* d = vals + (size_t)slot * 9;
+  for (int e = 0; e < 9; ++e) d[e] = (e % 4 == 0) ? 1.0 : 0.0;
+  for (int r = 0; r < 3; ++r) rhs[3 * (size_t)i + r] = (dmask[i] && ud) ? ud[3 * (size_t)i + r] : 0.0;
+}
+
+}  // namespace
+
+tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells, int npc, const int* cells,
+                                  const int* mat, int n_mat, const double* props, const double* T,
+                                  double T_ref, const double* body, const unsigned char* dmask,
+                                  const double* ud, double* rhs, cudaStream_t s) {
+  TAM_CHECK(n_nodes > 0 && n_cells >= 0 && n_mat > 0, TAM_ERR_INVALID_ARG, "fem_assemble: bad sizes");
+  TAM_CHECK(npc == 4 || npc == 10, TAM_ERR_INVALID_ARG, "fem_assemble: nodes_per_cell must be 4 or 10");
+  TAM_CHECK(coords && (cells || n_cells == 0) && (mat || n_cells == 0) && props && dmask && rhs,
+            TAM_ERR_INVALID_ARG, "fem_assemble: null pointer");
+  auto M = new tam_matrix_s();
+  try {
+    M->n_nodes = n_nodes;
+    const long long n_entries = (long long)n_cells * npc;
+    DBuf<int> flag(2, s);
+    flag.zero();
+    if (n_cells > 0) {
+      validate_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, npc, n_nodes, mat, n_cells,
+                                                                n_mat, flag.p);
+      TAM_LAUNCH_CHECK();
+      int bad = read_back_int(flag.p, s);
+      TAM_CHECK(bad == 0, TAM_ERR_INVALID_ARG,
+                bad == 1 ? "fem_assemble: cell node id out of range" : "fem_assemble: material id out of range");
+    }
+    // cell-node incidence
+    DBuf<int> inc_ptr((size_t)n_nodes + 1, s), cursor((size_t)n_nodes, s), inc((size_t)std::max(1LL, n_entries), s);
+    inc_ptr.zero();
+    cursor.zero();
+    if (n_cells > 0) {
+      incidence_count_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, inc_ptr.p);
+      TAM_LAUNCH_CHECK();
+    }
+    exclusive_scan_i32(inc_ptr.p, inc_ptr.p, n_nodes, s);
+    if (n_cells > 0) {
+      incidence_fill_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, npc, inc_ptr.p, cursor.p,
+                                                                     inc.p);
+      TAM_LAUNCH_CHECK();
+    }
+    // pattern
+    Bsr& A = M->A;
+    A.n_rows = A.n_cols = n_nodes;
+    A.br = A.bc = 3;
+    A.row_ptr = DBuf<int>((size_t)n_nodes + 1, s);
+    unsigned pg = grid_for(n_nodes, PAT_WARPS);
+    pattern_kernel<false><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
+                                                       nullptr, nullptr, flag.p + 1);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
+    A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
+    TAM_CHECK(read_back_int(flag.p + 1, s) == 0, TAM_ERR_UNSUPPORTED,
+              "fem_assemble: a node has too many incident cells for the pattern builder");
+    A.col_idx = DBuf<int>((size_t)A.nnzb, s);
+    pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, nullptr,
+                                                      A.row_ptr.p, A.col_idx.p, flag.p + 1);
+    TAM_LAUNCH_CHECK();
+    // numeric
+    A.vals = DBuf<double>((size_t)A.nnzb * 9, s);
+    A.vals.zero();
+    TAM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * (size_t)n_nodes, s));
+    AsmArgs args{coords, cells, mat, props, T, T_ref, body, dmask, ud, A.row_ptr.p, A.col_idx.p,
+                 A.vals.p, rhs, n_cells, flag.p};
+    if (n_cells > 0) {
+      if (npc == 4)
+        assemble_p1_kernel<<<grid_for(n_cells, 128), 128, 0, s>>>(args);
+      else
+        assemble_p2_kernel<<<grid_for(n_cells, P2_WARPS), P2_WARPS * 32, 0, s>>>(args);
+      TAM_LAUNCH_CHECK();
+    }
+    dirichlet_rows_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, dmask, inc_ptr.p, ud, A.row_ptr.p,
+                                                                 A.col_idx.p, A.vals.p, rhs);
+    TAM_LAUNCH_CHECK();
+    TAM_CHECK(read_back_int(flag.p, s) == 0, TAM_ERR_DEGENERATE_CELL,
+              "fem_assemble: a cell has non-positive or non-finite volume");
+    M->dmask = DBuf<unsigned char>((size_t)n_nodes, s);
+    TAM_CUDA(cudaMemcpyAsync(M->dmask.p, dmask, n_nodes, cudaMemcpyDeviceToDevice, s));
+    bsr_to_sell(A, M->S, s);
+    TAM_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete M;
+    throw;
+  }
+  return M;
+}
+
+}  // namespace tam

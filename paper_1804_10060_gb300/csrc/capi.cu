@@ -1,0 +1,273 @@
+// C ABI of the thermoamg library (declared in include/thermoamg.h).  Every
+// entry point converts internal exceptions into a status code and a message
+// for tam_last_error(); none aborts the process.
+#include <cmath>
+#include <cstring>
+
+#include "handles.cuh"
+
+namespace tam {
+const char* last_error_cstr();
+}
+
+using namespace tam;
+
+tam_amg_s::~tam_amg_s() {
+  if (iter_exec) cudaGraphExecDestroy(iter_exec);
+}
+
+namespace {
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    set_last_error("");
+    return f();
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return TAM_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return TAM_ERR_INTERNAL;
+  } catch (...) {
+    set_last_error("unknown failure");
+    return TAM_ERR_INTERNAL;
+  }
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void export_bsr(const Bsr& A, int* rp, int* ci, double* v, cudaStream_t s) {
+  TAM_CUDA(cudaMemcpyAsync(rp, A.row_ptr.p, sizeof(int) * ((size_t)A.n_rows + 1), cudaMemcpyDeviceToDevice, s));
+  if (A.nnzb > 0) {
+    TAM_CUDA(cudaMemcpyAsync(ci, A.col_idx.p, sizeof(int) * (size_t)A.nnzb, cudaMemcpyDeviceToDevice, s));
+    TAM_CUDA(cudaMemcpyAsync(v, A.vals.p, sizeof(double) * (size_t)A.nnzb * A.block_elems(),
+                             cudaMemcpyDeviceToDevice, s));
+  }
+  TAM_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tam_last_error(void) { return last_error_cstr(); }
+
+int fem_assemble_elasticity(int n_nodes, const double* coords, int n_cells, int nodes_per_cell, const int* cells,
+                            const int* cell_material, int n_mat, const double* mat_props, const double* T,
+                            double T_ref, const double* body_force, const unsigned char* dirichlet_mask,
+                            const double* u_dirichlet, tam_matrix* K_out, double* rhs_out, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(K_out, TAM_ERR_INVALID_ARG, "fem_assemble: K_out is NULL");
+    *K_out = nullptr;
+    *K_out = assemble_elasticity(n_nodes, coords, n_cells, nodes_per_cell, cells, cell_material, n_mat, mat_props, T,
+                                 T_ref, body_force, dirichlet_mask, u_dirichlet, rhs_out, as_stream(stream));
+    return TAM_OK;
+  });
+}
+
+int tam_matrix_info(tam_matrix K, int* n_block_rows, long long* nnzb, int* block_size) {
+  return guarded([&] {
+    TAM_CHECK(K, TAM_ERR_INVALID_ARG, "tam_matrix_info: NULL handle");
+    if (n_block_rows) *n_block_rows = K->A.n_rows;
+    if (nnzb) *nnzb = K->A.nnzb;
+    if (block_size) *block_size = K->A.br;
+    return TAM_OK;
+  });
+}
+
+int tam_matrix_export_bsr(tam_matrix K, int* row_ptr, int* col_idx, double* vals, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(K && row_ptr && col_idx && vals, TAM_ERR_INVALID_ARG, "tam_matrix_export_bsr: NULL argument");
+    export_bsr(K->A, row_ptr, col_idx, vals, as_stream(stream));
+    return TAM_OK;
+  });
+}
+
+int tam_matrix_spmv(tam_matrix K, const double* x, double* y, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(K && x && y && x != y, TAM_ERR_INVALID_ARG, "tam_matrix_spmv: bad argument");
+    spmv_K(K, x, y, as_stream(stream));
+    return TAM_OK;
+  });
+}
+
+int tam_matrix_destroy(tam_matrix K) {
+  return guarded([&] {
+    delete K;
+    return TAM_OK;
+  });
+}
+
+int amg_params_default(amg_params* p) {
+  return guarded([&] {
+    TAM_CHECK(p, TAM_ERR_INVALID_ARG, "amg_params_default: NULL");
+    p->strength_theta = 0.0;
+    p->smoother_degree = 2;
+    p->cheb_lo = 0.1;
+    p->cheb_hi = 1.1;
+    p->eig_iters = 10;
+    p->coarse_max_dofs = 2000;
+    p->max_levels = 10;
+    p->use_rotations = 1;
+    p->level_precision = 0;
+    return TAM_OK;
+  });
+}
+
+int amg_setup(tam_matrix K, const double* coords, const amg_params* params, tam_amg* amg_out, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(K && coords && amg_out, TAM_ERR_INVALID_ARG, "amg_setup: NULL argument");
+    *amg_out = nullptr;
+    amg_params prm;
+    if (params) prm = *params; else amg_params_default(&prm);
+    *amg_out = amg_build(K, coords, prm, as_stream(stream));
+    return TAM_OK;
+  });
+}
+
+int amg_info(tam_amg amg, int* n_levels, long long* level_rows, long long* level_nnzb, int* level_block,
+             double* level_lambda, double* op_complexity) {
+  return guarded([&] {
+    TAM_CHECK(amg, TAM_ERR_INVALID_ARG, "amg_info: NULL handle");
+    const int L = (int)amg->levels.size();
+    if (n_levels) *n_levels = L;
+    double tot = 0.0, fine = 0.0;
+    for (int l = 0; l < L; ++l) {
+      const Level& lv = amg->levels[l];
+      if (level_rows) level_rows[l] = lv.n_rows;
+      if (level_nnzb) level_nnzb[l] = lv.A->nnzb;
+      if (level_block) level_block[l] = lv.bs;
+      if (level_lambda) level_lambda[l] = lv.lambda_host;
+      double nz = (double)lv.A->nnzb * lv.bs * lv.bs;
+      tot += nz;
+      if (l == 0) fine = nz;
+    }
+    if (op_complexity) *op_complexity = fine > 0 ? tot / fine : 0.0;
+    return TAM_OK;
+  });
+}
+
+int amg_level_aggregates(tam_amg amg, int level, int* agg, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(amg && agg && level >= 0 && level < (int)amg->levels.size(), TAM_ERR_INVALID_ARG,
+              "amg_level_aggregates: bad argument");
+    const Level& L = amg->levels[level];
+    cudaStream_t s = as_stream(stream);
+    if (L.agg.p)
+      TAM_CUDA(cudaMemcpyAsync(agg, L.agg.p, sizeof(int) * L.n_rows, cudaMemcpyDeviceToDevice, s));
+    else
+      TAM_CUDA(cudaMemsetAsync(agg, 0xff, sizeof(int) * L.n_rows, s));
+    TAM_CUDA(cudaStreamSynchronize(s));
+    return TAM_OK;
+  });
+}
+
+int amg_level_export(tam_amg amg, int level, int which, int* n_rows, int* n_cols, int* br, int* bc, long long* nnzb,
+                     int* row_ptr, int* col_idx, double* vals, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(amg && level >= 0 && level < (int)amg->levels.size() && which >= 0 && which <= 3,
+              TAM_ERR_INVALID_ARG, "amg_level_export: bad argument");
+    const Level& L = amg->levels[level];
+    const Bsr* M = which == 0 ? L.A : which == 1 ? &L.P : which == 2 ? &L.R : &L.Pt;
+    TAM_CHECK(which == 0 || L.n_agg > 0, TAM_ERR_INVALID_ARG, "amg_level_export: the coarsest level has no P/R");
+    if (n_rows) *n_rows = M->n_rows;
+    if (n_cols) *n_cols = M->n_cols;
+    if (br) *br = M->br;
+    if (bc) *bc = M->bc;
+    if (nnzb) *nnzb = M->nnzb;
+    if (row_ptr) {
+      TAM_CHECK(col_idx && vals, TAM_ERR_INVALID_ARG, "amg_level_export: NULL array");
+      export_bsr(*M, row_ptr, col_idx, vals, as_stream(stream));
+    }
+    return TAM_OK;
+  });
+}
+
+int amg_vcycle(tam_amg amg, const double* r, double* z, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(amg && r && z && r != z, TAM_ERR_INVALID_ARG, "amg_vcycle: bad argument");
+    vcycle_apply(amg, r, z, nullptr, as_stream(stream));
+    return TAM_OK;
+  });
+}
+
+int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double atol, int max_iter, int* iters_out,
+                  double* final_rel_resid_out, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(amg, TAM_ERR_INVALID_ARG, "amg_pcg_solve: NULL handle");
+    int st = pcg_solve(amg, b, x, rtol, atol, max_iter, iters_out, final_rel_resid_out, as_stream(stream));
+    if (st != TAM_OK) {
+      const char* msg = st == TAM_ERR_NOT_CONVERGED   ? "amg_pcg_solve: max_iter reached"
+                        : st == TAM_ERR_BREAKDOWN      ? "amg_pcg_solve: p^T K p <= 0"
+                        : st == TAM_ERR_INDEFINITE_PRECOND ? "amg_pcg_solve: r^T M^-1 r <= 0 (indefinite preconditioner)"
+                        : st == TAM_ERR_NAN            ? "amg_pcg_solve: NaN/Inf encountered"
+                                                      : "amg_pcg_solve: failed";
+      set_last_error(msg);
+    }
+    return st;
+  });
+}
+
+int amg_destroy(tam_amg amg) {
+  return guarded([&] {
+    delete amg;
+    return TAM_OK;
+  });
+}
+
+int tam_solve_elasticity_host(int n_nodes, const double* coords_h, int n_cells, int npc, const int* cells_h,
+                              const int* mat_h, int n_mat, const double* props_h, const double* T_h, double T_ref,
+                              const double* body_h, const unsigned char* dmask_h, const double* ud_h,
+                              const amg_params* params, double rtol, int max_iter, double* u_h, int* iters_out,
+                              double* rel_out, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(n_nodes > 0 && n_cells >= 0 && (npc == 4 || npc == 10) && n_mat > 0, TAM_ERR_INVALID_ARG,
+              "tam_solve_elasticity_host: bad sizes");
+    TAM_CHECK(coords_h && (cells_h || !n_cells) && (mat_h || !n_cells) && props_h && dmask_h && u_h,
+              TAM_ERR_INVALID_ARG, "tam_solve_elasticity_host: NULL argument");
+    cudaStream_t s = as_stream(stream);
+    const size_t n3 = (size_t)n_nodes * 3, ne = (size_t)n_cells * npc;
+    DBuf<double> X(n3, s), Td(T_h ? n_nodes : 0, s), Bd(body_h ? n3 : 0, s), Ud(ud_h ? n3 : 0, s),
+        props(3 * (size_t)n_mat, s), rhs(n3, s), u(n3, s);
+    DBuf<int> C(std::max<size_t>(ne, 1), s), M(std::max<size_t>(n_cells, 1), s);
+    DBuf<unsigned char> D(n_nodes, s);
+    TAM_CUDA(cudaMemcpyAsync(X.p, coords_h, n3 * 8, cudaMemcpyHostToDevice, s));
+    if (ne) TAM_CUDA(cudaMemcpyAsync(C.p, cells_h, ne * 4, cudaMemcpyHostToDevice, s));
+    if (n_cells) TAM_CUDA(cudaMemcpyAsync(M.p, mat_h, (size_t)n_cells * 4, cudaMemcpyHostToDevice, s));
+    TAM_CUDA(cudaMemcpyAsync(props.p, props_h, 24 * (size_t)n_mat, cudaMemcpyHostToDevice, s));
+    if (T_h) TAM_CUDA(cudaMemcpyAsync(Td.p, T_h, (size_t)n_nodes * 8, cudaMemcpyHostToDevice, s));
+    if (body_h) TAM_CUDA(cudaMemcpyAsync(Bd.p, body_h, n3 * 8, cudaMemcpyHostToDevice, s));
+    if (ud_h) TAM_CUDA(cudaMemcpyAsync(Ud.p, ud_h, n3 * 8, cudaMemcpyHostToDevice, s));
+    TAM_CUDA(cudaMemcpyAsync(D.p, dmask_h, (size_t)n_nodes, cudaMemcpyHostToDevice, s));
+    tam_matrix_s* K = assemble_elasticity(n_nodes, X.p, n_cells, npc, C.p, M.p, n_mat, props.p, Td.p, T_ref, Bd.p, D.p,
+                                          Ud.p, rhs.p, s);
+    int st = TAM_OK;
+    try {
+      amg_params prm;
+      if (params) prm = *params; else amg_params_default(&prm);
+      tam_amg_s* H = amg_build(K, X.p, prm, s);
+      try {
+        u.zero();
+        st = pcg_solve(H, rhs.p, u.p, rtol, 0.0, max_iter, iters_out, rel_out, s);
+      } catch (...) {
+        delete H;
+        throw;
+      }
+      delete H;
+    } catch (...) {
+      delete K;
+      throw;
+    }
+    delete K;
+    TAM_CUDA(cudaMemcpyAsync(u_h, u.p, n3 * 8, cudaMemcpyDeviceToHost, s));
+    TAM_CUDA(cudaStreamSynchronize(s));
+    if (st != TAM_OK) set_last_error("tam_solve_elasticity_host: PCG did not reach the tolerance");
+    return st;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Opaque handle types behind the C ABI and the internal entry points that
+// the C ABI wraps.
+#pragma once
+
+#include <vector>
+
+#include "sparse.cuh"
+
+struct tam_matrix_s {
+  int n_nodes = 0;
+  tam::Bsr A;                          // 3x3 blocks, Dirichlet rows are identity rows
+  tam::Sell S;                         // SELL-32 copy used by every SpMV with K
+  tam::DBuf<unsigned char> dmask;      // Dirichlet mask [n_nodes]
+};
+
+namespace tam {
+
+// Device-side state of one PCG solve (one per hierarchy).
+struct PcgScalars {
+  double rho;       // r . z of the current iterate
+  double alpha, beta;
+  double rr;        // ||r||^2
+  double tol2;      // stop when rr <= tol2
+  double bb;        // ||b||^2
+  int iter;
+  int max_iter;
+  int stop;         // nonzero: every solver kernel returns at entry
+  int status;       // TAM_OK or a TAM_ERR_* code
+};
+
+struct Level {
+  int n_rows = 0;     // block rows
+  int bs = 0;         // block size of A on this level
+  int kdim = 0;       // near-nullspace columns (block size of the next level)
+  const Bsr* A = nullptr;   // level 0: the matrix handle's K
+  const Sell* AS = nullptr;
+  Bsr A_own;
+  Sell AS_own;
+  DBuf<double> dinv;        // point-Jacobi inverse diagonal [n_rows*bs] (0 on zero diagonals)
+  DBuf<double> consts;      // [0] lambda_max, [1] omega, [2..] Chebyshev (c_d, c_r) per step
+  DBuf<int> agg;            // aggregate id per block row (-1 = none)
+  int n_agg = 0;
+  Bsr Pt, P, R;             // tentative prolongator, smoothed prolongator, R = P^T
+  Sell PS, RS;
+  // V-cycle work vectors (n_rows*bs each)
+  DBuf<double> b, xa, xb, d, t, y;  // y: the level's V-cycle result (never an internal buffer)
+  double lambda_host = 0.0;
+};
+
+}  // namespace tam
+
+struct tam_amg_s {
+  tam_matrix_s* K = nullptr;
+  amg_params prm{};
+  std::vector<tam::Level> levels;
+  int n_coarse = 0;                      // dense coarsest size (scalars)
+  tam::DBuf<double> coarse_inv;          // [n_coarse * n_coarse]
+  // PCG workspace
+  tam::DBuf<double> r, z, p, q;
+  tam::DBuf<tam::PcgScalars> sc;
+  tam::DBuf<double> partials;            // grid-reduction partials
+  tam::DBuf<unsigned int> ticket;
+  int max_grid = 0;
+  // captured V-cycle + iteration graph (rebuilt when buffers change)
+  cudaGraphExec_t iter_exec = nullptr;
+  const double* graph_b = nullptr;
+  double* graph_x = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  ~tam_amg_s();
+};
+
+namespace tam {
+
+tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells, int npc, const int* cells,
+                                  const int* mat, int n_mat, const double* props, const double* T,
+                                  double T_ref, const double* body, const unsigned char* dmask,
+                                  const double* ud, double* rhs, cudaStream_t s);
+
+tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& prm, cudaStream_t s);
+
+// One V-cycle z = M^-1 r on level 0 (r, z device vectors of the fine size).
+void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s);
+
+int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
+              double* rel, cudaStream_t s);
+
+void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s);
+
+}  // namespace tam

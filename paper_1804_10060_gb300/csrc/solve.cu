@@ -1,0 +1,391 @@
+// AMG V-cycle and preconditioned CG (paper Sec. 2.1: CG with a preconditioner
+// that bounds the condition number independently of h; Sec. 5.1: smoothed
+// aggregation with Chebyshev smoothing).
+//
+// V-cycle on level l (A_l, D_l, Chebyshev on D^-1 A over [lo, hi] lambda):
+//   x  = Cheb(A, b, x = 0)           pre-smoothing, `degree` steps
+//   t  = b - A x                     residual
+//   b' = R t,  x' = V-cycle(l+1, b') restriction + coarse correction
+//   x += P x'                        prolongation
+//   x  = Cheb(A, b, x)               post-smoothing (same polynomial)
+// and the coarsest level applies its dense inverse.  Each Chebyshev step is
+// ONE fused SpMV kernel: res = D^-1 (b - A x), d = c_d d + c_r res, x' = x + d.
+//
+// PCG keeps every scalar on the device; kernels after a stop (convergence,
+// breakdown, NaN, iteration cap) return at entry, so a fixed-length CUDA
+// graph of one iteration can be replayed without host round trips.
+#include <algorithm>
+#include <cmath>
+
+#include "handles.cuh"
+
+namespace tam {
+namespace {
+
+constexpr int TPB = 256;
+
+__global__ void cheb_first_zero_kernel(const double* __restrict__ b, const double* __restrict__ dinv,
+                                       const double* __restrict__ consts, double* __restrict__ d,
+                                       double* __restrict__ x, long long N, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  const double cr = consts[3];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double di = cr * dinv[i] * b[i];
+    d[i] = di;
+    x[i] = di;
+  }
+}
+
+// One Chebyshev step fused into the SpMV of x.
+template <int BR>
+struct EpiCheb {
+  const double* b;
+  const double* x;     // current iterate (own rows)
+  const double* dinv;
+  const double* coef;  // (c_d, c_r) of this step
+  double* d;
+  double* xn;          // next iterate (other buffer)
+  int n_rows;
+  const int* stop;
+  __device__ bool skip() const { return stop && *stop; }
+  __device__ void operator()(int row, const double (&acc)[BR], double*) const {
+    if (row >= n_rows) return;
+    const double cd = coef[0], cr = coef[1];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+      size_t i = (size_t)row * BR + r;
+      double res = dinv[i] * (b[i] - acc[r]);
+      double di = cd != 0.0 ? cd * d[i] + cr * res : cr * res;
+      d[i] = di;
+      xn[i] = x[i] + di;
+    }
+  }
+};
+
+// y = Ainv b (dense), warp per row
+__global__ void dense_gemv_kernel(const double* __restrict__ A, const double* __restrict__ b, double* __restrict__ y,
+                                  int N, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= N) return;
+  const double* a = A + (size_t)row * N;
+  double s = 0.0;
+  for (int j = lane; j < N; j += 32) s = fma(a[j], b[j], s);
+  s = warp_sum(s);
+  if (lane == 0) y[row] = s;
+}
+
+// ---------------------------------------------------------------------------
+// PCG kernels
+// ---------------------------------------------------------------------------
+__global__ void pcg_start_kernel(const double* __restrict__ b, long long N, GridReduce gr, PcgScalars* sc,
+                                 double rtol, double atol, int max_iter) {
+  __shared__ double sh[32];
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    acc[0] += b[i] * b[i];
+  double tot[1];
+  if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) {
+    sc->bb = tot[0];
+    double t = fmax(rtol * sqrt(tot[0]), atol);
+    sc->tol2 = t * t;
+    sc->iter = 0;
+    sc->max_iter = max_iter;
+    sc->stop = 0;
+    sc->status = TAM_OK;
+    sc->rho = sc->alpha = sc->beta = 0.0;
+    sc->rr = 0.0;
+  }
+}
+
+// r = b - K x and ||r||^2 -> stop if already converged
+template <int BR>
+struct EpiInitResidual {
+  const double* b;
+  double* r;
+  int n_rows;
+  GridReduce gr;
+  PcgScalars* sc;
+  __device__ bool skip() const { return false; }
+  __device__ void operator()(int row, const double (&acc)[BR], double* sh) const {
+    double s[1] = {0.0};
+    if (row < n_rows)
+#pragma unroll
+      for (int k = 0; k < BR; ++k) {
+        size_t i = (size_t)row * BR + k;
+        double v = b[i] - acc[k];
+        r[i] = v;
+        s[0] += v * v;
+      }
+    double tot[1];
+    if (grid_reduce<1>(gr, s, tot, sh) && threadIdx.x == 0) {
+      sc->rr = tot[0];
+      if (!isfinite(tot[0])) { sc->status = TAM_ERR_NAN; sc->stop = 1; }
+      else if (tot[0] <= sc->tol2) sc->stop = 1;
+      else if (sc->max_iter <= 0) { sc->status = TAM_ERR_NOT_CONVERGED; sc->stop = 1; }
+    }
+  }
+};
+
+// rho = r . z (> 0 for an SPD preconditioner);  first call also sets p = z
+__global__ void pcg_rz_kernel(const double* __restrict__ r, const double* __restrict__ z, double* __restrict__ p,
+                              long long N, GridReduce gr, PcgScalars* sc, int first) {
+  __shared__ double sh[32];
+  if (sc->stop) return;
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    acc[0] += r[i] * z[i];
+    if (first) p[i] = z[i];
+  }
+  double tot[1];
+  if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) {
+    const double rz = tot[0];
+    if (!isfinite(rz)) { sc->status = TAM_ERR_NAN; sc->stop = 1; return; }
+    if (!(rz > 0.0)) { sc->status = TAM_ERR_INDEFINITE_PRECOND; sc->stop = 1; return; }
+    if (!first) sc->beta = rz / sc->rho;
+    sc->rho = rz;
+  }
+}
+
+// q = K p and p . q -> alpha
+template <int BR>
+struct EpiPq {
+  const double* p;
+  double* q;
+  int n_rows;
+  GridReduce gr;
+  PcgScalars* sc;
+  __device__ bool skip() const { return sc->stop; }
+  __device__ void operator()(int row, const double (&acc)[BR], double* sh) const {
+    double s[1] = {0.0};
+    if (row < n_rows)
+#pragma unroll
+      for (int k = 0; k < BR; ++k) {
+        size_t i = (size_t)row * BR + k;
+        q[i] = acc[k];
+        s[0] += p[i] * acc[k];
+      }
+    double tot[1];
+    if (grid_reduce<1>(gr, s, tot, sh) && threadIdx.x == 0) {
+      const double pq = tot[0];
+      if (!isfinite(pq)) { sc->status = TAM_ERR_NAN; sc->stop = 1; }
+      else if (!(pq > 0.0)) { sc->status = TAM_ERR_BREAKDOWN; sc->stop = 1; }
+      else sc->alpha = sc->rho / pq;
+    }
+  }
+};
+
+// x += alpha p; r -= alpha q; ||r||^2; convergence / cap
+__global__ void pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                                  const double* __restrict__ q, long long N, GridReduce gr, PcgScalars* sc) {
+  __shared__ double sh[32];
+  if (sc->stop) return;
+  const double a = sc->alpha;
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    double ri = r[i] - a * q[i];
+    r[i] = ri;
+    acc[0] += ri * ri;
+  }
+  double tot[1];
+  if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) {
+    sc->rr = tot[0];
+    sc->iter += 1;
+    if (!isfinite(tot[0])) { sc->status = TAM_ERR_NAN; sc->stop = 1; }
+    else if (tot[0] <= sc->tol2) sc->stop = 1;
+    else if (sc->iter >= sc->max_iter) { sc->status = TAM_ERR_NOT_CONVERGED; sc->stop = 1; }
+  }
+}
+
+__global__ void pcg_direction_kernel(const double* __restrict__ z, double* __restrict__ p, long long N,
+                                     const PcgScalars* sc) {
+  if (sc->stop) return;
+  const double beta = sc->beta;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// final ||b - K x||^2
+template <int BR>
+struct EpiResNorm {
+  const double* b;
+  int n_rows;
+  GridReduce gr;
+  double* out;
+  __device__ bool skip() const { return false; }
+  __device__ void operator()(int row, const double (&acc)[BR], double* sh) const {
+    double s[1] = {0.0};
+    if (row < n_rows)
+#pragma unroll
+      for (int k = 0; k < BR; ++k) {
+        double v = b[(size_t)row * BR + k] - acc[k];
+        s[0] += v * v;
+      }
+    double tot[1];
+    if (grid_reduce<1>(gr, s, tot, sh) && threadIdx.x == 0) *out = tot[0];
+  }
+};
+
+unsigned vec_grid(long long N) { return std::min<unsigned>(grid_for(N, TPB), 152u * 8u); }
+
+// ---------------------------------------------------------------------------
+// Dispatch on block shapes (3x3, 6x6 for A; 3x6, 6x3, 6x6, 3x3 for P and R)
+// ---------------------------------------------------------------------------
+void cheb_step(const Level& L, const double* b, const double* x, double* d, double* xn, int step, const int* stop,
+               cudaStream_t s) {
+  const double* coef = L.consts.p + 2 + 2 * step;
+  if (L.bs == 3)
+    sell_spmv<3, 3>(*L.AS, x, EpiCheb<3>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
+  else
+    sell_spmv<6, 6>(*L.AS, x, EpiCheb<6>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
+}
+
+void residual(const Level& L, const double* b, const double* x, double* t, const int* stop, cudaStream_t s) {
+  if (L.bs == 3)
+    sell_spmv<3, 3>(*L.AS, x, EpiResidual<3>{b, t, L.n_rows, stop}, s);
+  else
+    sell_spmv<6, 6>(*L.AS, x, EpiResidual<6>{b, t, L.n_rows, stop}, s);
+}
+
+void restrict_to(const Level& L, const double* t, double* bc, const int* stop, cudaStream_t s) {
+  // R: rows = coarse nodes (kdim), cols = fine nodes (bs)
+  const int nr = L.RS.n_rows;
+  if (L.kdim == 6 && L.bs == 3) sell_spmv<6, 3>(L.RS, t, EpiStore<6>{bc, nr, stop}, s);
+  else if (L.kdim == 6 && L.bs == 6) sell_spmv<6, 6>(L.RS, t, EpiStore<6>{bc, nr, stop}, s);
+  else sell_spmv<3, 3>(L.RS, t, EpiStore<3>{bc, nr, stop}, s);
+}
+
+void prolong_add(const Level& L, const double* xc, double* x, const int* stop, cudaStream_t s) {
+  const int nr = L.PS.n_rows;
+  if (L.kdim == 6 && L.bs == 3) sell_spmv<3, 6>(L.PS, xc, EpiAdd<3>{x, nr, stop}, s);
+  else if (L.kdim == 6 && L.bs == 6) sell_spmv<6, 6>(L.PS, xc, EpiAdd<6>{x, nr, stop}, s);
+  else sell_spmv<3, 3>(L.PS, xc, EpiAdd<3>{x, nr, stop}, s);
+}
+
+// V-cycle on level l with rhs b; the result lands in *out (level 0: caller's z)
+void vcycle_level(tam_amg_s* H, int l, const double* b, double* out, const int* stop, cudaStream_t s) {
+  Level& L = H->levels[l];
+  const long long N = (long long)L.n_rows * L.bs;
+  if (l == (int)H->levels.size() - 1) {
+    dense_gemv_kernel<<<grid_for((long long)H->n_coarse * 32, TPB), TPB, 0, s>>>(H->coarse_inv.p, b, out,
+                                                                                  H->n_coarse, stop);
+    TAM_LAUNCH_CHECK();
+    return;
+  }
+  const int deg = H->prm.smoother_degree;
+  double* xa = L.xa.p;
+  double* xb = L.xb.p;
+  // pre-smoothing from zero
+  cheb_first_zero_kernel<<<vec_grid(N), TPB, 0, s>>>(b, L.dinv.p, L.consts.p, L.d.p, xa, N, stop);
+  TAM_LAUNCH_CHECK();
+  for (int k = 1; k < deg; ++k) {
+    cheb_step(L, b, xa, L.d.p, xb, k, stop, s);
+    std::swap(xa, xb);
+  }
+  residual(L, b, xa, L.t.p, stop, s);
+  Level& C = H->levels[l + 1];
+  restrict_to(L, L.t.p, C.b.p, stop, s);
+  double* xc = C.y.p;
+  vcycle_level(H, l + 1, C.b.p, xc, stop, s);
+  prolong_add(L, xc, xa, stop, s);
+  // post-smoothing from x
+  for (int k = 0; k < deg; ++k) {
+    double* dst = (k == deg - 1) ? out : xb;
+    cheb_step(L, b, xa, L.d.p, dst, k, stop, s);
+    xb = xa;
+    xa = dst;
+  }
+}
+
+void spmv_outer_pq(tam_amg_s* H, cudaStream_t s) {
+  GridReduce gr{H->partials.p, H->ticket.p};
+  sell_spmv<3, 3>(H->K->S, H->p.p, EpiPq<3>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s);
+}
+
+void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
+  const long long N = (long long)H->K->n_nodes * 3;
+  GridReduce gr{H->partials.p, H->ticket.p};
+  const int* stop = &H->sc.p->stop;
+  spmv_outer_pq(H, s);
+  pcg_update_kernel<<<vec_grid(N), TPB, 0, s>>>(x, H->r.p, H->p.p, H->q.p, N, gr, H->sc.p);
+  TAM_LAUNCH_CHECK();
+  vcycle_level(H, 0, H->r.p, H->z.p, stop, s);
+  pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, H->sc.p, 0);
+  TAM_LAUNCH_CHECK();
+  pcg_direction_kernel<<<vec_grid(N), TPB, 0, s>>>(H->z.p, H->p.p, N, H->sc.p);
+  TAM_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s) {
+  sell_spmv<3, 3>(K->S, x, EpiStore<3>{y, K->n_nodes, nullptr}, s);
+}
+
+void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s) {
+  vcycle_level(H, 0, r, z, stop, s);
+}
+
+int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
+              double* rel, cudaStream_t s) {
+  TAM_CHECK(b && x && rtol >= 0.0 && atol >= 0.0 && max_iter >= 0, TAM_ERR_INVALID_ARG, "amg_pcg_solve: bad argument");
+  const long long N = (long long)H->K->n_nodes * 3;
+  GridReduce gr{H->partials.p, H->ticket.p};
+  PcgScalars* sc = H->sc.p;
+  pcg_start_kernel<<<vec_grid(N), TPB, 0, s>>>(b, N, gr, sc, rtol, atol, max_iter);
+  TAM_LAUNCH_CHECK();
+  sell_spmv<3, 3>(H->K->S, x, EpiInitResidual<3>{b, H->r.p, H->K->n_nodes, gr, sc}, s);
+  vcycle_level(H, 0, H->r.p, H->z.p, &sc->stop, s);
+  pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, sc, 1);
+  TAM_LAUNCH_CHECK();
+  // one iteration as a CUDA graph, rebuilt if the target vector changed
+  if (!H->iter_exec || H->graph_x != x || H->graph_stream != s) {
+    if (H->iter_exec) {
+      cudaGraphExecDestroy(H->iter_exec);
+      H->iter_exec = nullptr;
+    }
+    cudaStream_t cs;
+    TAM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    TAM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_iteration(H, x, cs);
+    } catch (...) {
+      cudaStreamEndCapture(cs, &g);
+      cudaStreamDestroy(cs);
+      throw;
+    }
+    TAM_CUDA(cudaStreamEndCapture(cs, &g));
+    TAM_CUDA(cudaGraphInstantiate(&H->iter_exec, g, 0));
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    H->graph_x = x;
+    H->graph_stream = s;
+  }
+  HostScalars& hs = host_scalars();
+  const int chunk = 8;
+  int launched = 0;
+  while (launched < max_iter) {
+    int todo = std::min(chunk, max_iter - launched);
+    for (int i = 0; i < todo; ++i) TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
+    launched += todo;
+    TAM_CUDA(cudaMemcpyAsync(hs.ll, &sc->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TAM_CUDA(cudaStreamSynchronize(s));
+    if (*reinterpret_cast<int*>(hs.ll)) break;
+  }
+  // final true residual
+  DBuf<double> rn(1, s);
+  sell_spmv<3, 3>(H->K->S, x, EpiResNorm<3>{b, H->K->n_nodes, gr, rn.p}, s);
+  PcgScalars host;
+  TAM_CUDA(cudaMemcpyAsync(&host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  double rr = read_back_double(rn.p, s);  // synchronises the stream
+  if (iters) *iters = host.iter;
+  double nb = std::sqrt(host.bb);
+  if (rel) *rel = nb > 0 ? std::sqrt(rr) / nb : std::sqrt(rr);
+  int status = host.status;
+  if (status == TAM_OK && !host.stop) status = TAM_ERR_NOT_CONVERGED;
+  return status;
+}
+
+}  // namespace tam

@@ -1,0 +1,343 @@
+// Block-sparse building blocks of the AMG setup: SELL-32 conversion, block
+// transpose and the block SpGEMM C = X * Y used for A P_tent and R (A P).
+#include "sparse.cuh"
+
+namespace tam {
+
+// ---------------------------------------------------------------------------
+// SELL-32 conversion
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void sell_slice_len_kernel(const int* __restrict__ row_ptr, int n_rows, int n_slices,
+                                      int* __restrict__ len) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slices) return;
+  int m = 0;
+  int r1 = min(32 * s + 32, n_rows);
+  for (int r = 32 * s; r < r1; ++r) m = max(m, row_ptr[r + 1] - row_ptr[r]);
+  len[s] = m;
+}
+
+// One thread per (slice, lane).  Pads a row with zero blocks pointing at the
+// row's last real column (keeps the padded x reads local).
+__global__ void sell_fill_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
+                                 const double* __restrict__ vals, int n_rows, int n_slices, int bb,
+                                 const int* __restrict__ slice_ptr, int* __restrict__ scols,
+                                 double* __restrict__ svals, bool with_pattern) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = t >> 5, lane = t & 31;
+  if (s >= n_slices) return;
+  int row = t;
+  int rp = 0, len = 0;
+  if (row < n_rows) {
+    rp = row_ptr[row];
+    len = row_ptr[row + 1] - rp;
+  }
+  int k0 = slice_ptr[s], K = slice_ptr[s + 1] - k0;
+  int lastc = len > 0 ? col_idx[rp + len - 1] : 0;
+  for (int k = 0; k < K; ++k) {
+    size_t slot = (size_t)(k0 + k);
+    if (with_pattern) scols[slot * 32 + lane] = k < len ? col_idx[rp + k] : lastc;
+    for (int e = 0; e < bb; ++e)
+      svals[(slot * bb + e) * 32 + lane] = k < len ? vals[((size_t)rp + k) * bb + e] : 0.0;
+  }
+}
+
+}  // namespace
+
+void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s) {
+  TAM_CHECK(A.n_cols > 0, TAM_ERR_INTERNAL, "SELL of a matrix without columns");
+  S.n_rows = A.n_rows;
+  S.br = A.br;
+  S.bc = A.bc;
+  S.n_slices = (A.n_rows + 31) / 32;
+  S.slice_ptr = DBuf<int>((size_t)S.n_slices + 1, s);
+  sell_slice_len_kernel<<<grid_for(S.n_slices, 256), 256, 0, s>>>(A.row_ptr.p, A.n_rows, S.n_slices,
+                                                                  S.slice_ptr.p);
+  TAM_LAUNCH_CHECK();
+  exclusive_scan_i32(S.slice_ptr.p, S.slice_ptr.p, S.n_slices, s);
+  S.n_slots = read_back_int(S.slice_ptr.p + S.n_slices, s);
+  S.cols = DBuf<int>((size_t)S.n_slots * 32, s);
+  S.vals = DBuf<double>((size_t)S.n_slots * 32 * A.block_elems(), s);
+  sell_fill_kernel<<<grid_for((long long)S.n_slices * 32, 256), 256, 0, s>>>(
+      A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, S.n_slices, (int)A.block_elems(),
+      S.slice_ptr.p, S.cols.p, S.vals.p, true);
+  TAM_LAUNCH_CHECK();
+}
+
+void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s) {
+  sell_fill_kernel<<<grid_for((long long)S.n_slices * 32, 256), 256, 0, s>>>(
+      A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, S.n_slices, (int)A.block_elems(),
+      S.slice_ptr.p, S.cols.p, S.vals.p, false);
+  TAM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// Transpose
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void count_cols_kernel(const int* __restrict__ col_idx, long long nnzb, int* __restrict__ cnt) {
+  long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nnzb) atomicAdd(&cnt[col_idx[b]], 1);
+}
+
+__global__ void transpose_scatter_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
+                                         int n_rows, const int* __restrict__ rt_ptr, int* __restrict__ cursor,
+                                         int* __restrict__ tkey, int* __restrict__ tsrc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rows) return;
+  for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+    int c = col_idx[b];
+    int pos = rt_ptr[c] + atomicAdd(&cursor[c], 1);
+    tkey[pos] = i;
+    tsrc[pos] = b;
+  }
+}
+
+// Warp per transposed row: the rank of each (unique) key among its row gives
+// its sorted slot -- deterministic regardless of the scatter order.
+__global__ void transpose_rank_kernel(const int* __restrict__ rt_ptr, int n_rt, const int* __restrict__ tkey,
+                                      const int* __restrict__ tsrc, int* __restrict__ out_col,
+                                      int* __restrict__ out_src) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n_rt) return;
+  int s = rt_ptr[w], e = rt_ptr[w + 1];
+  for (int p = s + lane; p < e; p += 32) {
+    int key = tkey[p];
+    int rank = 0;
+    for (int q = s; q < e; ++q) rank += (tkey[q] < key);
+    out_col[s + rank] = key;
+    out_src[s + rank] = tsrc[p];
+  }
+}
+
+__global__ void transpose_vals_kernel(const double* __restrict__ vals, const int* __restrict__ src,
+                                      long long nnzb, int br, int bc, double* __restrict__ out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long bb = (long long)br * bc;
+  if (t >= nnzb * bb) return;
+  long long b = t / bb;
+  int e = (int)(t % bb);
+  int r = e / br, c = e % br;  // output block is bc x br: element (r, c) = input (c, r)
+  out[t] = vals[(size_t)src[b] * bb + (size_t)c * bc + r];
+}
+
+}  // namespace
+
+void bsr_transpose(const Bsr& A, Bsr& R, cudaStream_t s) {
+  R.n_rows = A.n_cols;
+  R.n_cols = A.n_rows;
+  R.br = A.bc;
+  R.bc = A.br;
+  R.nnzb = A.nnzb;
+  R.row_ptr = DBuf<int>((size_t)R.n_rows + 1, s);
+  R.row_ptr.zero();
+  count_cols_kernel<<<grid_for(A.nnzb, 256), 256, 0, s>>>(A.col_idx.p, A.nnzb, R.row_ptr.p);
+  TAM_LAUNCH_CHECK();
+  exclusive_scan_i32(R.row_ptr.p, R.row_ptr.p, R.n_rows, s);
+  DBuf<int> cursor((size_t)R.n_rows, s), tkey((size_t)A.nnzb, s), tsrc((size_t)A.nnzb, s), src((size_t)A.nnzb, s);
+  cursor.zero();
+  transpose_scatter_kernel<<<grid_for(A.n_rows, 256), 256, 0, s>>>(A.row_ptr.p, A.col_idx.p, A.n_rows,
+                                                                  R.row_ptr.p, cursor.p, tkey.p, tsrc.p);
+  TAM_LAUNCH_CHECK();
+  R.col_idx = DBuf<int>((size_t)A.nnzb, s);
+  transpose_rank_kernel<<<grid_for((long long)R.n_rows * 32, 256), 256, 0, s>>>(R.row_ptr.p, R.n_rows, tkey.p,
+                                                                                tsrc.p, R.col_idx.p, src.p);
+  TAM_LAUNCH_CHECK();
+  R.vals = DBuf<double>((size_t)A.nnzb * A.block_elems(), s);
+  transpose_vals_kernel<<<grid_for(A.nnzb * (long long)A.block_elems(), 256), 256, 0, s>>>(
+      A.vals.p, src.p, A.nnzb, A.br, A.bc, R.vals.p);
+  TAM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// SpGEMM C = X Y.  Symbolic: one warp per row inserts the candidate columns
+// into a shared-memory hash set (open addressing), counts, and in the fill
+// pass compacts and bitonic-sorts them.  Numeric: one warp per row
+// accumulates the row's output blocks in shared memory, a window of columns
+// at a time; lanes own block ELEMENTS, so accumulation needs no atomics.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int SG_WARPS = 4;
+constexpr int HT = 2048;            // hash slots per warp
+constexpr int HT_MAX = 1536;        // max unique columns per row (load 0.75)
+constexpr int ACC_BYTES = 16384;    // numeric accumulator per warp
+
+__device__ __forceinline__ bool ht_insert(int* tab, int col) {
+  unsigned h = ((unsigned)col * 2654435761u) & (HT - 1);
+  int key = col + 1;
+  for (int probe = 0; probe < HT; ++probe) {
+    int prev = atomicCAS(&tab[h], 0, key);
+    if (prev == 0) return true;
+    if (prev == key) return false;
+    h = (h + 1) & (HT - 1);
+  }
+  return false;  // table full: caught by the count check
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(SG_WARPS * 32)
+spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, int n_rows,
+                       const int* __restrict__ yrp, const int* __restrict__ yci,
+                       int* __restrict__ row_cnt, const int* __restrict__ crp, int* __restrict__ cci,
+                       int* __restrict__ overflow) {
+  __shared__ int tab_all[SG_WARPS][HT];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * SG_WARPS + wid;
+  if (row >= n_rows) return;
+  int* tab = tab_all[wid];
+  for (int i = lane; i < HT; i += 32) tab[i] = 0;
+  __syncwarp();
+  int ins = 0;
+  const int xs = xrp[row], xe = xrp[row + 1];
+  for (int p = xs + lane; p < xe; p += 32) {
+    int j = xci[p];
+    for (int q = yrp[j]; q < yrp[j + 1]; ++q) ins += ht_insert(tab, yci[q]) ? 1 : 0;
+  }
+  __syncwarp();
+  int cnt = warp_sum_i(ins);
+  if (cnt > HT_MAX) {
+    if (lane == 0) atomicExch(overflow, 1);
+    if (!FILL && lane == 0) row_cnt[row] = 0;
+    return;
+  }
+  if (!FILL) {
+    if (lane == 0) row_cnt[row] = cnt;
+    return;
+  }
+  // compact non-empty slots (decoded) to the front, pad, sort
+  int base = 0;
+  for (int i0 = 0; i0 < HT; i0 += 32) {
+    int v = tab[i0 + lane];
+    bool keep = v != 0;
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();
+    if (keep) tab[base + __popc(m & ((1u << lane) - 1u))] = v - 1;
+    base += __popc(m);
+    __syncwarp();
+  }
+  int n2 = next_pow2(cnt);
+  for (int i = cnt + lane; i < n2; i += 32) tab[i] = 0x7fffffff;
+  __syncwarp();
+  warp_bitonic_sort<false>(tab, nullptr, n2);
+  const int c0 = crp[row];
+  for (int i = lane; i < cnt; i += 32) cci[c0 + i] = tab[i];
+}
+
+// dynamic smem: SG_WARPS * (ACC_BYTES + wcap*4)
+template <int M, int K, int N>
+__global__ void __launch_bounds__(SG_WARPS * 32)
+spgemm_numeric_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
+                      int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
+                      const double* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
+                      double* __restrict__ cv) {
+  constexpr int MN = M * N;
+  constexpr int W = ACC_BYTES / (MN * 8);
+  extern __shared__ double sm[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * SG_WARPS + wid;
+  if (row >= n_rows) return;
+  double* acc = sm + (size_t)wid * (ACC_BYTES / 8);
+  int* wcols = reinterpret_cast<int*>(sm + (size_t)SG_WARPS * (ACC_BYTES / 8)) + wid * W;
+  const int cs = crp[row], ce = crp[row + 1];
+  const int xs = xrp[row], xe = xrp[row + 1];
+  for (int w0 = cs; w0 < ce; w0 += W) {
+    const int wn = min(W, ce - w0);
+    for (int i = lane; i < wn; i += 32) wcols[i] = cci[w0 + i];
+    for (int i = lane; i < wn * MN; i += 32) acc[i] = 0.0;
+    __syncwarp();
+    const int clo = wcols[0], chi = wcols[wn - 1];
+    for (int p = xs; p < xe; ++p) {
+      const int j = xci[p];
+      const double* xb = xv + (size_t)p * M * K;
+      int qs = yrp[j], qe = yrp[j + 1];
+      // first entry of Y row j with col >= clo
+      {
+        int lo = qs, hi = qe;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (yci[mid] < clo) lo = mid + 1; else hi = mid;
+        }
+        qs = lo;
+      }
+      for (int q = qs; q < qe; ++q) {
+        const int c = yci[q];
+        if (c > chi) break;
+        // position of c in the window (present by construction)
+        int lo = 0, hi = wn - 1;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (wcols[mid] < c) lo = mid + 1; else hi = mid;
+        }
+        const double* yb = yv + (size_t)q * K * N;
+        for (int e = lane; e < MN; e += 32) {
+          const int r = e / N, s2 = e % N;
+          double a = acc[lo * MN + e];
+#pragma unroll
+          for (int t = 0; t < K; ++t) a = fma(xb[r * K + t], yb[t * N + s2], a);
+          acc[lo * MN + e] = a;
+        }
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = acc[i];
+    __syncwarp();
+  }
+}
+
+template <int M, int K, int N>
+void launch_numeric(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
+  constexpr int W = ACC_BYTES / (M * N * 8);
+  size_t smem = (size_t)SG_WARPS * (ACC_BYTES + W * 4);
+  static bool attr_set = false;
+  if (!attr_set) {
+    TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_kernel<M, K, N>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  spgemm_numeric_kernel<M, K, N><<<grid_for(X.n_rows, SG_WARPS), SG_WARPS * 32, smem, s>>>(
+      X.row_ptr.p, X.col_idx.p, X.vals.p, X.n_rows, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, C.row_ptr.p,
+      C.col_idx.p, C.vals.p);
+  TAM_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
+  TAM_CHECK(X.bc == Y.br && X.n_cols == Y.n_rows, TAM_ERR_INTERNAL, "spgemm: shape mismatch");
+  C.n_rows = X.n_rows;
+  C.n_cols = Y.n_cols;
+  C.br = X.br;
+  C.bc = Y.bc;
+  C.row_ptr = DBuf<int>((size_t)C.n_rows + 1, s);
+  DBuf<int> overflow(1, s);
+  overflow.zero();
+  unsigned grid = grid_for(X.n_rows, SG_WARPS);
+  spgemm_symbolic_kernel<false><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
+                                                             Y.col_idx.p, C.row_ptr.p, nullptr, nullptr,
+                                                             overflow.p);
+  TAM_LAUNCH_CHECK();
+  exclusive_scan_i32(C.row_ptr.p, C.row_ptr.p, C.n_rows, s);
+  C.nnzb = read_back_int(C.row_ptr.p + C.n_rows, s);
+  TAM_CHECK(read_back_int(overflow.p, s) == 0, TAM_ERR_INTERNAL,
+            "spgemm: an output row exceeds 1536 blocks");
+  C.col_idx = DBuf<int>((size_t)C.nnzb, s);
+  C.vals = DBuf<double>((size_t)C.nnzb * C.block_elems(), s);
+  spgemm_symbolic_kernel<true><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
+                                                            Y.col_idx.p, nullptr, C.row_ptr.p, C.col_idx.p,
+                                                            overflow.p);
+  TAM_LAUNCH_CHECK();
+  const int m = X.br, k = X.bc, n = Y.bc;
+  if (m == 3 && k == 3 && n == 6) launch_numeric<3, 3, 6>(X, Y, C, s);
+  else if (m == 6 && k == 3 && n == 6) launch_numeric<6, 3, 6>(X, Y, C, s);
+  else if (m == 6 && k == 6 && n == 6) launch_numeric<6, 6, 6>(X, Y, C, s);
+  else if (m == 3 && k == 3 && n == 3) launch_numeric<3, 3, 3>(X, Y, C, s);
+  else if (m == 6 && k == 6 && n == 3) launch_numeric<6, 6, 3>(X, Y, C, s);
+  else if (m == 3 && k == 6 && n == 6) launch_numeric<3, 6, 6>(X, Y, C, s);
+  else throw Error(TAM_ERR_UNSUPPORTED, "spgemm: block shape not instantiated");
+}
+
+}  // namespace tam

@@ -1,0 +1,301 @@
+"""Python binding of libthermoamg.so (C ABI in include/thermoamg.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions keep the C names; device arrays are torch CUDA tensors (float64,
+int32 or uint8, contiguous) and `stream` is a torch.cuda.Stream (default: the
+current stream).  Importing this module loads the library and raises
+ImportError when it has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libthermoamg.so")
+
+TAM_OK = 0
+STATUS_NAMES = {
+    0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "DEGENERATE_CELL", -5: "NOT_CONVERGED",
+    -6: "BREAKDOWN", -7: "INDEFINITE_PRECOND", -8: "NAN", -9: "INTERNAL", -10: "UNSUPPORTED",
+}
+
+
+class TamError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class AmgParams(ctypes.Structure):
+    _fields_ = [
+        ("strength_theta", ctypes.c_double),
+        ("smoother_degree", ctypes.c_int),
+        ("cheb_lo", ctypes.c_double),
+        ("cheb_hi", ctypes.c_double),
+        ("eig_iters", ctypes.c_int),
+        ("coarse_max_dofs", ctypes.c_int),
+        ("max_levels", ctypes.c_int),
+        ("use_rotations", ctypes.c_int),
+        ("level_precision", ctypes.c_int),
+    ]
+
+
+_vp, _i, _d, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+_pi, _pd, _pll = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)
+
+_SIGNATURES = {
+    "tam_last_error": ([], ctypes.c_char_p),
+    "fem_assemble_elasticity": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp,
+                                 ctypes.POINTER(_vp), _vp, _vp], _i),
+    "tam_matrix_info": ([_vp, _pi, _pll, _pi], _i),
+    "tam_matrix_export_bsr": ([_vp, _vp, _vp, _vp, _vp], _i),
+    "tam_matrix_spmv": ([_vp, _vp, _vp, _vp], _i),
+    "tam_matrix_destroy": ([_vp], _i),
+    "amg_params_default": ([ctypes.POINTER(AmgParams)], _i),
+    "amg_setup": ([_vp, _vp, ctypes.POINTER(AmgParams), ctypes.POINTER(_vp), _vp], _i),
+    "amg_info": ([_vp, _pi, _pll, _pll, _pi, _pd, _pd], _i),
+    "amg_level_aggregates": ([_vp, _i, _vp, _vp], _i),
+    "amg_level_export": ([_vp, _i, _i, _pi, _pi, _pi, _pi, _pll, _vp, _vp, _vp, _vp], _i),
+    "amg_vcycle": ([_vp, _vp, _vp, _vp], _i),
+    "amg_pcg_solve": ([_vp, _vp, _vp, _d, _d, _i, _pi, _pd, _vp], _i),
+    "amg_destroy": ([_vp], _i),
+    "tam_solve_elasticity_host": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp,
+                                   ctypes.POINTER(AmgParams), _d, _i, _vp, _pi, _pd, _vp], _i),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1804_10060_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    return lib.tam_last_error().decode()
+
+
+def _check(status, allow=()):
+    if status != TAM_OK and status not in allow:
+        raise TamError(status, last_error())
+    return status
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _dev(t, dtype, name, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
+    return _vp(t.data_ptr())
+
+
+class Matrix:
+    """Handle of an assembled 3x3-block system matrix K."""
+
+    def __init__(self, handle, n_nodes):
+        self.handle = handle
+        self.n_nodes = n_nodes
+
+    def info(self):
+        n, nnzb, bs = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        _check(lib.tam_matrix_info(self.handle, ctypes.byref(n), ctypes.byref(nnzb), ctypes.byref(bs)))
+        return n.value, nnzb.value, bs.value
+
+    def destroy(self):
+        if self.handle:
+            lib.tam_matrix_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Amg:
+    """Handle of an SA-AMG hierarchy (keeps its matrix alive)."""
+
+    def __init__(self, handle, K):
+        self.handle = handle
+        self.K = K
+
+    def destroy(self):
+        if self.handle:
+            lib.amg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fem_assemble_elasticity(coords, cells, cell_material, mat_props, T=None, T_ref=0.0, body_force=None,
+                            dirichlet_mask=None, u_dirichlet=None, stream=None):
+    """Assemble K and the load; returns (Matrix, rhs[n,3] float64 CUDA tensor)."""
+    n_nodes = coords.shape[0]
+    n_cells, npc = cells.shape
+    rhs = torch.empty((n_nodes, 3), dtype=torch.float64, device=coords.device)
+    h = _vp()
+    _check(lib.fem_assemble_elasticity(
+        n_nodes, _dev(coords, torch.float64, "coords"), n_cells, npc, _dev(cells, torch.int32, "cells"),
+        _dev(cell_material, torch.int32, "cell_material"), mat_props.shape[0],
+        _dev(mat_props, torch.float64, "mat_props"), _dev(T, torch.float64, "T", True), float(T_ref),
+        _dev(body_force, torch.float64, "body_force", True), _dev(dirichlet_mask, torch.uint8, "dirichlet_mask"),
+        _dev(u_dirichlet, torch.float64, "u_dirichlet", True), ctypes.byref(h), _vp(rhs.data_ptr()),
+        _stream(stream)))
+    return Matrix(h, n_nodes), rhs
+
+
+def tam_matrix_export_bsr(K: Matrix, stream=None):
+    n, nnzb, bs = K.info()
+    dev = torch.device("cuda")
+    rp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(nnzb, dtype=torch.int32, device=dev)
+    v = torch.empty((nnzb, bs, bs), dtype=torch.float64, device=dev)
+    _check(lib.tam_matrix_export_bsr(K.handle, _vp(rp.data_ptr()), _vp(ci.data_ptr()), _vp(v.data_ptr()),
+                                     _stream(stream)))
+    return rp, ci, v
+
+
+def tam_matrix_spmv(K: Matrix, x, y=None, stream=None):
+    if y is None:
+        y = torch.empty_like(x)
+    _check(lib.tam_matrix_spmv(K.handle, _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"),
+                               _stream(stream)))
+    return y
+
+
+def amg_params_default(**overrides) -> AmgParams:
+    p = AmgParams()
+    _check(lib.amg_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def amg_setup(K: Matrix, coords, params: AmgParams | None = None, stream=None) -> Amg:
+    h = _vp()
+    pp = ctypes.byref(params) if params is not None else None
+    _check(lib.amg_setup(K.handle, _dev(coords, torch.float64, "coords"), pp, ctypes.byref(h), _stream(stream)))
+    return Amg(h, K)
+
+
+def amg_info(amg: Amg) -> dict:
+    L = ctypes.c_int()
+    _check(lib.amg_info(amg.handle, ctypes.byref(L), None, None, None, None, None))
+    n = L.value
+    rows = (ctypes.c_longlong * n)()
+    nnzb = (ctypes.c_longlong * n)()
+    blk = (ctypes.c_int * n)()
+    lam = (ctypes.c_double * n)()
+    oc = ctypes.c_double()
+    _check(lib.amg_info(amg.handle, ctypes.byref(L), rows, nnzb, blk, lam, ctypes.byref(oc)))
+    return {"n_levels": n, "rows": list(rows), "nnzb": list(nnzb), "block": list(blk), "lambda": list(lam),
+            "op_complexity": oc.value}
+
+
+def amg_level_aggregates(amg: Amg, level: int, stream=None):
+    info = amg_info(amg)
+    agg = torch.empty(info["rows"][level], dtype=torch.int32, device="cuda")
+    _check(lib.amg_level_aggregates(amg.handle, level, _vp(agg.data_ptr()), _stream(stream)))
+    return agg
+
+
+def amg_level_export(amg: Amg, level: int, which: int, stream=None) -> dict:
+    nr, nc, br, bc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nnzb = ctypes.c_longlong()
+    args = [ctypes.byref(x) for x in (nr, nc, br, bc, nnzb)]
+    _check(lib.amg_level_export(amg.handle, level, which, *args, None, None, None, _stream(stream)))
+    rp = torch.empty(nr.value + 1, dtype=torch.int32, device="cuda")
+    ci = torch.empty(max(nnzb.value, 1), dtype=torch.int32, device="cuda")
+    v = torch.empty((max(nnzb.value, 1), br.value, bc.value), dtype=torch.float64, device="cuda")
+    _check(lib.amg_level_export(amg.handle, level, which, *args, _vp(rp.data_ptr()), _vp(ci.data_ptr()),
+                                _vp(v.data_ptr()), _stream(stream)))
+    return {"n_rows": nr.value, "n_cols": nc.value, "br": br.value, "bc": bc.value, "nnzb": nnzb.value,
+            "row_ptr": rp, "col_idx": ci[:nnzb.value], "vals": v[:nnzb.value]}
+
+
+def amg_vcycle(amg: Amg, r, z=None, stream=None):
+    if z is None:
+        z = torch.empty_like(r)
+    _check(lib.amg_vcycle(amg.handle, _dev(r, torch.float64, "r"), _dev(z, torch.float64, "z"), _stream(stream)))
+    return z
+
+
+def amg_pcg_solve(amg: Amg, b, x, rtol=1e-8, atol=0.0, max_iter=1000, stream=None, raise_on_error=True):
+    """Returns (iterations, ||b-Kx||/||b||, status)."""
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    st = lib.amg_pcg_solve(amg.handle, _dev(b, torch.float64, "b"), _dev(x, torch.float64, "x"), float(rtol),
+                           float(atol), int(max_iter), ctypes.byref(it), ctypes.byref(rel), _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return it.value, rel.value, st
+
+
+def _host(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, _vp(arr.ctypes.data)
+
+
+def tam_solve_elasticity_host(coords, cells, cell_material, mat_props, T, T_ref, body_force, dirichlet_mask,
+                              u_dirichlet=None, params: AmgParams | None = None, rtol=1e-8, max_iter=1000,
+                              u_out=None, stream=None):
+    """Host-buffer path (numpy or pinned CPU torch tensors).  Returns (u[n,3], iters, rel)."""
+    def hp(a, dt):
+        if a is None:
+            return None, None
+        if isinstance(a, torch.Tensor):
+            assert a.device.type == "cpu" and a.is_contiguous()
+            return a, _vp(a.data_ptr())
+        return _host(a, dt)
+    keep = []
+    ptrs = []
+    for a, dt in ((coords, np.float64), (cells, np.int32), (cell_material, np.int32), (mat_props, np.float64),
+                  (T, np.float64), (body_force, np.float64), (dirichlet_mask, np.uint8), (u_dirichlet, np.float64)):
+        arr, p = hp(a, dt)
+        keep.append(arr)
+        ptrs.append(p)
+    n_nodes = coords.shape[0]
+    if u_out is None:
+        u_out = np.empty((n_nodes, 3), dtype=np.float64)
+    up = _vp(u_out.data_ptr()) if isinstance(u_out, torch.Tensor) else _vp(u_out.ctypes.data)
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    pp = ctypes.byref(params) if params is not None else None
+    st = lib.tam_solve_elasticity_host(n_nodes, ptrs[0], cells.shape[0], cells.shape[1], ptrs[1], ptrs[2],
+                                       mat_props.shape[0], ptrs[3], ptrs[4], float(T_ref), ptrs[5], ptrs[6], ptrs[7],
+                                       pp, float(rtol), int(max_iter), up, ctypes.byref(it), ctypes.byref(rel),
+                                       _stream(stream))
+    _check(st)
+    return u_out, it.value, rel.value
+
+
+def problem_to_device(pb, device="cuda"):
+    """Host arrays of a meshgen.Problem as the device tensors the C ABI takes."""
+    t = lambda a, dt: None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+    return dict(coords=t(pb.coords, np.float64), cells=t(pb.cells, np.int32),
+                cell_material=t(pb.cell_material, np.int32), mat_props=t(pb.mat_props, np.float64),
+                T=t(pb.T, np.float64), T_ref=pb.T_ref, body_force=t(pb.body_force, np.float64),
+                dirichlet_mask=t(pb.dirichlet_mask, np.uint8), u_dirichlet=t(pb.u_dirichlet, np.float64))
