@@ -1,0 +1,367 @@
+"""Benchmark: solved DOF/s of the FP64 thermoelastic AMG-PCG path on one GB300.
+
+One step = assemble K and f (P1, fem_assemble_elasticity) + SA-AMG setup
+(amg_setup) + PCG to ||r|| <= 1e-8 ||b|| (amg_pcg_solve) + release, for the
+two-material box [0,4]x[0,1]^2 at 256x64x64 hexes split into 6,291,456 Kuhn
+tets (1,085,825 nodes, 3,257,475 DOF), E in {1, 10} in alternating x-slabs,
+nu = 0.3, alpha = 1e-3, seeded 8-mode Fourier temperature, clamped at x = 0.
+Inputs are seeded synthetic arrays resident in HBM before timing; the
+working set (K alone is 1.2 GB) is far larger than L2 and a 512 MB buffer is
+also rewritten between steps.
+
+value = DOF solved per second over the whole job (N replicas under torchrun:
+the single solve does not shard, each rank solves its own copy).
+e2e   = the same metric through tam_solve_elasticity_host from pinned host
+        buffers, host<->device copies inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved DOF/s to rtol 1e-8 (FP64 AMG-PCG, assemble+setup+solve)"
+WORKLOAD = ("two-material box [0,4]x[0,1]^2, 256x64x64 hexes -> 6,291,456 P1 tets, 3,257,475 DOF, "
+            "E in {1,10} slabs, seeded Fourier temperature, clamped x=0; FP64 assemble+SA-AMG setup+PCG rtol 1e-8")
+DIMS = (256, 64, 64)
+SAMPLE_DIMS = (96, 24, 24)      # bounded oracle sample (same structure, 181,875 DOF)
+FALLBACK_HBM_GBS = 6800.0       # recipe fallback when MEASURED_PEAKS.json is absent
+NOMINAL_FP64_TFLOPS = 1.25      # GB300 FP64 (nominal table)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dims", default=None, help="override box hexes, e.g. 64x16x16 (testing only)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm), in a fresh single-threaded process
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+from paper_1804_10060_gb300 import meshgen
+from oracle import fem, amg
+pb = meshgen.slab_box_problem(*{dims!r})
+out = []
+for _ in range({reps}):
+    t0 = time.perf_counter()
+    K, f = fem.assemble_system(pb)
+    H = amg.setup(K, fem.rigid_body_modes(pb.coords, pb.dirichlet_mask), 3)
+    x, it, rel = amg.pcg(K, f, H, rtol=1e-8)
+    out.append(dict(t=time.perf_counter() - t0, it=it, rel=rel))
+print(json.dumps(dict(n_dof=pb.n_dof, runs=out)))
+"""
+
+
+def run_oracle(reps, dims=SAMPLE_DIMS):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, dims=tuple(dims), reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(res, dims=SAMPLE_DIMS):
+    ts = [x["t"] for x in res["runs"]]
+    v = res["n_dof"] * len(ts) / sum(ts)
+    return {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle assemble+SA-AMG setup+PCG rtol 1e-8 on the same two-material box at "
+                       f"{dims[0]}x{dims[1]}x{dims[2]} hexes ({res['n_dof']} DOF), {len(ts)} run(s), "
+                       f"{res['runs'][-1]['it']} iterations, single-threaded NumPy/SciPy; "
+                       f"host has {os.cpu_count()} cores")}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def reference_arm(args):
+    rank, world, local = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    dims = SAMPLE_DIMS
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state worth priming beyond one run below
+    res = run_oracle(max(args.steps, 1), dims)
+    cb = cpu_baseline_obj(res, dims)
+    ts = [x["t"] for x in res["runs"]]
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "DOF/s", "n_gpus": args.gpus,
+            "steps": len(ts), "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_sample": f"{dims[0]}x{dims[1]}x{dims[2]}"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def native_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_1804_10060_gb300 import meshgen
+    from paper_1804_10060_gb300 import thermoamg as tam
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dims = tuple(int(x) for x in args.dims.split("x")) if args.dims else DIMS
+    pb = meshgen.slab_box_problem(*dims)
+    d = tam.problem_to_device(pb)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    params = tam.amg_params_default()
+    last = {}
+
+    def step(record=False):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            K, rhs = tam.fem_assemble_elasticity(**d, stream=stream)
+            H = tam.amg_setup(K, d["coords"], params, stream=stream)
+            x = torch.zeros_like(rhs)
+            it, rel, st = tam.amg_pcg_solve(H, rhs, x, rtol=1e-8, max_iter=1000, stream=stream)
+            if record:
+                last.update(iters=it, rel=rel, info=tam.amg_info(H))
+            H.destroy()
+            K.destroy()
+        return it
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = tam.kernel_launches()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            step(record=(k == args.steps - 1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches = tam.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = world * pb.n_dof / (ms * 1e-3)
+
+    # per-phase times of one more step (events around each call)
+    phases = {}
+    with torch.cuda.stream(stream):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        K, rhs = tam.fem_assemble_elasticity(**d, stream=stream)
+        ev[1].record(stream)
+        H = tam.amg_setup(K, d["coords"], params, stream=stream)
+        ev[2].record(stream)
+        x = torch.zeros_like(rhs)
+        it, rel, st = tam.amg_pcg_solve(H, rhs, x, rtol=1e-8, max_iter=1000, stream=stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        phases = {"assemble_ms": ev[0].elapsed_time(ev[1]), "setup_ms": ev[1].elapsed_time(ev[2]),
+                  "solve_ms": ev[2].elapsed_time(ev[3])}
+        # dominant kernel: level-0 SELL-32 FP64 block SpMV, timed alone with L2 flushed before each launch
+        n, nnzb, _ = K.info()
+        xs = torch.randn(n, 3, dtype=torch.float64, device="cuda")
+        ys = torch.empty_like(xs)
+        reps = 20
+        tsum = 0.0
+        for _ in range(3):
+            tam.tam_matrix_spmv(K, xs, ys, stream=stream)
+        for _ in range(reps):
+            flush.fill_(2.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tam.tam_matrix_spmv(K, xs, ys, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            tsum += a.elapsed_time(b)
+        spmv_ms = tsum / reps
+        H.destroy()
+        K.destroy()
+    alg_bytes = nnzb * 76 + n * 48          # 72 B values + 4 B column per block; x read, y written
+    alg_flops = nnzb * 18                   # 9 FMA per 3x3 block
+    hbm_peak, hbm_src = peaks()
+    achieved_tf = alg_flops / (spmv_ms * 1e-3) / 1e12
+    achieved_gbs = alg_bytes / (spmv_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("bytes_per_launch_full_size")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+                "kernel": "sell_spmv_kernel<3,3,EpiStore<3>> (level-0 FP64 block SpMV)",
+                "spmv_ms": spmv_ms, "alg_bytes": alg_bytes, "alg_flops": alg_flops,
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
+
+    # end to end through the host-buffer entry point (pinned host arrays)
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+    hx = dict(coords=pin(pb.coords, np.float64), cells=pin(pb.cells, np.int32),
+              cell_material=pin(pb.cell_material, np.int32), mat_props=pin(pb.mat_props, np.float64),
+              T=pin(pb.T, np.float64), body_force=None, dirichlet_mask=pin(pb.dirichlet_mask, np.uint8))
+    u_host = torch.empty((pb.n_nodes, 3), dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in hx.values() if v is not None)
+    d2h = u_host.numel() * 8
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(1):
+        tam.tam_solve_elasticity_host(**hx, T_ref=pb.T_ref, u_dirichlet=None, params=params, u_out=u_host,
+                                      stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tam.tam_solve_elasticity_host(**hx, T_ref=pb.T_ref, u_dirichlet=None, params=params, u_out=u_host,
+                                      stream=stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, world)
+    e2e_val = world * pb.n_dof / (e2e_ms * 1e-3)
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dof": pb.n_dof, "nnzb": int(nnzb), "parallelism": "replicas",
+                       "l2": "inputs and K (1.2 GB) larger than L2; 512 MB buffer rewritten before every step",
+                       "iterations": last.get("iters"), "final_rel_resid": last.get("rel"),
+                       "levels": last.get("info", {}).get("rows"),
+                       "op_complexity": last.get("info", {}).get("op_complexity"), **phases},
+            "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(launches),
+            "e2e": {"value": e2e_val, "unit": "DOF/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_ms}}
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_obj(run_oracle(1))
+        except Exception as e:  # reported, never silently replaced
+            line["cpu_baseline"] = {"error": str(e)[-300:]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        native_arm(args)
+
+
+if __name__ == "__main__":
+    main()

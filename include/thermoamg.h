@@ -53,6 +53,11 @@ typedef struct tam_amg_s* tam_amg;       /* SA-AMG hierarchy bound to one tam_ma
 /* Message for the calling thread's last failing call ("" if none). */
 const char* tam_last_error(void);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (kernels replayed from its CUDA graphs included).  Instrumentation for
+ * benchmarks; never fails. */
+long long tam_kernel_launches(void);
+
 /* ------------------------------------------------------------------------
  * Assembly (Sec. 3, Eq. wf_elastic, steady, traction free; Eq. u-dbc).
  *

@@ -56,6 +56,8 @@ extern "C" {
 
 const char* tam_last_error(void) { return last_error_cstr(); }
 
+long long tam_kernel_launches(void) { return launches_total(); }
+
 int fem_assemble_elasticity(int n_nodes, const double* coords, int n_cells, int nodes_per_cell, const int* cells,
                             const int* cell_material, int n_mat, const double* mat_props, const double* T,
                             double T_ref, const double* body_force, const unsigned char* dirichlet_mask,

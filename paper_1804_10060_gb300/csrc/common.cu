@@ -2,11 +2,23 @@
 // and the three-phase (block sums, scan of sums, apply) exclusive scan.
 #include "common.cuh"
 
+#include <atomic>
 #include <mutex>
 
 namespace tam {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+thread_local bool g_capturing = false;
+static thread_local long long g_captured = 0;
+
+void count_launch() {
+  if (g_capturing) ++g_captured;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_graph_launch(long long kernel_nodes) { g_launches.fetch_add(kernel_nodes, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(); }
+long long captured_and_reset() { long long c = g_captured; g_captured = 0; return c; }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error_cstr() { return g_last_error.c_str(); }

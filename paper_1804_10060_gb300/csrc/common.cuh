@@ -38,7 +38,18 @@ void set_last_error(const std::string& msg);
     if (!(cond)) throw ::tam::Error((code), std::string(msg));     \
   } while (0)
 
-#define TAM_LAUNCH_CHECK() TAM_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by TAM_LAUNCH_CHECK(), which
+// also counts it (launches recorded into a CUDA graph are counted when the
+// graph is launched, see count_graph_launch).
+void count_launch();
+void count_graph_launch(long long kernel_nodes);
+extern thread_local bool g_capturing;
+
+#define TAM_LAUNCH_CHECK()        \
+  do {                            \
+    TAM_CUDA(cudaGetLastError()); \
+    ::tam::count_launch();        \
+  } while (0)
 
 // ---------------------------------------------------------------------------
 // Stream-ordered device memory (default pool, kept cached between calls).

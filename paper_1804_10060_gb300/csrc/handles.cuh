@@ -66,6 +66,7 @@ struct tam_amg_s {
   const double* graph_b = nullptr;
   double* graph_x = nullptr;
   cudaStream_t graph_stream = nullptr;
+  long long graph_kernels = 0;           // kernel nodes in iter_exec
   ~tam_amg_s();
 };
 
@@ -85,5 +86,8 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
               double* rel, cudaStream_t s);
 
 void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s);
+
+long long launches_total();
+long long captured_and_reset();
 
 }  // namespace tam

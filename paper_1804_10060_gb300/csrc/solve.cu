@@ -349,13 +349,18 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
     TAM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g;
     TAM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    captured_and_reset();
+    g_capturing = true;
     try {
       enqueue_iteration(H, x, cs);
     } catch (...) {
+      g_capturing = false;
       cudaStreamEndCapture(cs, &g);
       cudaStreamDestroy(cs);
       throw;
     }
+    g_capturing = false;
+    H->graph_kernels = captured_and_reset();
     TAM_CUDA(cudaStreamEndCapture(cs, &g));
     TAM_CUDA(cudaGraphInstantiate(&H->iter_exec, g, 0));
     cudaGraphDestroy(g);
@@ -368,7 +373,10 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   int launched = 0;
   while (launched < max_iter) {
     int todo = std::min(chunk, max_iter - launched);
-    for (int i = 0; i < todo; ++i) TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
+    for (int i = 0; i < todo; ++i) {
+      TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
+      count_graph_launch(H->graph_kernels);
+    }
     launched += todo;
     TAM_CUDA(cudaMemcpyAsync(hs.ll, &sc->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
     TAM_CUDA(cudaStreamSynchronize(s));

@@ -49,6 +49,7 @@ _pi, _pd, _pll = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), 
 
 _SIGNATURES = {
     "tam_last_error": ([], ctypes.c_char_p),
+    "tam_kernel_launches": ([], ctypes.c_longlong),
     "fem_assemble_elasticity": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp,
                                  ctypes.POINTER(_vp), _vp, _vp], _i),
     "tam_matrix_info": ([_vp, _pi, _pll, _pi], _i),
@@ -84,6 +85,11 @@ lib = _load()
 
 def last_error() -> str:
     return lib.tam_last_error().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process (graph replays included)."""
+    return int(lib.tam_kernel_launches())
 
 
 def _check(status, allow=()):

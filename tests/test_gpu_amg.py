@@ -122,7 +122,9 @@ def test_vcycle_is_symmetric_and_positive():
 
 def test_max_iter_and_status_paths():
     pb = meshgen.unit_cube_problem(6)
-    tam, d, K, rhs, H = _setup(pb)
+    # 1,029 DOF would be the dense coarsest level itself with the default
+    # coarse_max_dofs (an exact preconditioner); force two levels
+    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=100)
     x = torch.zeros_like(rhs)
     it, rel, st = tam.amg_pcg_solve(H, rhs, x, rtol=1e-14, max_iter=3, raise_on_error=False)
     assert st == -5 and it == 3
