@@ -47,7 +47,35 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dims", default=None, help="override box hexes, e.g. 64x16x16 (testing only)")
+    ap.add_argument("--summarize-ncu", default=None, metavar="CSV",
+                    help="print a per-kernel summary (launches, time, share) of an ncu --csv launch list and exit")
     return ap.parse_args()
+
+
+def summarize_ncu(path, top=25):
+    """Per-kernel launches / total time / share from `ncu --metrics gpu__time_duration.sum --csv`."""
+    import csv
+    rows = []
+    with open(path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    for rec in csv.DictReader(lines):
+        if rec.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        v = float(rec["Metric Value"].replace(",", ""))
+        unit = rec.get("Metric Unit", "ns")
+        scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}.get(unit, 1e-3)
+        rows.append((rec["Kernel Name"], v * scale))
+    agg = {}
+    for name, us in rows:
+        short = name.split("(")[0]
+        a = agg.setdefault(short, [0, 0.0])
+        a[0] += 1
+        a[1] += us
+    total = sum(a[1] for a in agg.values())
+    print(f"{len(rows)} launches, {total / 1e3:.3f} ms total device time")
+    print(f"{'kernel':70s} {'launches':>8s} {'total_ms':>10s} {'share':>7s} {'avg_us':>9s}")
+    for name, (n, us) in sorted(agg.items(), key=lambda kv: -kv[1][1])[:top]:
+        print(f"{name[:70]:70s} {n:8d} {us / 1e3:10.3f} {100 * us / total:6.2f}% {us / n:9.2f}")
 
 
 def peaks():
@@ -357,6 +385,9 @@ def native_arm(args):
 
 def main():
     args = parse()
+    if args.summarize_ncu:
+        summarize_ncu(args.summarize_ncu)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:
