@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dims", default=None, help="override box hexes, e.g. 64x16x16 (testing only)")
+    ap.add_argument("--spmv-only", type=int, default=0, metavar="LAUNCHES",
+                    help="assemble K and launch only the level-0 SpMV this many times (profiling target)")
     ap.add_argument("--summarize-ncu", default=None, metavar="CSV",
                     help="print a per-kernel summary (launches, time, share) of an ncu --csv launch list and exit")
     return ap.parse_args()
@@ -383,10 +385,32 @@ def native_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def spmv_only(args):
+    """Assemble the box and launch only tam_matrix_spmv (a small, single-kernel profiling target)."""
+    import torch
+
+    from paper_1804_10060_gb300 import meshgen
+    from paper_1804_10060_gb300 import thermoamg as tam
+    dims = tuple(int(x) for x in args.dims.split("x")) if args.dims else DIMS
+    pb = meshgen.slab_box_problem(*dims)
+    d = tam.problem_to_device(pb)
+    K, rhs = tam.fem_assemble_elasticity(**d)
+    x = torch.randn(pb.n_nodes, 3, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(args.spmv_only):
+        tam.tam_matrix_spmv(K, x, y)
+    torch.cuda.synchronize()
+    n, nnzb, _ = K.info()
+    print(json.dumps({"spmv_only": args.spmv_only, "n": n, "nnzb": nnzb, "dims": dims}))
+
+
 def main():
     args = parse()
     if args.summarize_ncu:
         summarize_ncu(args.summarize_ncu)
+        return
+    if args.spmv_only:
+        spmv_only(args)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -103,6 +103,15 @@ int tam_matrix_export_bsr(tam_matrix K, int* row_ptr, int* col_idx, double* vals
 /* y = K x (x, y: [3n] float64 device vectors, must not overlap). */
 int tam_matrix_spmv(tam_matrix K, const double* x, double* y, void* stream);
 
+/* ||b - K x||_2 into *norm_host (host double): the true residual of a
+ * candidate displacement, the quantity the CG stopping test of Sec. 2.1 is
+ * judged by.  b, x: [3n] float64 device vectors.  One fused SpMV + grid
+ * reduction; its per-block partial sums live in scratch memory the call
+ * allocates stream-ordered and frees again.  Synchronising.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int tam_matrix_residual_norm(tam_matrix K, const double* b, const double* x, double* norm_host,
+                             void* stream);
+
 /* Releases K (an AMG built on K must be destroyed first). */
 int tam_matrix_destroy(tam_matrix K);
 

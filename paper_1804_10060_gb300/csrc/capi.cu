@@ -97,6 +97,14 @@ int tam_matrix_spmv(tam_matrix K, const double* x, double* y, void* stream) {
   });
 }
 
+int tam_matrix_residual_norm(tam_matrix K, const double* b, const double* x, double* norm_host, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(K && b && x && norm_host, TAM_ERR_INVALID_ARG, "tam_matrix_residual_norm: NULL argument");
+    *norm_host = residual_norm_K(K, b, x, as_stream(stream));
+    return TAM_OK;
+  });
+}
+
 int tam_matrix_destroy(tam_matrix K) {
   return guarded([&] {
     delete K;

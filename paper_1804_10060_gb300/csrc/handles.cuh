@@ -86,6 +86,7 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
               double* rel, cudaStream_t s);
 
 void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s);
+double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaStream_t s);
 
 long long launches_total();
 long long captured_and_reset();

@@ -323,6 +323,16 @@ void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s) {
   sell_spmv<3, 3>(K->S, x, EpiStore<3>{y, K->n_nodes, nullptr}, s);
 }
 
+double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaStream_t s) {
+  const unsigned grid = sell_grid(K->S);
+  DBuf<double> partials(grid, s), out(1, s);
+  DBuf<unsigned int> ticket(1, s);
+  ticket.zero();
+  GridReduce gr{partials.p, ticket.p};
+  sell_spmv<3, 3>(K->S, x, EpiResNorm<3>{b, K->n_nodes, gr, out.p}, s);
+  return std::sqrt(read_back_double(out.p, s));
+}
+
 void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s) {
   vcycle_level(H, 0, r, z, stop, s);
 }

@@ -55,6 +55,7 @@ _SIGNATURES = {
     "tam_matrix_info": ([_vp, _pi, _pll, _pi], _i),
     "tam_matrix_export_bsr": ([_vp, _vp, _vp, _vp, _vp], _i),
     "tam_matrix_spmv": ([_vp, _vp, _vp, _vp], _i),
+    "tam_matrix_residual_norm": ([_vp, _vp, _vp, _pd, _vp], _i),
     "tam_matrix_destroy": ([_vp], _i),
     "amg_params_default": ([ctypes.POINTER(AmgParams)], _i),
     "amg_setup": ([_vp, _vp, ctypes.POINTER(AmgParams), ctypes.POINTER(_vp), _vp], _i),
@@ -190,6 +191,14 @@ def tam_matrix_spmv(K: Matrix, x, y=None, stream=None):
     _check(lib.tam_matrix_spmv(K.handle, _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"),
                                _stream(stream)))
     return y
+
+
+def tam_matrix_residual_norm(K: Matrix, b, x, stream=None) -> float:
+    """||b - K x||_2 (host float)."""
+    out = ctypes.c_double()
+    _check(lib.tam_matrix_residual_norm(K.handle, _dev(b, torch.float64, "b"), _dev(x, torch.float64, "x"),
+                                        ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def amg_params_default(**overrides) -> AmgParams:

@@ -128,3 +128,16 @@ def test_full_size_box_sampled_rows():
                     assert abs(blk[r, cc] - ref.get(3 * c + cc, 0.0)) <= TOL * scale
             assert set(int(c) // 3 for c, val in zip(row.indices, row.data) if val != 0) <= set(blocks)
             assert abs(f[i, r] - fo[3 * i + r]) <= TOL * max(np.abs(fo).max(), 1e-300)
+
+
+def test_residual_norm_entry_point():
+    tam = need_gpu()
+    pb = _rich_problem(6, 1)
+    d = tam.problem_to_device(pb)
+    K, rhs = tam.fem_assemble_elasticity(**d)
+    rp, ci, v = tam.tam_matrix_export_bsr(K)
+    Kg = bsr_to_csr(rp, ci, v, pb.n_nodes)
+    x = torch.randn(pb.n_nodes, 3, dtype=torch.float64, device="cuda")
+    got = tam.tam_matrix_residual_norm(K, rhs, x)
+    ref = np.linalg.norm(rhs.cpu().numpy().ravel() - Kg @ x.cpu().numpy().ravel())
+    assert abs(got - ref) <= 1e-12 * ref
