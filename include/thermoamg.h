@@ -112,6 +112,24 @@ int tam_matrix_spmv(tam_matrix K, const double* x, double* y, void* stream);
 int tam_matrix_residual_norm(tam_matrix K, const double* b, const double* x, double* norm_host,
                              void* stream);
 
+/* Same result as tam_matrix_residual_norm, for callers that must not
+ * allocate device memory (code inside a custom allocator or pool callback,
+ * applications with a device-memory budget fixed at start-up, paths that
+ * cannot take cudaMalloc's implicit synchronisation).  The paper has no
+ * counterpart; this is a library-integration entry point.
+ *  - Allocates nothing: the reduction scratch is a 128 KiB file-scope device
+ *    array that every device loading the library keeps until exit.
+ *  - Limit: K with at most 2,097,152 block rows (16384 blocks of 128 rows);
+ *    larger K returns INVALID_ARG without launching anything.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that call before any stream
+ *    capture begins.
+ *  - All calls share the array: calls whose work overlaps on the GPU race.
+ * b, x: [3n] float64 device vectors; *norm_host receives ||b - K x||_2.
+ * Synchronising.  Errors: INVALID_ARG, CUDA. */
+int tam_matrix_residual_norm_noalloc(tam_matrix K, const double* b, const double* x,
+                                     double* norm_host, void* stream);
+
 /* Releases K (an AMG built on K must be destroyed first). */
 int tam_matrix_destroy(tam_matrix K);
 

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "tam_matrix_export_bsr": ([_vp, _vp, _vp, _vp, _vp], _i),
     "tam_matrix_spmv": ([_vp, _vp, _vp, _vp], _i),
     "tam_matrix_residual_norm": ([_vp, _vp, _vp, _pd, _vp], _i),
+    "tam_matrix_residual_norm_noalloc": ([_vp, _vp, _vp, _pd, _vp], _i),
     "tam_matrix_destroy": ([_vp], _i),
     "amg_params_default": ([ctypes.POINTER(AmgParams)], _i),
     "amg_setup": ([_vp, _vp, ctypes.POINTER(AmgParams), ctypes.POINTER(_vp), _vp], _i),
@@ -198,6 +199,14 @@ def tam_matrix_residual_norm(K: Matrix, b, x, stream=None) -> float:
     out = ctypes.c_double()
     _check(lib.tam_matrix_residual_norm(K.handle, _dev(b, torch.float64, "b"), _dev(x, torch.float64, "x"),
                                         ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def tam_matrix_residual_norm_noalloc(K: Matrix, b, x, stream=None) -> float:
+    """||b - K x||_2 without any device allocation (static 128 KiB scratch; see the C header)."""
+    out = ctypes.c_double()
+    _check(lib.tam_matrix_residual_norm_noalloc(K.handle, _dev(b, torch.float64, "b"),
+                                                _dev(x, torch.float64, "x"), ctypes.byref(out), _stream(stream)))
     return out.value
 
 
