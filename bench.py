@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dims", default=None, help="override box hexes, e.g. 64x16x16 (testing only)")
+    ap.add_argument("--one-step", action="store_true",
+                    help="run exactly one assemble+setup+solve (profiling target) and exit")
     ap.add_argument("--spmv-only", type=int, default=0, metavar="LAUNCHES",
                     help="assemble K and launch only the level-0 SpMV this many times (profiling target)")
     ap.add_argument("--summarize-ncu", default=None, metavar="CSV",
@@ -303,7 +305,8 @@ def native_arm(args):
         ev[3].record(stream)
         torch.cuda.synchronize()
         phases = {"assemble_ms": ev[0].elapsed_time(ev[1]), "setup_ms": ev[1].elapsed_time(ev[2]),
-                  "solve_ms": ev[2].elapsed_time(ev[3])}
+                  "solve_ms": ev[2].elapsed_time(ev[3]), "solve_iterations": it,
+                  "setup_phases_ms": {k: round(v, 3) for k, v in tam.amg_setup_stats(H).items()}}
         # dominant kernel: level-0 SELL-32 FP64 block SpMV, timed alone with L2 flushed before each launch
         n, nnzb, _ = K.info()
         xs = torch.randn(n, 3, dtype=torch.float64, device="cuda")
@@ -364,6 +367,37 @@ def native_arm(args):
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, world)
     e2e_val = world * pb.n_dof / (e2e_ms * 1e-3)
 
+    # reduced-precision V-cycle variants (FP64 CG, FP64 coarse solve), same workload and accuracy target
+    variants = {}
+    for name, prec in (("fp32_vcycle", 1), ("bf16_fine_fp32_vcycle", 2)):
+        vparams = tam.amg_params_default(level_precision=prec)
+        vrec = {}
+
+        def vstep(rec=False):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                K, rhs = tam.fem_assemble_elasticity(**d, stream=stream)
+                H = tam.amg_setup(K, d["coords"], vparams, stream=stream)
+                x = torch.zeros_like(rhs)
+                it, rel, st = tam.amg_pcg_solve(H, rhs, x, rtol=1e-8, max_iter=1000, stream=stream)
+                if rec:
+                    vrec.update(iterations=it, final_rel_resid=rel, status=st)
+                H.destroy()
+                K.destroy()
+
+        vstep()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nv = max(1, min(args.steps, 3))
+        a.record(stream)
+        for k in range(nv):
+            vstep(rec=(k == nv - 1))
+        b.record(stream)
+        torch.cuda.synchronize()
+        vms = max_over_ranks(a.elapsed_time(b) / nv, world)
+        variants[name] = {"value": world * pb.n_dof / (vms * 1e-3), "unit": "DOF/s", "ms_per_step": vms,
+                          "steps": nv, **vrec}
+
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
@@ -376,7 +410,8 @@ def native_arm(args):
                        "op_complexity": last.get("info", {}).get("op_complexity"), **phases},
             "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(launches),
             "e2e": {"value": e2e_val, "unit": "DOF/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "ms_per_step": e2e_ms}}
+                    "ms_per_step": e2e_ms},
+            "variants": variants}
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_obj(run_oracle(1))
@@ -404,6 +439,24 @@ def spmv_only(args):
     print(json.dumps({"spmv_only": args.spmv_only, "n": n, "nnzb": nnzb, "dims": dims}))
 
 
+def one_step(args):
+    """Exactly one assemble + setup + solve of the workload (launch-list profiling target)."""
+    import torch
+
+    from paper_1804_10060_gb300 import meshgen
+    from paper_1804_10060_gb300 import thermoamg as tam
+    dims = tuple(int(x) for x in args.dims.split("x")) if args.dims else DIMS
+    pb = meshgen.slab_box_problem(*dims)
+    d = tam.problem_to_device(pb)
+    K, rhs = tam.fem_assemble_elasticity(**d)
+    H = tam.amg_setup(K, d["coords"])
+    x = torch.zeros_like(rhs)
+    it, rel, _ = tam.amg_pcg_solve(H, rhs, x, rtol=1e-8, max_iter=1000)
+    torch.cuda.synchronize()
+    print(json.dumps({"one_step": True, "dims": dims, "iterations": it, "rel": rel,
+                      "levels": tam.amg_info(H)["rows"], "launches": tam.kernel_launches()}))
+
+
 def main():
     args = parse()
     if args.summarize_ncu:
@@ -411,6 +464,9 @@ def main():
         return
     if args.spmv_only:
         spmv_only(args)
+        return
+    if args.one_step:
+        one_step(args)
         return
     if args.impl == "reference":
         reference_arm(args)

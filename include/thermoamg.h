@@ -146,9 +146,15 @@ typedef struct amg_params {
   double cheb_hi;          /* 1.1                                                                    */
   int eig_iters;           /* Lanczos steps for lambda_max(D^-1 A); default 10                        */
   int coarse_max_dofs;     /* stop coarsening at or below this many DOFs; default 2000                */
+  int coarse_min_dofs;     /* redo a distance-2 aggregation with distance-1 roots when it would give
+                              fewer coarse DOFs than this (0 = never); default 500                  */
+  int small_level_dofs;    /* smoothed levels with at most this many DOFs use ...                     */
+  int small_level_degree;  /* ... this Chebyshev degree (they are cheap and, above an aggressively
+                              coarsened coarsest grid, must nearly solve their problem); 20000, 16 */
   int max_levels;          /* including the finest; default 10                                       */
   int use_rotations;       /* 1: six rigid-body modes; 0: three translations only; default 1         */
-  int level_precision;     /* 0: FP64 hierarchy (the only value this build accepts)                   */
+  int level_precision;     /* V-cycle storage/arithmetic: 0 FP64; 1 FP32; 2 FP32 with BF16 finest-level
+                              values.  The outer CG and the coarsest dense solve stay FP64; default 0 */
 } amg_params;
 
 /* Fills *p with the defaults above. */
@@ -170,6 +176,13 @@ int amg_setup(tam_matrix K, const double* coords, const amg_params* params, tam_
  * lambda_max estimate; op_complexity = sum nnz(A_l) / nnz(A_0) in scalars. */
 int amg_info(tam_amg amg, int* n_levels, long long* level_rows_host, long long* level_nnzb_host,
              int* level_block_host, double* level_lambda_host, double* op_complexity);
+
+/* Device time of the setup phases summed over levels, in milliseconds, into
+ * phase_ms_host[8] (host): 0 diagonal + Lanczos lambda_max, 1 strength +
+ * aggregation, 2 tentative prolongator, 3 A P_tent + smoothing, 4 R = P^T,
+ * 5 Galerkin product (A P, R (A P)), 6 SpMV-layout conversions, 7 coarsest
+ * dense inverse.  Measured with CUDA events; never synchronises. */
+int amg_setup_stats(tam_amg amg, double* phase_ms_host);
 
 /* Aggregate id of every block row of `level` (-1 = not aggregated) into
  * agg[n_rows] (device int32).  Synchronising. */

@@ -101,8 +101,12 @@ def strength_graph(A, bs, theta=0.0):
     return nbrs
 
 
-def mis2_aggregate(nbrs, level):
-    """Aggregates from the greedy distance-2 MIS (see module header). Returns (agg, n_agg, roots)."""
+def mis2_aggregate(nbrs, level, distance=2):
+    """Aggregates from the greedy distance-`distance` MIS (see module header).
+
+    distance=2 is the default (aggressive) rule; distance=1 gives roots that
+    are only pairwise non-adjacent (smaller aggregates).  Returns (agg, n_agg, roots).
+    """
     n = len(nbrs)
     prio = node_priority(n, level)
     isolated = np.array([len(x) == 0 for x in nbrs])
@@ -117,8 +121,9 @@ def mis2_aggregate(nbrs, level):
         excluded[i] = True
         for j in nbrs[i]:
             excluded[j] = True
-            for k in nbrs[j]:
-                excluded[k] = True
+            if distance == 2:
+                for k in nbrs[j]:
+                    excluded[k] = True
     roots = np.nonzero(is_root)[0]
     agg = -np.ones(n, np.int64)
     agg[roots] = np.arange(roots.size)
@@ -304,6 +309,7 @@ class Level:
     R: sp.csr_matrix = None
     agg: np.ndarray = None
     n_agg: int = 0
+    degree: int = 2
 
 
 @dataclass
@@ -314,7 +320,18 @@ class Hierarchy:
 
 
 DEFAULTS = dict(theta=0.0, degree=2, cheb_lo=0.1, cheb_hi=1.1, eig_steps=10,
-                coarse_max_dofs=2000, max_levels=10, droptol=1e-10)
+                coarse_max_dofs=2000, coarse_min_dofs=500, small_level_dofs=20000,
+                small_level_degree=16, max_levels=10, droptol=1e-10)
+
+
+def aggregate_level(nbrs, level, k, coarse_min_dofs):
+    """Distance-2 aggregation, redone with distance-1 roots when it would leave
+    fewer than coarse_min_dofs coarse DOFs (k per aggregate): the paper asks
+    for fast coarsening but also finds a larger coarsest grid more robust."""
+    agg, n_agg, _ = mis2_aggregate(nbrs, level)
+    if coarse_min_dofs and n_agg * k < coarse_min_dofs:
+        agg, n_agg, _ = mis2_aggregate(nbrs, level, distance=1)
+    return agg, n_agg
 
 
 def setup(A, B, bs=3, **kw):
@@ -330,14 +347,19 @@ def setup(A, B, bs=3, **kw):
         if A.shape[0] <= prm["coarse_max_dofs"] or lev == prm["max_levels"] - 1:
             break
         nbrs = strength_graph(A, bs, prm["theta"])
-        agg, n_agg, _ = mis2_aggregate(nbrs, lev)
-        if n_agg == 0:
+        agg, n_agg = aggregate_level(nbrs, lev, B.shape[1], prm["coarse_min_dofs"])
+        if n_agg == 0 or n_agg >= A.shape[0] // bs:
             break
         Pt, Bc = tentative_prolongator(agg, n_agg, B, bs, prm["droptol"])
         P = smooth_prolongator(A, Pt, L.lam)
         Ac, R = galerkin(A, P)
         L.P, L.R, L.agg, L.n_agg = P, R, agg, n_agg
         A, B, bs = Ac, Bc, B.shape[1]
+    # small (cheap) smoothed levels get a higher-degree Chebyshev: with an
+    # aggressively coarsened coarsest grid they must nearly solve their own problem
+    for L in levels[:-1]:
+        small = L.A.shape[0] <= prm["small_level_dofs"]
+        L.degree = prm["small_level_degree"] if small else prm["degree"]
     return Hierarchy(levels=levels, coarse_inv=coarse_inverse(levels[-1].A), params=prm)
 
 
@@ -347,10 +369,10 @@ def vcycle(H, b, lev=0):
         return H.coarse_inv @ b
     p = H.params
     lo, hi = p["cheb_lo"] * L.lam, p["cheb_hi"] * L.lam
-    x = chebyshev(L.A, L.dinv, b, np.zeros_like(b), lo, hi, p["degree"])
+    x = chebyshev(L.A, L.dinv, b, np.zeros_like(b), lo, hi, L.degree)
     r = b - L.A @ x
     x = x + L.P @ vcycle(H, L.R @ r, lev + 1)
-    return chebyshev(L.A, L.dinv, b, x, lo, hi, p["degree"])
+    return chebyshev(L.A, L.dinv, b, x, lo, hi, L.degree)
 
 
 def pcg(A, b, H, rtol=1e-8, atol=0.0, max_iter=1000, x0=None):

@@ -10,6 +10,7 @@
 // A_c = R A P.  The coarsest operator is inverted densely (Gauss-Jordan).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "handles.cuh"
 
@@ -281,16 +282,17 @@ __global__ void mis_round1_kernel(const int* __restrict__ rp, const int* __restr
 
 __global__ void mis_round2_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
                                   unsigned char* __restrict__ state, const unsigned long long* __restrict__ m1, int n,
-                                  int level, int* __restrict__ undecided) {
+                                  int level, int distance, int* __restrict__ undecided) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (state[i] != ST_UND) return;
-  unsigned long long m = m1[i];
-  for (int p = rp[i]; p < rp[i + 1]; ++p)
-    if (strong[p]) {
-      unsigned long long t = m1[ci[p]];
-      m = t > m ? t : m;
-    }
+  unsigned long long m = m1[i];  // max over the closed 1-neighbourhood
+  if (distance == 2)
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (strong[p]) {
+        unsigned long long t = m1[ci[p]];
+        m = t > m ? t : m;
+      }
   const unsigned long long mine = mis_tuple(ST_UND, level, i);
   if (m == mine) state[i] = ST_ROOT;
   else if ((m >> 62) == 2ull) state[i] = ST_OUT;
@@ -541,10 +543,10 @@ static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s) {
   for (int j = 0; j < k; ++j) {
     if (L.bs == 3) {
       EpiLanczos<3> epi{w.p, sv.p, v.p, L.n_rows, gr, ab.p + j, done};
-      sell_spmv<3, 3>(*L.AS, u.p, epi, s);
+      spop_apply<3, 3>(L.Aop, u.p, epi, s);
     } else {
       EpiLanczos<6> epi{w.p, sv.p, v.p, L.n_rows, gr, ab.p + j, done};
-      sell_spmv<6, 6>(*L.AS, u.p, epi, s);
+      spop_apply<6, 6>(L.Aop, u.p, epi, s);
     }
     lanczos_orth_kernel<<<g, TPB, 0, s>>>(LW, j, gr, done);
     TAM_LAUNCH_CHECK();
@@ -555,7 +557,7 @@ static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s) {
       TAM_LAUNCH_CHECK();
     }
   }
-  const int deg = std::max(H->prm.smoother_degree, 1);
+  const int deg = std::max(L.deg, 1);
   L.consts = DBuf<double>(2 + 2 * (size_t)deg, s);
   tridiag_lmax_kernel<<<1, 1, 0, s>>>(ab.p, mdone.p, k, H->prm.cheb_lo, H->prm.cheb_hi, deg, L.consts.p);
   TAM_LAUNCH_CHECK();
@@ -564,7 +566,7 @@ static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s) {
             "amg_setup: lambda_max estimate is not positive");
 }
 
-static int aggregate(Level& L, int level, double theta, cudaStream_t s) {
+static int aggregate(Level& L, int level, double theta, int distance, cudaStream_t s) {
   const Bsr& A = *L.A;
   const int n = A.n_rows;
   DBuf<double> nrm((size_t)A.nnzb, s), dnrm(n, s);
@@ -584,7 +586,7 @@ static int aggregate(Level& L, int level, double theta, cudaStream_t s) {
     mis_round1_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, n, level, m1.p);
     TAM_LAUNCH_CHECK();
     mis_round2_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, m1.p, n, level,
-                                                       und.p);
+                                                       distance, und.p);
     TAM_LAUNCH_CHECK();
     if (read_back_int(und.p, s) == 0) break;
     TAM_CHECK(it < 999, TAM_ERR_INTERNAL, "amg_setup: MIS-2 did not terminate");
@@ -679,13 +681,38 @@ static void alloc_level_vectors(Level& L, cudaStream_t s) {
   L.y = DBuf<double>(N, s);
 }
 
+// Setup phase timing with CUDA events (no extra synchronisation): the time
+// between mark(p) and the next mark is charged to phase p.
+struct PhaseTimer {
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  void mark(int phase, cudaStream_t s) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    marks.emplace_back(phase, e);
+  }
+  void finish(double* ms) {
+    for (size_t i = 0; i + 1 < marks.size(); ++i) {
+      float t = 0.f;
+      if (marks[i].first >= 0 && cudaEventElapsedTime(&t, marks[i].second, marks[i + 1].second) == cudaSuccess)
+        ms[marks[i].first] += t;
+    }
+  }
+  ~PhaseTimer() {
+    for (auto& m : marks) cudaEventDestroy(m.second);
+  }
+};
+
 tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& prm, cudaStream_t s) {
-  TAM_CHECK(prm.level_precision == 0, TAM_ERR_UNSUPPORTED, "amg_setup: only the FP64 hierarchy is built");
+  TAM_CHECK(prm.level_precision >= 0 && prm.level_precision <= 2, TAM_ERR_INVALID_ARG,
+            "amg_setup: level_precision must be 0 (FP64), 1 (FP32) or 2 (FP32, BF16 finest values)");
   TAM_CHECK(prm.smoother_degree >= 1 && prm.smoother_degree <= 8 && prm.eig_iters >= 1 && prm.eig_iters <= 64 &&
-                prm.max_levels >= 1 && prm.max_levels <= 20 && prm.coarse_max_dofs >= 1 &&
+                prm.max_levels >= 1 && prm.max_levels <= 20 && prm.coarse_max_dofs >= 1 && prm.coarse_min_dofs >= 0 &&
+                prm.small_level_dofs >= 0 && prm.small_level_degree >= 1 && prm.small_level_degree <= 32 &&
                 prm.cheb_hi > prm.cheb_lo && prm.cheb_lo > 0 && prm.strength_theta >= 0,
             TAM_ERR_INVALID_ARG, "amg_setup: parameter out of range");
   auto H = new tam_amg_s();
+  PhaseTimer T;
   try {
     H->K = K;
     H->prm = prm;
@@ -693,7 +720,7 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
     H->max_grid = 8 * 1024;
     {
       unsigned g0 = sell_grid(K->S);
-      H->max_grid = std::max<int>(H->max_grid, (int)g0);
+      H->max_grid = std::max<int>(65536, (int)g0);  // covers every reducing SpMV launch of the hierarchy
     }
     H->partials = DBuf<double>((size_t)H->max_grid * 4, s);
     H->ticket = DBuf<unsigned int>(1, s);
@@ -711,46 +738,65 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
     H->levels.emplace_back();
     H->levels[0].A = &K->A;
     H->levels[0].AS = &K->S;
+    H->levels[0].Aop = SpOp{&K->A, &K->S, choose_lpr(K->A)};
     for (int lev = 0;; ++lev) {
       Level& L = H->levels[lev];
       L.n_rows = L.A->n_rows;
       L.bs = L.A->br;
       L.kdim = k;
+      L.deg = (long long)L.n_rows * L.bs <= prm.small_level_dofs ? prm.small_level_degree : prm.smoother_degree;
       L.dinv = DBuf<double>((size_t)L.n_rows * L.bs, s);
+      T.mark(0, s);
       point_dinv_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.A->row_ptr.p, L.A->col_idx.p, L.A->vals.p, L.n_rows,
                                                                 L.bs, L.dinv.p);
       TAM_LAUNCH_CHECK();
       lanczos_lambda(H, L, lev, s);
       alloc_level_vectors(L, s);
       const bool last = (long long)L.n_rows * L.bs <= prm.coarse_max_dofs || lev == prm.max_levels - 1;
-      if (!last) L.n_agg = aggregate(L, lev, prm.strength_theta, s);
+      if (!last) {
+        T.mark(1, s);
+        L.n_agg = aggregate(L, lev, prm.strength_theta, 2, s);
+        // a distance-2 aggregation that would leave too small a coarse grid is
+        // redone with distance-1 roots (smaller aggregates)
+        if (prm.coarse_min_dofs > 0 && (long long)L.n_agg * k < prm.coarse_min_dofs)
+          L.n_agg = aggregate(L, lev, prm.strength_theta, 1, s);
+      }
       if (last || L.n_agg == 0 || L.n_agg >= L.n_rows) {
         L.n_agg = 0;
         L.agg.reset();
+        T.mark(7, s);
         coarse_inverse(H, L, s);
         break;
       }
       DBuf<double> Bc;
+      T.mark(2, s);
       tentative(L, B.p, 1e-10, Bc, s);
       // P = (I - omega D^-1 A) P_tent, computed on the pattern of A P_tent
+      T.mark(3, s);
       bsr_spgemm(*L.A, L.Pt, L.P, s);
       smooth_prolongator_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p,
                                                                         L.n_rows, L.bs, k, L.dinv.p, L.consts.p,
                                                                         L.agg.p, L.Pt.row_ptr.p, L.Pt.vals.p);
       TAM_LAUNCH_CHECK();
+      T.mark(4, s);
       bsr_transpose(L.P, L.R, s);
       {
         Bsr AP;
+        T.mark(5, s);
         bsr_spgemm(*L.A, L.P, AP, s);
         H->levels.emplace_back();
         Level& C = H->levels[lev + 1];
         bsr_spgemm(L.R, AP, C.A_own, s);
         C.A = &C.A_own;
         C.AS = &C.AS_own;
-        bsr_to_sell(C.A_own, C.AS_own, s);
+        C.Aop = SpOp{&C.A_own, &C.AS_own, choose_lpr(C.A_own)};
+        if (C.Aop.lpr == 0) bsr_to_sell(C.A_own, C.AS_own, s);
       }
-      bsr_to_sell(L.P, L.PS, s);
-      bsr_to_sell(L.R, L.RS, s);
+      L.Pop = SpOp{&L.P, &L.PS, choose_lpr(L.P)};
+      L.Rop = SpOp{&L.R, &L.RS, choose_lpr(L.R)};
+      T.mark(6, s);
+      if (L.Pop.lpr == 0) bsr_to_sell(L.P, L.PS, s);
+      if (L.Rop.lpr == 0) bsr_to_sell(L.R, L.RS, s);
       B = std::move(Bc);
     }
     H->r = DBuf<double>((size_t)n0 * 3, s);
@@ -758,7 +804,13 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
     H->p = DBuf<double>((size_t)n0 * 3, s);
     H->q = DBuf<double>((size_t)n0 * 3, s);
     H->sc = DBuf<PcgScalars>(1, s);
+    if (prm.level_precision > 0) {
+      T.mark(6, s);
+      build_low_precision(H, s);
+    }
+    T.mark(-1, s);
     TAM_CUDA(cudaStreamSynchronize(s));
+    T.finish(H->setup_ms);
   } catch (...) {
     delete H;
     throw;

@@ -121,6 +121,9 @@ int amg_params_default(amg_params* p) {
     p->cheb_hi = 1.1;
     p->eig_iters = 10;
     p->coarse_max_dofs = 2000;
+    p->coarse_min_dofs = 500;
+    p->small_level_dofs = 20000;
+    p->small_level_degree = 16;
     p->max_levels = 10;
     p->use_rotations = 1;
     p->level_precision = 0;
@@ -157,6 +160,14 @@ int amg_info(tam_amg amg, int* n_levels, long long* level_rows, long long* level
       if (l == 0) fine = nz;
     }
     if (op_complexity) *op_complexity = fine > 0 ? tot / fine : 0.0;
+    return TAM_OK;
+  });
+}
+
+int amg_setup_stats(tam_amg amg, double* phase_ms_host) {
+  return guarded([&] {
+    TAM_CHECK(amg && phase_ms_host, TAM_ERR_INVALID_ARG, "amg_setup_stats: NULL argument");
+    for (int i = 0; i < 8; ++i) phase_ms_host[i] = amg->setup_ms[i];
     return TAM_OK;
   });
 }

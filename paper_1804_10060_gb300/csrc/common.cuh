@@ -3,6 +3,7 @@
 // small warp-level sorts used by the symbolic (pattern-building) phases.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -32,6 +32,7 @@ struct Level {
   int n_rows = 0;     // block rows
   int bs = 0;         // block size of A on this level
   int kdim = 0;       // near-nullspace columns (block size of the next level)
+  int deg = 2;        // Chebyshev degree used on this level
   const Bsr* A = nullptr;   // level 0: the matrix handle's K
   const Sell* AS = nullptr;
   Bsr A_own;
@@ -42,9 +43,16 @@ struct Level {
   int n_agg = 0;
   Bsr Pt, P, R;             // tentative prolongator, smoothed prolongator, R = P^T
   Sell PS, RS;
+  SpOp Aop, Pop, Rop;       // SpMV strategy per operator (SELL thread-per-row or lanes per row)
   // V-cycle work vectors (n_rows*bs each)
   DBuf<double> b, xa, xb, d, t, y;  // y: the level's V-cycle result (never an internal buffer)
   double lambda_host = 0.0;
+  // reduced-precision V-cycle (level_precision 1: FP32; 2: FP32 with BF16 finest-level values)
+  DBuf<float> dinv32, consts32, b32, xa32, xb32, d32, t32, y32;
+  DBuf<float> A32v, P32v, R32v;
+  DBuf<__nv_bfloat16> A16v;
+  SpOpLow<float> A32, P32, R32;
+  SpOpLow<__nv_bfloat16> A16;
 };
 
 }  // namespace tam
@@ -67,6 +75,7 @@ struct tam_amg_s {
   double* graph_x = nullptr;
   cudaStream_t graph_stream = nullptr;
   long long graph_kernels = 0;           // kernel nodes in iter_exec
+  double setup_ms[8] = {};               // setup phase times, see amg_setup_stats
   ~tam_amg_s();
 };
 
@@ -81,6 +90,10 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
 
 // One V-cycle z = M^-1 r on level 0 (r, z device vectors of the fine size).
 void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s);
+// The reduced-precision V-cycle (FP32 vectors and arithmetic; FP64 in/out on
+// level 0 and FP64 dense coarsest solve), and its set-up after amg_build.
+void vcycle_apply_low(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s);
+void build_low_precision(tam_amg_s* H, cudaStream_t s);
 
 int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
               double* rel, cudaStream_t s);

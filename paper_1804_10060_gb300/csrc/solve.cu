@@ -236,31 +236,31 @@ void cheb_step(const Level& L, const double* b, const double* x, double* d, doub
                cudaStream_t s) {
   const double* coef = L.consts.p + 2 + 2 * step;
   if (L.bs == 3)
-    sell_spmv<3, 3>(*L.AS, x, EpiCheb<3>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
+    spop_apply<3, 3>(L.Aop, x, EpiCheb<3>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
   else
-    sell_spmv<6, 6>(*L.AS, x, EpiCheb<6>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
+    spop_apply<6, 6>(L.Aop, x, EpiCheb<6>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
 }
 
 void residual(const Level& L, const double* b, const double* x, double* t, const int* stop, cudaStream_t s) {
   if (L.bs == 3)
-    sell_spmv<3, 3>(*L.AS, x, EpiResidual<3>{b, t, L.n_rows, stop}, s);
+    spop_apply<3, 3>(L.Aop, x, EpiResidual<3>{b, t, L.n_rows, stop}, s);
   else
-    sell_spmv<6, 6>(*L.AS, x, EpiResidual<6>{b, t, L.n_rows, stop}, s);
+    spop_apply<6, 6>(L.Aop, x, EpiResidual<6>{b, t, L.n_rows, stop}, s);
 }
 
 void restrict_to(const Level& L, const double* t, double* bc, const int* stop, cudaStream_t s) {
   // R: rows = coarse nodes (kdim), cols = fine nodes (bs)
-  const int nr = L.RS.n_rows;
-  if (L.kdim == 6 && L.bs == 3) sell_spmv<6, 3>(L.RS, t, EpiStore<6>{bc, nr, stop}, s);
-  else if (L.kdim == 6 && L.bs == 6) sell_spmv<6, 6>(L.RS, t, EpiStore<6>{bc, nr, stop}, s);
-  else sell_spmv<3, 3>(L.RS, t, EpiStore<3>{bc, nr, stop}, s);
+  const int nr = L.R.n_rows;
+  if (L.kdim == 6 && L.bs == 3) spop_apply<6, 3>(L.Rop, t, EpiStore<6>{bc, nr, stop}, s);
+  else if (L.kdim == 6 && L.bs == 6) spop_apply<6, 6>(L.Rop, t, EpiStore<6>{bc, nr, stop}, s);
+  else spop_apply<3, 3>(L.Rop, t, EpiStore<3>{bc, nr, stop}, s);
 }
 
 void prolong_add(const Level& L, const double* xc, double* x, const int* stop, cudaStream_t s) {
-  const int nr = L.PS.n_rows;
-  if (L.kdim == 6 && L.bs == 3) sell_spmv<3, 6>(L.PS, xc, EpiAdd<3>{x, nr, stop}, s);
-  else if (L.kdim == 6 && L.bs == 6) sell_spmv<6, 6>(L.PS, xc, EpiAdd<6>{x, nr, stop}, s);
-  else sell_spmv<3, 3>(L.PS, xc, EpiAdd<3>{x, nr, stop}, s);
+  const int nr = L.P.n_rows;
+  if (L.kdim == 6 && L.bs == 3) spop_apply<3, 6>(L.Pop, xc, EpiAdd<3>{x, nr, stop}, s);
+  else if (L.kdim == 6 && L.bs == 6) spop_apply<6, 6>(L.Pop, xc, EpiAdd<6>{x, nr, stop}, s);
+  else spop_apply<3, 3>(L.Pop, xc, EpiAdd<3>{x, nr, stop}, s);
 }
 
 // V-cycle on level l with rhs b; the result lands in *out (level 0: caller's z)
@@ -273,7 +273,7 @@ void vcycle_level(tam_amg_s* H, int l, const double* b, double* out, const int* 
     TAM_LAUNCH_CHECK();
     return;
   }
-  const int deg = H->prm.smoother_degree;
+  const int deg = L.deg;
   double* xa = L.xa.p;
   double* xb = L.xb.p;
   // pre-smoothing from zero
@@ -298,6 +298,12 @@ void vcycle_level(tam_amg_s* H, int l, const double* b, double* out, const int* 
   }
 }
 
+// z = M^-1 r with the hierarchy's V-cycle precision
+void precondition(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s) {
+  if (H->prm.level_precision > 0) vcycle_apply_low(H, r, z, stop, s);
+  else vcycle_level(H, 0, r, z, stop, s);
+}
+
 void spmv_outer_pq(tam_amg_s* H, cudaStream_t s) {
   GridReduce gr{H->partials.p, H->ticket.p};
   sell_spmv<3, 3>(H->K->S, H->p.p, EpiPq<3>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s);
@@ -310,7 +316,7 @@ void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
   spmv_outer_pq(H, s);
   pcg_update_kernel<<<vec_grid(N), TPB, 0, s>>>(x, H->r.p, H->p.p, H->q.p, N, gr, H->sc.p);
   TAM_LAUNCH_CHECK();
-  vcycle_level(H, 0, H->r.p, H->z.p, stop, s);
+  precondition(H, H->r.p, H->z.p, stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, H->sc.p, 0);
   TAM_LAUNCH_CHECK();
   pcg_direction_kernel<<<vec_grid(N), TPB, 0, s>>>(H->z.p, H->p.p, N, H->sc.p);
@@ -334,7 +340,7 @@ double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaSt
 }
 
 void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s) {
-  vcycle_level(H, 0, r, z, stop, s);
+  precondition(H, r, z, stop, s);
 }
 
 int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
@@ -346,7 +352,7 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   pcg_start_kernel<<<vec_grid(N), TPB, 0, s>>>(b, N, gr, sc, rtol, atol, max_iter);
   TAM_LAUNCH_CHECK();
   sell_spmv<3, 3>(H->K->S, x, EpiInitResidual<3>{b, H->r.p, H->K->n_nodes, gr, sc}, s);
-  vcycle_level(H, 0, H->r.p, H->z.p, &sc->stop, s);
+  precondition(H, H->r.p, H->z.p, &sc->stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, sc, 1);
   TAM_LAUNCH_CHECK();
   // one iteration as a CUDA graph, rebuilt if the target vector changed

@@ -1,5 +1,7 @@
 // Block-sparse building blocks of the AMG setup: SELL-32 conversion, block
 // transpose and the block SpGEMM C = X * Y used for A P_tent and R (A P).
+#include <algorithm>
+
 #include "sparse.cuh"
 
 namespace tam {
@@ -155,16 +157,14 @@ void bsr_transpose(const Bsr& A, Bsr& R, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // SpGEMM C = X Y.  Symbolic: one warp per row inserts the candidate columns
 // into a shared-memory hash set (open addressing), counts, and in the fill
-// pass compacts and bitonic-sorts them.  Numeric: one warp per row
-// accumulates the row's output blocks in shared memory, a window of columns
-// at a time; lanes own block ELEMENTS, so accumulation needs no atomics.
+// pass compacts and bitonic-sorts them.  Numeric: one thread per output block
+// (see spgemm_numeric_os_kernel).
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int SG_WARPS = 4;
 constexpr int HT = 2048;            // hash slots per warp
 constexpr int HT_MAX = 1536;        // max unique columns per row (load 0.75)
-constexpr int ACC_BYTES = 16384;    // numeric accumulator per warp
 
 __device__ __forceinline__ bool ht_insert(int* tab, int col) {
   unsigned h = ((unsigned)col * 2654435761u) & (HT - 1);
@@ -227,80 +227,70 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   for (int i = lane; i < cnt; i += 32) cci[c0 + i] = tab[i];
 }
 
-// dynamic smem: SG_WARPS * (ACC_BYTES + wcap*4)
+// Output-stationary numeric pass: one thread per output block C_ic.  It walks
+// X's row i, finds column c in Y's row j by binary search and accumulates
+// X_ij Y_jc in registers -- every FP64 FMA is useful work, nothing is shared
+// between threads (no atomics, no shared-memory windows), and the threads of
+// one output row read the same X row (L1 broadcast).
+__global__ void expand_rows_kernel(const int* __restrict__ rp, int n_rows, int* __restrict__ row_of) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rows) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) row_of[p] = i;
+}
+
 template <int M, int K, int N>
-__global__ void __launch_bounds__(SG_WARPS * 32)
-spgemm_numeric_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
-                      int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
-                      const double* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
-                      double* __restrict__ cv) {
-  constexpr int MN = M * N;
-  constexpr int W = ACC_BYTES / (MN * 8);
-  extern __shared__ double sm[];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * SG_WARPS + wid;
-  if (row >= n_rows) return;
-  double* acc = sm + (size_t)wid * (ACC_BYTES / 8);
-  int* wcols = reinterpret_cast<int*>(sm + (size_t)SG_WARPS * (ACC_BYTES / 8)) + wid * W;
-  const int cs = crp[row], ce = crp[row + 1];
-  const int xs = xrp[row], xe = xrp[row + 1];
-  for (int w0 = cs; w0 < ce; w0 += W) {
-    const int wn = min(W, ce - w0);
-    for (int i = lane; i < wn; i += 32) wcols[i] = cci[w0 + i];
-    for (int i = lane; i < wn * MN; i += 32) acc[i] = 0.0;
-    __syncwarp();
-    const int clo = wcols[0], chi = wcols[wn - 1];
-    for (int p = xs; p < xe; ++p) {
-      const int j = xci[p];
-      const double* xb = xv + (size_t)p * M * K;
-      int qs = yrp[j], qe = yrp[j + 1];
-      // first entry of Y row j with col >= clo
-      {
-        int lo = qs, hi = qe;
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          if (yci[mid] < clo) lo = mid + 1; else hi = mid;
-        }
-        qs = lo;
-      }
-      for (int q = qs; q < qe; ++q) {
-        const int c = yci[q];
-        if (c > chi) break;
-        // position of c in the window (present by construction)
-        int lo = 0, hi = wn - 1;
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          if (wcols[mid] < c) lo = mid + 1; else hi = mid;
-        }
-        const double* yb = yv + (size_t)q * K * N;
-        for (int e = lane; e < MN; e += 32) {
-          const int r = e / N, s2 = e % N;
-          double a = acc[lo * MN + e];
+__global__ void __launch_bounds__(128)
+spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
+                         const int* __restrict__ yrp, const int* __restrict__ yci, const double* __restrict__ yv,
+                         const int* __restrict__ crow, const int* __restrict__ cci, long long nnzc,
+                         double* __restrict__ cv) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzc) return;
+  const int i = crow[t], c = cci[t];
+  double acc[M * N];
 #pragma unroll
-          for (int t = 0; t < K; ++t) a = fma(xb[r * K + t], yb[t * N + s2], a);
-          acc[lo * MN + e] = a;
-        }
+  for (int e = 0; e < M * N; ++e) acc[e] = 0.0;
+  const int pe = xrp[i + 1];
+  for (int p = xrp[i]; p < pe; ++p) {
+    const int j = xci[p];
+    int lo = yrp[j], hi = yrp[j + 1];
+    const int end = hi;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (yci[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    if (lo < end && yci[lo] == c) {
+      const double* __restrict__ xb = xv + (size_t)p * M * K;
+      const double* __restrict__ yb = yv + (size_t)lo * K * N;
+      double xr[M * K];
+#pragma unroll
+      for (int e = 0; e < M * K; ++e) xr[e] = xb[e];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        double yr[N];
+#pragma unroll
+        for (int s2 = 0; s2 < N; ++s2) yr[s2] = yb[k * N + s2];
+#pragma unroll
+        for (int r = 0; r < M; ++r)
+#pragma unroll
+          for (int s2 = 0; s2 < N; ++s2) acc[r * N + s2] = fma(xr[r * K + k], yr[s2], acc[r * N + s2]);
       }
     }
-    __syncwarp();
-    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = acc[i];
-    __syncwarp();
   }
+  double* out = cv + (size_t)t * M * N;
+#pragma unroll
+  for (int e = 0; e < M * N; ++e) out[e] = acc[e];
 }
 
 template <int M, int K, int N>
 void launch_numeric(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
-  constexpr int W = ACC_BYTES / (M * N * 8);
-  size_t smem = (size_t)SG_WARPS * (ACC_BYTES + W * 4);
-  static bool attr_set = false;
-  if (!attr_set) {
-    TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_kernel<M, K, N>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
-  spgemm_numeric_kernel<M, K, N><<<grid_for(X.n_rows, SG_WARPS), SG_WARPS * 32, smem, s>>>(
-      X.row_ptr.p, X.col_idx.p, X.vals.p, X.n_rows, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, C.row_ptr.p,
-      C.col_idx.p, C.vals.p);
+  if (C.nnzb == 0) return;
+  DBuf<int> crow((size_t)C.nnzb, s);
+  expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
+  TAM_LAUNCH_CHECK();
+  spgemm_numeric_os_kernel<M, K, N><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
+      X.row_ptr.p, X.col_idx.p, X.vals.p, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, crow.p, C.col_idx.p, C.nnzb,
+      C.vals.p);
   TAM_LAUNCH_CHECK();
 }
 
@@ -338,6 +328,48 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
   else if (m == 6 && k == 6 && n == 3) launch_numeric<6, 6, 3>(X, Y, C, s);
   else if (m == 3 && k == 6 && n == 6) launch_numeric<3, 6, 6>(X, Y, C, s);
   else throw Error(TAM_ERR_UNSUPPORTED, "spgemm: block shape not instantiated");
+}
+
+// ---------------------------------------------------------------------------
+// Reduced-precision value copies
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+__global__ void convert_kernel(const double* __restrict__ in, T* __restrict__ out, long long n);
+template <>
+__global__ void convert_kernel<float>(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __double2float_rn(in[i]);
+}
+template <>
+__global__ void convert_kernel<__nv_bfloat16>(const double* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                                              long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __double2bfloat16(in[i]);
+}
+
+template <typename T>
+void convert_values(const SpOp& op, DBuf<T>& out, cudaStream_t s) {
+  const double* src;
+  long long n;
+  if (op.lpr == 0) {
+    src = op.S->vals.p;
+    n = op.S->n_slots * 32 * (long long)op.S->br * op.S->bc;
+  } else {
+    src = op.B->vals.p;
+    n = op.B->nnzb * (long long)op.B->block_elems();
+  }
+  out = DBuf<T>((size_t)std::max(1LL, n), s);
+  if (n > 0) {
+    convert_kernel<T><<<std::min<unsigned>(grid_for(n, 256), 152u * 16u), 256, 0, s>>>(src, out.p, n);
+    TAM_LAUNCH_CHECK();
+  }
+}
+}  // namespace
+
+void convert_values_f32(const SpOp& op, DBuf<float>& out, cudaStream_t s) { convert_values<float>(op, out, s); }
+void convert_values_bf16(const SpOp& op, DBuf<__nv_bfloat16>& out, cudaStream_t s) {
+  convert_values<__nv_bfloat16>(op, out, s);
 }
 
 }  // namespace tam

@@ -257,8 +257,9 @@ def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
     """
     n_t = n_blades * n_theta_per_blade
     r_in, r_out, r_tip, thick = 0.2, 1.0, 1.3, 0.1
-    r_nodes = np.concatenate([np.linspace(r_in, r_out, n_r + 1),
-                              np.linspace(r_out, r_tip, n_r_blade + 1)[1:]])
+    # geometric radial spacing keeps cells near-isotropic: dr ~ r dtheta
+    r_nodes = np.concatenate([np.geomspace(r_in, r_out, n_r + 1),
+                              np.geomspace(r_out, r_tip, n_r_blade + 1)[1:]])
     n_rr = r_nodes.size
     z_nodes = np.linspace(-0.5 * thick, 0.5 * thick, n_z + 1)
     t_nodes = np.arange(n_t) * (2.0 * np.pi / n_t)
@@ -302,7 +303,7 @@ def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
     cells[neg] = cells[neg][:, [0, 1, 3, 2]]
     # seeded jitter of interior nodes (not on the bore, rim faces or blade surfaces)
     rng = np.random.default_rng(seed)
-    h = min(thick / n_z, (r_out - r_in) / n_r, 2 * np.pi * r_in / n_t)
+    h = min(thick / n_z, r_nodes[1] - r_nodes[0], 2 * np.pi * r_in / n_t)
     cnt = np.zeros(coords.shape[0], np.int64)
     np.add.at(cnt, cells.ravel(), 1)
     # interior nodes of a Kuhn lattice touch 24 tets

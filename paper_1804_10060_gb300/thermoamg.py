@@ -38,6 +38,9 @@ class AmgParams(ctypes.Structure):
         ("cheb_hi", ctypes.c_double),
         ("eig_iters", ctypes.c_int),
         ("coarse_max_dofs", ctypes.c_int),
+        ("coarse_min_dofs", ctypes.c_int),
+        ("small_level_dofs", ctypes.c_int),
+        ("small_level_degree", ctypes.c_int),
         ("max_levels", ctypes.c_int),
         ("use_rotations", ctypes.c_int),
         ("level_precision", ctypes.c_int),
@@ -61,6 +64,7 @@ _SIGNATURES = {
     "amg_params_default": ([ctypes.POINTER(AmgParams)], _i),
     "amg_setup": ([_vp, _vp, ctypes.POINTER(AmgParams), ctypes.POINTER(_vp), _vp], _i),
     "amg_info": ([_vp, _pi, _pll, _pll, _pi, _pd, _pd], _i),
+    "amg_setup_stats": ([_vp, _pd], _i),
     "amg_level_aggregates": ([_vp, _i, _vp, _vp], _i),
     "amg_level_export": ([_vp, _i, _i, _pi, _pi, _pi, _pi, _pll, _vp, _vp, _vp, _vp], _i),
     "amg_vcycle": ([_vp, _vp, _vp, _vp], _i),
@@ -237,6 +241,17 @@ def amg_info(amg: Amg) -> dict:
     _check(lib.amg_info(amg.handle, ctypes.byref(L), rows, nnzb, blk, lam, ctypes.byref(oc)))
     return {"n_levels": n, "rows": list(rows), "nnzb": list(nnzb), "block": list(blk), "lambda": list(lam),
             "op_complexity": oc.value}
+
+
+SETUP_PHASES = ("lambda_max", "aggregation", "tentative", "smoothing", "transpose", "galerkin", "layout",
+                "coarse_inverse")
+
+
+def amg_setup_stats(amg: Amg) -> dict:
+    """Setup phase device times in ms (CUDA events), keyed by phase name."""
+    buf = (ctypes.c_double * 8)()
+    _check(lib.amg_setup_stats(amg.handle, buf))
+    return dict(zip(SETUP_PHASES, list(buf)))
 
 
 def amg_level_aggregates(amg: Amg, level: int, stream=None):

@@ -35,12 +35,13 @@ def _export(tam, H, level, which):
     return bsr_to_csr(e["row_ptr"], e["col_idx"], e["vals"], e["n_cols"]), e
 
 
+@pytest.mark.parametrize("coarse_min", [0, 500])
 @pytest.mark.parametrize("problem", ["cube8", "slab_small", "cube_p2"])
-def test_hierarchy_matches_oracle_step_by_step(problem):
+def test_hierarchy_matches_oracle_step_by_step(problem, coarse_min):
     pb = {"cube8": lambda: meshgen.unit_cube_problem(8),
           "slab_small": lambda: meshgen.slab_box_problem(24, 8, 8),
           "cube_p2": lambda: meshgen.unit_cube_problem(4, 2)}[problem]()
-    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60)
+    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60, coarse_min_dofs=coarse_min)
     info = tam.amg_info(H)
     assert info["n_levels"] >= 2
     Ko, fo = fem.assemble_system(pb)
@@ -55,7 +56,7 @@ def test_hierarchy_matches_oracle_step_by_step(problem):
         # aggregation: unique under the priority rule -> bit-exact
         agg_g = tam.amg_level_aggregates(H, lev).cpu().numpy()
         nbrs = oamg.strength_graph(Ag, bs, 0.0)
-        agg_o, n_agg, _ = oamg.mis2_aggregate(nbrs, lev)
+        agg_o, n_agg = oamg.aggregate_level(nbrs, lev, 6, coarse_min)
         assert np.array_equal(agg_g, agg_o), f"aggregates level {lev}"
         assert oamg.check_aggregates(agg_g, n_agg, nbrs) == []
         # tentative prolongator from the same aggregates and near-nullspace
