@@ -146,11 +146,12 @@ typedef struct amg_params {
   double cheb_hi;          /* 1.1                                                                    */
   int eig_iters;           /* Lanczos steps for lambda_max(D^-1 A); default 10                        */
   int coarse_max_dofs;     /* stop coarsening at or below this many DOFs; default 2000                */
+  int aggressive_levels;   /* levels aggregated with distance-2 roots (fast coarsening); distance-1
+                              roots below; default 1                                                */
   int coarse_min_dofs;     /* redo a distance-2 aggregation with distance-1 roots when it would give
                               fewer coarse DOFs than this (0 = never); default 500                  */
   int small_level_dofs;    /* smoothed levels with at most this many DOFs use ...                     */
-  int small_level_degree;  /* ... this Chebyshev degree (they are cheap and, above an aggressively
-                              coarsened coarsest grid, must nearly solve their problem); 20000, 16 */
+  int small_level_degree;  /* ... this Chebyshev degree instead of smoother_degree; default 0 (off), 16 */
   int max_levels;          /* including the finest; default 10                                       */
   int use_rotations;       /* 1: six rigid-body modes; 0: three translations only; default 1         */
   int level_precision;     /* V-cycle storage/arithmetic: 0 FP64; 1 FP32; 2 FP32 with BF16 finest-level

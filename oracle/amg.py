@@ -320,14 +320,18 @@ class Hierarchy:
 
 
 DEFAULTS = dict(theta=0.0, degree=2, cheb_lo=0.1, cheb_hi=1.1, eig_steps=10,
-                coarse_max_dofs=2000, coarse_min_dofs=500, small_level_dofs=20000,
+                coarse_max_dofs=2000, coarse_min_dofs=500, aggressive_levels=1, small_level_dofs=0,
                 small_level_degree=16, max_levels=10, droptol=1e-10)
 
 
-def aggregate_level(nbrs, level, k, coarse_min_dofs):
-    """Distance-2 aggregation, redone with distance-1 roots when it would leave
-    fewer than coarse_min_dofs coarse DOFs (k per aggregate): the paper asks
-    for fast coarsening but also finds a larger coarsest grid more robust."""
+def aggregate_level(nbrs, level, k, coarse_min_dofs, aggressive_levels=99):
+    """Distance-2 aggregation on the first `aggressive_levels` levels (distance-1
+    after), redone with distance-1 roots when it would leave fewer than
+    coarse_min_dofs coarse DOFs (k per aggregate): the paper asks for fast
+    coarsening but also finds a larger coarsest grid more robust."""
+    if level >= aggressive_levels:
+        agg, n_agg, _ = mis2_aggregate(nbrs, level, distance=1)
+        return agg, n_agg
     agg, n_agg, _ = mis2_aggregate(nbrs, level)
     if coarse_min_dofs and n_agg * k < coarse_min_dofs:
         agg, n_agg, _ = mis2_aggregate(nbrs, level, distance=1)
@@ -347,7 +351,8 @@ def setup(A, B, bs=3, **kw):
         if A.shape[0] <= prm["coarse_max_dofs"] or lev == prm["max_levels"] - 1:
             break
         nbrs = strength_graph(A, bs, prm["theta"])
-        agg, n_agg = aggregate_level(nbrs, lev, B.shape[1], prm["coarse_min_dofs"])
+        agg, n_agg = aggregate_level(nbrs, lev, B.shape[1], prm["coarse_min_dofs"],
+                                     prm["aggressive_levels"])
         if n_agg == 0 or n_agg >= A.shape[0] // bs:
             break
         Pt, Bc = tentative_prolongator(agg, n_agg, B, bs, prm["droptol"])

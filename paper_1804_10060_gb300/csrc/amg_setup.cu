@@ -8,11 +8,15 @@
 // six rigid-body modes on the finest level), prolongator smoothing
 // P = (I - 4/(3 lambda) D^-1 A) P_tent, R = P^T and the Galerkin product
 // A_c = R A P.  The coarsest operator is inverted densely (Gauss-Jordan).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "handles.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tam {
 namespace {
@@ -482,34 +486,39 @@ __global__ void dense_inactive_kernel(double* __restrict__ D, int N, unsigned ch
   }
 }
 
-__global__ void gj_pivot_kernel(double* __restrict__ D, int N, int k, double* __restrict__ colk, double* __restrict__ pivinv,
-                                int* __restrict__ bad) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N) return;
-  const double p = D[(size_t)k * N + k];
-  if (t == 0) {
-    if (!(p > 0.0)) atomicExch(bad, 1);
-    *pivinv = 1.0 / p;
+// In-place Gauss-Jordan inversion of an SPD matrix (no pivoting needed).  Step
+// k: (a) save column k and divide row k by the pivot p = D_kk; (b) for i != k:
+// D_ij -= D_ik(old) * D_kj(new) (j != k), D_ik = -D_ik(old) / p, and D_kk = 1/p.
+// The grid-wide barrier separates (a) from (b) and each step from the next;
+// the kernel is launched cooperatively, so all blocks are co-resident.
+__global__ void __launch_bounds__(256) gj_coop_kernel(double* __restrict__ D, int N, double* __restrict__ colk,
+                                                      int* __restrict__ bad) {
+  cg::grid_group grid = cg::this_grid();
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long NN = (long long)N * N;
+  for (int k = 0; k < N; ++k) {
+    const double p = D[(size_t)k * N + k];  // not written in phase (a)
+    if (tid == 0 && !(p > 0.0)) *bad = 1;
+    for (long long t = tid; t < N; t += nth)
+      if (t != k) {
+        colk[t] = D[(size_t)t * N + k];
+        D[(size_t)k * N + t] /= p;
+      }
+    grid.sync();
+    const double inv = 1.0 / p;
+    for (long long e = tid; e < NN; e += nth) {
+      const int i = (int)(e / N), j = (int)(e % N);
+      if (i == k) {
+        if (j == k) D[(size_t)k * N + k] = inv;
+        continue;
+      }
+      const double f = colk[i];
+      if (j == k) D[(size_t)i * N + k] = -f * inv;
+      else D[(size_t)i * N + j] -= f * D[(size_t)k * N + j];
+    }
+    grid.sync();
   }
-  if (t != k) {
-    colk[t] = D[(size_t)t * N + k];
-    D[(size_t)k * N + t] /= p;
-  }
-}
-
-__global__ void gj_update_kernel(double* __restrict__ D, int N, int k, const double* __restrict__ colk,
-                                 const double* __restrict__ pivinv) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y;
-  if (j >= N) return;
-  const double inv = *pivinv;
-  if (i == k) {
-    if (j == k) D[(size_t)k * N + k] = inv;
-    return;
-  }
-  const double f = colk[i];
-  if (j == k) D[(size_t)i * N + k] = -f * inv;
-  else D[(size_t)i * N + j] -= f * D[(size_t)k * N + j];
 }
 
 __global__ void dense_zero_inactive_kernel(double* __restrict__ D, int N, const unsigned char* __restrict__ inactive) {
@@ -657,14 +666,24 @@ static void coarse_inverse(tam_amg_s* H, const Level& L, cudaStream_t s) {
   DBuf<unsigned char> inactive(N, s);
   dense_inactive_kernel<<<N, 128, 0, s>>>(H->coarse_inv.p, N, inactive.p);
   TAM_LAUNCH_CHECK();
-  DBuf<double> colk(N, s), pinv(1, s);
+  DBuf<double> colk(N, s);
   DBuf<int> bad(1, s);
   bad.zero();
   dim3 ug(grid_for(N, TPB), N);
-  for (int k = 0; k < N; ++k) {
-    gj_pivot_kernel<<<grid_for(N, TPB), TPB, 0, s>>>(H->coarse_inv.p, N, k, colk.p, pinv.p, bad.p);
-    gj_update_kernel<<<ug, TPB, 0, s>>>(H->coarse_inv.p, N, k, colk.p, pinv.p);
-  }
+  // all N pivot steps in one cooperative launch (grid-wide barrier between
+  // the two phases of a step) instead of 2N kernel launches
+  int dev = 0, n_sm = 0, per_sm = 0;
+  TAM_CUDA(cudaGetDevice(&dev));
+  TAM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  TAM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_coop_kernel, TPB, 0));
+  TAM_CHECK(per_sm >= 1, TAM_ERR_INTERNAL, "amg_setup: Gauss-Jordan kernel cannot be resident");
+  double* dp = H->coarse_inv.p;
+  double* cp = colk.p;
+  int* bp = bad.p;
+  int n_arg = N;
+  void* args[] = {&dp, &n_arg, &cp, &bp};
+  TAM_CUDA(cudaLaunchCooperativeKernel((const void*)gj_coop_kernel, dim3(n_sm * std::min(per_sm, 2)), dim3(TPB), args,
+                                       0, s));
   TAM_LAUNCH_CHECK();
   dense_zero_inactive_kernel<<<ug, TPB, 0, s>>>(H->coarse_inv.p, N, inactive.p);
   TAM_LAUNCH_CHECK();
@@ -707,7 +726,7 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
   TAM_CHECK(prm.level_precision >= 0 && prm.level_precision <= 2, TAM_ERR_INVALID_ARG,
             "amg_setup: level_precision must be 0 (FP64), 1 (FP32) or 2 (FP32, BF16 finest values)");
   TAM_CHECK(prm.smoother_degree >= 1 && prm.smoother_degree <= 8 && prm.eig_iters >= 1 && prm.eig_iters <= 64 &&
-                prm.max_levels >= 1 && prm.max_levels <= 20 && prm.coarse_max_dofs >= 1 && prm.coarse_min_dofs >= 0 &&
+                prm.max_levels >= 1 && prm.max_levels <= 20 && prm.coarse_max_dofs >= 1 && prm.coarse_min_dofs >= 0 && prm.aggressive_levels >= 0 &&
                 prm.small_level_dofs >= 0 && prm.small_level_degree >= 1 && prm.small_level_degree <= 32 &&
                 prm.cheb_hi > prm.cheb_lo && prm.cheb_lo > 0 && prm.strength_theta >= 0,
             TAM_ERR_INVALID_ARG, "amg_setup: parameter out of range");
@@ -755,10 +774,12 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       const bool last = (long long)L.n_rows * L.bs <= prm.coarse_max_dofs || lev == prm.max_levels - 1;
       if (!last) {
         T.mark(1, s);
-        L.n_agg = aggregate(L, lev, prm.strength_theta, 2, s);
-        // a distance-2 aggregation that would leave too small a coarse grid is
-        // redone with distance-1 roots (smaller aggregates)
-        if (prm.coarse_min_dofs > 0 && (long long)L.n_agg * k < prm.coarse_min_dofs)
+        // distance-2 (aggressive) roots on the first aggressive_levels levels,
+        // distance-1 below; an aggressive aggregation that would leave too
+        // small a coarse grid is redone with distance-1 roots
+        const bool aggressive = lev < prm.aggressive_levels;
+        L.n_agg = aggregate(L, lev, prm.strength_theta, aggressive ? 2 : 1, s);
+        if (aggressive && prm.coarse_min_dofs > 0 && (long long)L.n_agg * k < prm.coarse_min_dofs)
           L.n_agg = aggregate(L, lev, prm.strength_theta, 1, s);
       }
       if (last || L.n_agg == 0 || L.n_agg >= L.n_rows) {

@@ -121,8 +121,9 @@ int amg_params_default(amg_params* p) {
     p->cheb_hi = 1.1;
     p->eig_iters = 10;
     p->coarse_max_dofs = 2000;
+    p->aggressive_levels = 1;
     p->coarse_min_dofs = 500;
-    p->small_level_dofs = 20000;
+    p->small_level_dofs = 0;
     p->small_level_degree = 16;
     p->max_levels = 10;
     p->use_rotations = 1;

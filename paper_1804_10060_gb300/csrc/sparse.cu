@@ -282,9 +282,107 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   for (int e = 0; e < M * N; ++e) out[e] = acc[e];
 }
 
+// Row-stationary numeric pass for tall X blocks (M = 6: R (A P) and the coarse
+// levels): one warp per output row, the row's output blocks accumulated in
+// shared memory a window of W columns at a time.  For each X entry (i, j) the
+// lanes take the (Y-row entry q, block row r) items: item (q, r) computes row
+// r of X_ij Y_jq (K*N FMAs) and adds it to output block col(q).  Columns in a
+// Y row are distinct, so the items of one X entry never touch the same
+// accumulator element and no atomics are needed; X entries are processed one
+// after the other.  Most of the warp does useful FP64 work (items = M * |Y row|).
+constexpr int RS_WARPS = 4;
+constexpr int RS_ACC_BYTES = 16384;
+
+template <int M, int K, int N>
+__global__ void __launch_bounds__(RS_WARPS * 32)
+spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
+                         int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
+                         const double* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
+                         double* __restrict__ cv) {
+  constexpr int MN = M * N;
+  constexpr int W = RS_ACC_BYTES / (MN * 8);
+  extern __shared__ double sm[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * RS_WARPS + wid;
+  if (row >= n_rows) return;
+  double* acc = sm + (size_t)wid * (RS_ACC_BYTES / 8);
+  int* wcols = reinterpret_cast<int*>(sm + (size_t)RS_WARPS * (RS_ACC_BYTES / 8)) + wid * W;
+  const int cs = crp[row], ce = crp[row + 1];
+  const int xs = xrp[row], xe = xrp[row + 1];
+  for (int w0 = cs; w0 < ce; w0 += W) {
+    const int wn = min(W, ce - w0);
+    for (int i = lane; i < wn; i += 32) wcols[i] = cci[w0 + i];
+    for (int i = lane; i < wn * MN; i += 32) acc[i] = 0.0;
+    __syncwarp();
+    const int clo = wcols[0], chi = wcols[wn - 1];
+    for (int p = xs; p < xe; ++p) {
+      const int j = xci[p];
+      int qs = yrp[j], qe = yrp[j + 1];
+      if (wn < ce - cs) {  // restrict Y's row to the window's column range
+        int lo = qs, hi = qe;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (yci[mid] < clo) lo = mid + 1; else hi = mid;
+        }
+        qs = lo;
+        hi = qe;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (yci[mid] <= chi) lo = mid + 1; else hi = mid;
+        }
+        qe = lo;
+      }
+      const double* __restrict__ xb = xv + (size_t)p * M * K;
+      const int items = (qe - qs) * M;
+      for (int it = lane; it < items; it += 32) {
+        const int q = qs + it / M, r = it % M;
+        const int c = yci[q];
+        int lo = 0, hi = wn - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (wcols[mid] < c) lo = mid + 1; else hi = mid;
+        }
+        double xr[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) xr[k] = __ldg(xb + r * K + k);
+        const double* __restrict__ yb = yv + (size_t)q * K * N;
+        double* a = acc + lo * MN + r * N;
+#pragma unroll
+        for (int s2 = 0; s2 < N; ++s2) {
+          double t = a[s2];
+#pragma unroll
+          for (int k = 0; k < K; ++k) t = fma(xr[k], __ldg(yb + k * N + s2), t);
+          a[s2] = t;
+        }
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = acc[i];
+    __syncwarp();
+  }
+}
+
 template <int M, int K, int N>
 void launch_numeric(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
   if (C.nnzb == 0) return;
+  // 3-row blocks (A P_tent, A P on the finest level) keep the output-stationary
+  // pass: with only 3 rows per item the row-stationary warp idles (measured
+  // 2x slower on the 256x64x64 box).
+  if (M == 6) {
+    constexpr int W = RS_ACC_BYTES / (M * N * 8);
+    const size_t smem = (size_t)RS_WARPS * (RS_ACC_BYTES + W * 4);
+    static bool attr_set = false;
+    if (!attr_set) {
+      TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_rs_kernel<M, K, N>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_set = true;
+    }
+    spgemm_numeric_rs_kernel<M, K, N><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
+        X.row_ptr.p, X.col_idx.p, X.vals.p, X.n_rows, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, C.row_ptr.p,
+        C.col_idx.p, C.vals.p);
+    TAM_LAUNCH_CHECK();
+    return;
+  }
   DBuf<int> crow((size_t)C.nnzb, s);
   expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
   TAM_LAUNCH_CHECK();

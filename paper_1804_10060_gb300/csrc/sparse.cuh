@@ -12,6 +12,8 @@
 //         a shuffle tree, is the only arithmetic cost.
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tam {
@@ -157,12 +159,15 @@ struct SpOp {
 };
 
 // Strategy: thread-per-row SELL for many short rows, else lanes per row.
+// Each lane should own >= ~16 blocks: the closing shuffle reduction costs
+// log2(LPR) FP64 adds per output per lane, and on GB300 the FP64 pipe (not
+// bandwidth) is the limit, so a wide LPR on medium rows wastes it.
 inline int choose_lpr(const Bsr& A) {
   const double avg = A.n_rows > 0 ? (double)A.nnzb / A.n_rows : 0.0;
   if (A.n_rows >= 65536 && avg <= 48.0) return 0;
-  if (A.n_rows < 8192) return 32;
   int l = 2;
-  while (l < 32 && 2 * l < avg) l <<= 1;
+  while (l < 32 && 16 * l < avg) l <<= 1;
+  if (A.n_rows < 8192) l = std::max(l, 16);  // few rows: spread them over more lanes
   return l;
 }
 

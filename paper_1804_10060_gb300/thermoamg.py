@@ -38,6 +38,7 @@ class AmgParams(ctypes.Structure):
         ("cheb_hi", ctypes.c_double),
         ("eig_iters", ctypes.c_int),
         ("coarse_max_dofs", ctypes.c_int),
+        ("aggressive_levels", ctypes.c_int),
         ("coarse_min_dofs", ctypes.c_int),
         ("small_level_dofs", ctypes.c_int),
         ("small_level_degree", ctypes.c_int),

@@ -56,7 +56,7 @@ def test_hierarchy_matches_oracle_step_by_step(problem, coarse_min):
         # aggregation: unique under the priority rule -> bit-exact
         agg_g = tam.amg_level_aggregates(H, lev).cpu().numpy()
         nbrs = oamg.strength_graph(Ag, bs, 0.0)
-        agg_o, n_agg = oamg.aggregate_level(nbrs, lev, 6, coarse_min)
+        agg_o, n_agg = oamg.aggregate_level(nbrs, lev, 6, coarse_min, aggressive_levels=1)
         assert np.array_equal(agg_g, agg_o), f"aggregates level {lev}"
         assert oamg.check_aggregates(agg_g, n_agg, nbrs) == []
         # tentative prolongator from the same aggregates and near-nullspace
