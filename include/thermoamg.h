@@ -213,6 +213,58 @@ int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double a
 int amg_destroy(tam_amg amg);
 
 /* ------------------------------------------------------------------------
+ * Learned initial guess (an extension; the paper has no learned component).
+ * A node-wise multilayer perceptron maps per-node features to a displacement
+ * guess that seeds amg_pcg_solve; CG always iterates to the tolerance, so the
+ * network changes the iteration count, never the answer.  Network: n_in
+ * inputs, `depth` tanh layers of `width`, linear n_out outputs; inputs are
+ * standardised (x - shift) * scale, outputs multiplied by out_scale.
+ * Parameters: FP32, per layer W [fan_in x fan_out] row-major then bias, layers
+ * in order (Glorot-uniform init from SplitMix64(seed)).  Training minimises
+ * the mean squared error with Adam (beta 0.9, 0.999, eps 1e-8).
+ * All array arguments are device pointers unless named *_host.
+ */
+typedef struct tam_mlp_s* tam_mlp;
+
+int tam_mlp_create(int n_in, int width, int depth, int n_out, unsigned long long seed, tam_mlp* out);
+int tam_mlp_destroy(tam_mlp mlp);
+/* number of FP32 parameters and of layers */
+int tam_mlp_info(tam_mlp mlp, long long* n_params, int* n_layers);
+/* host arrays shift[n_in], scale[n_in], out_scale[n_out] */
+int tam_mlp_set_normalization(tam_mlp mlp, const float* shift_host, const float* scale_host,
+                              const float* out_scale_host);
+/* copy all parameters out of / into host memory (n_params floats) */
+int tam_mlp_get_params(tam_mlp mlp, float* theta_host);
+int tam_mlp_set_params(tam_mlp mlp, const float* theta_host);
+/* Y[n x n_out] = net(X[n x n_in]); bf16 != 0 reads BF16 copies of the weights */
+int tam_mlp_forward(tam_mlp mlp, long long n, const float* X, float* Y, int bf16, void* stream);
+/* mean squared error of net(X) against Yt and its gradient (grad_host: n_params
+ * floats, may be NULL); synchronising */
+int tam_mlp_loss_grad(tam_mlp mlp, long long n, const float* X, const float* Yt, double* loss_host,
+                      float* grad_host, void* stream);
+/* one Adam step on the batch (X, Yt) with learning rate lr; synchronising */
+int tam_mlp_train_step(tam_mlp mlp, long long n, const float* X, const float* Yt, float lr,
+                       double* loss_host, void* stream);
+
+/* Node features[n_nodes x 8] (FP32): x, y, z, T, grad T (volume-weighted mean
+ * of the cells' centroid gradients of the temperature interpolant), dist.
+ * T and dist (distance to the clamped boundary, [n_nodes]) may be NULL (0).
+ * Synchronising. */
+int tam_node_features(int n_nodes, const double* coords, int n_cells, int nodes_per_cell,
+                      const int* cells, const double* T, const double* dist, float* features,
+                      void* stream);
+
+/* x[3n] = the network's guess for K x = rhs (K of the hierarchy `amg`; 8
+ * features in, 3 displacements out), Dirichlet rows set to their prescribed
+ * values.  The guess is kept only if its preconditioned residual energy
+ * <r, M r> (r = rhs - K x, M one V-cycle of `amg`) is below <rhs, M rhs>, the
+ * zero guess's; otherwise x = 0.  used_host (may be NULL) tells which;
+ * energy_ratio_host (may be NULL) receives <r, M r> / <rhs, M rhs>.
+ * Synchronising. */
+int tam_learned_guess(tam_mlp mlp, tam_amg amg, const float* features, const double* rhs, int bf16,
+                      double* x, int* used_host, double* energy_ratio_host, void* stream);
+
+/* ------------------------------------------------------------------------
  * One-call host-buffer path: copies the mesh and fields from host memory
  * (pinned memory gives the fastest copies), assembles, builds the AMG, solves
  * to rtol and copies the displacement back into u_host[n_nodes*3].  Same

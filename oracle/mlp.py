@@ -65,6 +65,42 @@ def loss_and_grad(theta, shapes, X, Y, shift, scale, out_scale):
     return loss, g
 
 
+def node_features(coords, cells, T=None, dist=None):
+    """Features [n, 8]: x, y, z, T, grad T, dist.
+
+    grad T at a node is the volume-weighted mean over its cells of grad T_h at
+    the cell centroid, where T_h is the interpolant in the cell's Lagrange
+    space (P1 or P2); evaluated generically from the barycentric basis
+    polynomials of oracle.fem.
+    """
+    from fractions import Fraction
+
+    from . import fem
+    n = coords.shape[0]
+    F = np.zeros((n, 8))
+    F[:, :3] = coords
+    if T is None:
+        return F
+    F[:, 3] = T
+    degree = 1 if cells.shape[1] == 4 else 2
+    phi = fem.basis_polys(degree)
+    lam = (Fraction(1, 4),) * 4
+    # d phi_c / d lambda_k at the centroid
+    dphi = np.array([[float(sum(c * e[k] * np.prod([lam[q] ** (e[q] - (q == k)) for q in range(4)])
+                                for e, c in p.items() if e[k] > 0)) for k in range(4)] for p in phi])
+    G, vol = fem.barycentric_gradients(coords[cells[:, :4]])
+    grad = np.einsum("ec,ck,ekd->ed", T[cells], dphi, G)       # [cells, 3]
+    gsum = np.zeros((n, 3))
+    wsum = np.zeros(n)
+    for a in range(cells.shape[1]):
+        np.add.at(gsum, cells[:, a], vol[:, None] * grad)
+        np.add.at(wsum, cells[:, a], vol)
+    F[:, 4:7] = gsum / np.where(wsum > 0, wsum, 1.0)[:, None]
+    if dist is not None:
+        F[:, 7] = dist
+    return F
+
+
 def adam_step(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba 2015, Algorithm 1); t counts from 1."""
     m = beta1 * m + (1 - beta1) * g

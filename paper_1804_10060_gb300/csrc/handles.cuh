@@ -2,6 +2,7 @@
 // the C ABI wraps.
 #pragma once
 
+#include <memory>
 #include <vector>
 
 #include "sparse.cuh"
@@ -55,6 +56,32 @@ struct Level {
   SpOpLow<__nv_bfloat16> A16;
 };
 
+// Multi-right-hand-side solve state (block of independent CGs sharing every
+// SpMV as a multi-vector product).  Vectors are interleaved [rows][bs][mp]
+// with the RHS index fastest; mp = RHS count padded to a multiple of 8.
+struct MultiLevel {
+  DBuf<float> b, xa, xb, d, t, y;
+  int tmA = 8, tmP = 8, tmR = 8;  // RHS per thread, picked by the autotuner
+};
+
+struct MultiState {
+  int mp = 0;
+  DBuf<double> b, x, r, z, p, q;  // FP64 CG vectors [3n][mp]
+  DBuf<double> sc;                // per-RHS scalars [8][mp]
+  DBuf<int> flags;                // [0] stop, [1] iteration, [2] max_iter, [3] status
+  DBuf<double> partials;
+  DBuf<unsigned int> tickets;     // one per RHS chunk
+  std::vector<MultiLevel> lv;
+  int tmK = 8;
+  cudaGraphExec_t exec = nullptr;
+  double* graph_x = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  double tune_ms = 0.0;
+  ~MultiState() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 }  // namespace tam
 
 struct tam_amg_s {
@@ -76,6 +103,7 @@ struct tam_amg_s {
   cudaStream_t graph_stream = nullptr;
   long long graph_kernels = 0;           // kernel nodes in iter_exec
   double setup_ms[8] = {};               // setup phase times, see amg_setup_stats
+  std::unique_ptr<tam::MultiState> multi;  // multi-RHS workspace (built on first use)
   ~tam_amg_s();
 };
 

@@ -1,0 +1,486 @@
+// Learned CG initial guess: a node-wise multilayer perceptron, trained and
+// evaluated with the kernels in this file.
+//
+// The paper has no learned component.  The network maps per-node features
+// (coordinates, temperature, temperature gradient, distance to the clamped
+// boundary) to a displacement guess that seeds AMG-PCG; the solver always
+// iterates to the tolerance from it, and a guess whose residual exceeds the
+// load (||b - K x0|| > ||b||) is replaced by zero, so the network can cost
+// iterations but never accuracy.
+//
+// Layers: tanh hidden layers, linear output.  Inputs are standardised,
+// (x - shift) * scale, inside the first layer; outputs are multiplied by
+// out_scale.  Training minimises the mean squared error with Adam.  All
+// parameters are FP32 (master copy); inference can read a BF16 copy of the
+// weights.  Each dense layer is one tiled kernel: a 64-row tile of the
+// activations and the whole layer weight matrix sit in shared memory, and each
+// thread produces 8 consecutive outputs of one row.
+#include <cmath>
+#include <vector>
+
+#include "handles.cuh"
+
+struct tam_mlp_s {
+  int n_in = 0, width = 0, depth = 0, n_out = 0;
+  std::vector<std::pair<int, int>> shapes;  // (fan-in, fan-out) per layer
+  std::vector<long long> offset;            // start of W_l in theta (bias follows)
+  long long n_par = 0;
+  tam::DBuf<float> theta, grad, m1, m2, shift, scale, out_scale;
+  tam::DBuf<__nv_bfloat16> theta16;
+  bool theta16_valid = false;
+  int adam_t = 0;
+  tam::DBuf<float> act;  // activations of the current batch, layer after layer
+  size_t act_cap = 0;
+  tam::DBuf<float> dbuf[2];
+  size_t dcap = 0;
+  tam::DBuf<double> red;  // loss reduction
+  tam::DBuf<unsigned int> ticket;
+};
+
+namespace tam {
+namespace {
+
+constexpr int ROWS = 64;   // rows of the activation tile per block
+constexpr int THREADS = 256;
+
+template <typename TW>
+__device__ __forceinline__ float ld(const TW* p) { return (float)p[0]; }
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(p[0]); }
+
+// out[n x N] = epi(A[n x K] W + bias) with W [K x N] row-major (or W^T when
+// TRANS: W stored [N x K]).  MODE: 0 linear, 1 tanh, 2 output (* out_scale),
+// 3 backward through tanh: out = (A W^T) * (1 - H^2) with H = `aux`.
+// STD: standardise A on load with (a - shift) * scale.
+template <typename TW, int MODE, bool TRANS, bool STD>
+__global__ void __launch_bounds__(THREADS)
+dense_kernel(const float* __restrict__ A, int n, int K, int N, const TW* __restrict__ W,
+             const float* __restrict__ bias, const float* __restrict__ shift, const float* __restrict__ scale,
+             const float* __restrict__ out_scale, const float* __restrict__ aux, float* __restrict__ out) {
+  extern __shared__ float sm[];
+  float* Ws = sm;                     // [K][N]
+  float* As = sm + (size_t)K * N;     // [ROWS][K]
+  for (int e = threadIdx.x; e < K * N; e += THREADS) {
+    const int k = e / N, j = e % N;
+    Ws[e] = TRANS ? ld(W + (size_t)j * K + k) : ld(W + e);
+  }
+  const int groups = (N + 7) / 8;
+  for (long long r0 = (long long)blockIdx.x * ROWS; r0 < n; r0 += (long long)gridDim.x * ROWS) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < ROWS * K; e += THREADS) {
+      const int r = e / K, k = e % K;
+      const long long row = r0 + r;
+      float a = row < n ? A[row * K + k] : 0.f;
+      if (STD) a = (a - shift[k]) * scale[k];
+      As[e] = a;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < ROWS * groups; it += THREADS) {
+      const int r = it / groups, c0 = (it % groups) * 8;
+      const long long row = r0 + r;
+      if (row >= n) continue;
+      float acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+      const float* ar = As + r * K;
+      for (int k = 0; k < K; ++k) {
+        const float a = ar[k];
+        const float* wr = Ws + k * N + c0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (c0 + q < N) acc[q] = fmaf(a, wr[q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + q;
+        if (c >= N) break;
+        float z = acc[q] + (bias ? bias[c] : 0.f);
+        if (MODE == 1) z = tanhf(z);
+        else if (MODE == 2) z *= out_scale[c];
+        else if (MODE == 3) {
+          const float h = aux[row * N + c];
+          z *= (1.f - h * h);
+        }
+        out[row * N + c] = z;
+      }
+    }
+  }
+}
+
+// grad_W[K x N] += H^T D and grad_b[N] += colsum(D) over all n rows; every
+// block accumulates its share of rows in registers, then adds once.
+__global__ void __launch_bounds__(THREADS)
+weight_grad_kernel(const float* __restrict__ H, const float* __restrict__ D, int n, int K, int N,
+                   const float* __restrict__ shift, const float* __restrict__ scale, float* __restrict__ gW,
+                   float* __restrict__ gb) {
+  extern __shared__ float sm[];
+  float* Hs = sm;                   // [ROWS][K]
+  float* Ds = sm + ROWS * K;        // [ROWS][N]
+  const int KN = K * N;
+  const int per = (KN + N + THREADS - 1) / THREADS;  // entries of (W, b) owned by this thread
+  float acc[80];
+#pragma unroll
+  for (int q = 0; q < 80; ++q) acc[q] = 0.f;
+  for (long long r0 = (long long)blockIdx.x * ROWS; r0 < n; r0 += (long long)gridDim.x * ROWS) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < ROWS * K; e += THREADS) {
+      const int r = e / K, k = e % K;
+      const long long row = r0 + r;
+      float h = row < n ? H[row * K + k] : 0.f;
+      if (shift && row < n) h = (h - shift[k]) * scale[k];
+      Hs[e] = h;
+    }
+    for (int e = threadIdx.x; e < ROWS * N; e += THREADS) {
+      const long long row = r0 + e / N;
+      Ds[e] = row < n ? D[row * N + e % N] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 80; ++q) {
+      if (q >= per) break;
+      const int e = threadIdx.x + q * THREADS;
+      if (e < KN) {
+        const int k = e / N, j = e % N;
+        float s = acc[q];
+        for (int r = 0; r < ROWS; ++r) s = fmaf(Hs[r * K + k], Ds[r * N + j], s);
+        acc[q] = s;
+      } else if (e < KN + N) {
+        const int j = e - KN;
+        float s = acc[q];
+        for (int r = 0; r < ROWS; ++r) s += Ds[r * N + j];
+        acc[q] = s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 80; ++q) {
+    if (q >= per) break;
+    const int e = threadIdx.x + q * THREADS;
+    if (e < KN) atomicAdd(&gW[e], acc[q]);
+    else if (e < KN + N) atomicAdd(&gb[e - KN], acc[q]);
+  }
+}
+
+// d = 2 (pred - Y) / (n m) * out_scale;  loss = mean (pred - Y)^2
+__global__ void loss_grad_kernel(const float* __restrict__ pred, const float* __restrict__ Y, long long n, int m,
+                                 const float* __restrict__ out_scale, float* __restrict__ d, GridReduce gr,
+                                 double* __restrict__ loss) {
+  __shared__ double sh[32];
+  double acc[1] = {0.0};
+  const double inv = 1.0 / ((double)n * m);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n * m; i += (long long)gridDim.x * blockDim.x) {
+    const float diff = pred[i] - Y[i];
+    acc[0] += (double)diff * diff;
+    d[i] = (float)(2.0 * diff * inv) * out_scale[i % m];
+  }
+  double tot[1];
+  if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) *loss = tot[0] * inv;
+}
+
+// Adam (Kingma & Ba 2015): bias-corrected first/second moments
+__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void init_params_kernel(float* __restrict__ theta, long long off, int a, int b, unsigned long long seed) {
+  const long long nw = (long long)a * b;
+  const float lim = sqrtf(6.f / (float)(a + b));  // Glorot uniform
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nw + b; i += (long long)gridDim.x * blockDim.x) {
+    if (i < nw) {
+      const uint64_t z = splitmix64(seed ^ (uint64_t)(off + i) * 0x9E3779B97F4A7C15ull);
+      const float u = (float)((z >> 40) * (1.0 / 16777216.0));
+      theta[off + i] = (2.f * u - 1.f) * lim;
+    } else {
+      theta[off + i] = 0.f;
+    }
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16(in[i]);
+}
+
+unsigned ew_grid(long long n) { return std::min<unsigned>(grid_for(n, 256), 152u * 8u); }
+unsigned row_grid(long long n) { return std::min<unsigned>((unsigned)((n + ROWS - 1) / ROWS), 152u * 2u); }
+
+size_t dense_smem(int K, int N) { return sizeof(float) * ((size_t)K * N + (size_t)ROWS * K); }
+
+template <typename TW, int MODE, bool TRANS, bool STD>
+void dense(const float* A, long long n, int K, int N, const TW* W, const float* bias, const tam_mlp_s* M,
+           const float* aux, float* out, cudaStream_t s) {
+  const size_t smem = dense_smem(K, N);
+  TAM_CUDA(cudaFuncSetAttribute(dense_kernel<TW, MODE, TRANS, STD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  dense_kernel<TW, MODE, TRANS, STD><<<row_grid(n), THREADS, smem, s>>>(
+      A, (int)n, K, N, W, bias, M->shift.p, M->scale.p, M->out_scale.p, aux, out);
+  TAM_LAUNCH_CHECK();
+}
+
+void ensure_workspace(tam_mlp_s* M, long long n, cudaStream_t s) {
+  size_t need = 0;
+  for (auto& sh : M->shapes) need += (size_t)n * sh.second;
+  if (need > M->act_cap) {
+    M->act = DBuf<float>(need, s);
+    M->act_cap = need;
+  }
+  size_t dneed = (size_t)n * std::max(M->width, M->n_out);
+  if (dneed > M->dcap) {
+    M->dbuf[0] = DBuf<float>(dneed, s);
+    M->dbuf[1] = DBuf<float>(dneed, s);
+    M->dcap = dneed;
+  }
+}
+
+// forward into the workspace; returns the output pointer ([n x n_out])
+template <typename TW>
+float* forward(tam_mlp_s* M, const float* X, long long n, const TW* theta, cudaStream_t s) {
+  ensure_workspace(M, n, s);
+  const float* in = X;
+  float* o = M->act.p;
+  const int L = (int)M->shapes.size();
+  for (int l = 0; l < L; ++l) {
+    const int a = M->shapes[l].first, b = M->shapes[l].second;
+    const TW* W = theta + M->offset[l];
+    const float* bias_dummy = nullptr;
+    (void)bias_dummy;
+    // bias is FP32 in both precisions: read from the master copy
+    const float* bias = M->theta.p + M->offset[l] + (long long)a * b;
+    const bool last = l == L - 1;
+    if (l == 0) {
+      if (last) dense<TW, 2, false, true>(in, n, a, b, W, bias, M, nullptr, o, s);
+      else dense<TW, 1, false, true>(in, n, a, b, W, bias, M, nullptr, o, s);
+    } else {
+      if (last) dense<TW, 2, false, false>(in, n, a, b, W, bias, M, nullptr, o, s);
+      else dense<TW, 1, false, false>(in, n, a, b, W, bias, M, nullptr, o, s);
+    }
+    in = o;
+    o += (size_t)n * b;
+  }
+  return const_cast<float*>(in);
+}
+
+double loss_and_grad(tam_mlp_s* M, const float* X, const float* Y, long long n, cudaStream_t s) {
+  float* pred = forward<float>(M, X, n, M->theta.p, s);
+  M->grad.zero();
+  const int L = (int)M->shapes.size();
+  GridReduce gr{reinterpret_cast<double*>(M->red.p), M->ticket.p};
+  DBuf<double> loss(1, s);
+  float* d = M->dbuf[0].p;
+  float* d2 = M->dbuf[1].p;
+  loss_grad_kernel<<<ew_grid(n * M->n_out), 256, 0, s>>>(pred, Y, n, M->n_out, M->out_scale.p, d, gr, loss.p);
+  TAM_LAUNCH_CHECK();
+  // activations of layer l are at act + sum_{l'<l} n * b_l'
+  std::vector<float*> acts(L);
+  {
+    float* o = M->act.p;
+    for (int l = 0; l < L; ++l) {
+      acts[l] = o;
+      o += (size_t)n * M->shapes[l].second;
+    }
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const int a = M->shapes[l].first, b = M->shapes[l].second;
+    const float* Hin = l == 0 ? X : acts[l - 1];
+    const size_t smem = sizeof(float) * ((size_t)ROWS * a + (size_t)ROWS * b);
+    TAM_CUDA(cudaFuncSetAttribute(weight_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TAM_CHECK((a * b + b + THREADS - 1) / THREADS <= 80, TAM_ERR_UNSUPPORTED, "mlp: layer too wide");
+    weight_grad_kernel<<<row_grid(n), THREADS, smem, s>>>(Hin, d, (int)n, a, b, l == 0 ? M->shift.p : nullptr,
+                                                          l == 0 ? M->scale.p : nullptr, M->grad.p + M->offset[l],
+                                                          M->grad.p + M->offset[l] + (long long)a * b);
+    TAM_LAUNCH_CHECK();
+    if (l > 0) {
+      // d_prev = (d W^T) * (1 - H_{l-1}^2)
+      dense<float, 3, true, false>(d, n, b, a, M->theta.p + M->offset[l], nullptr, M, acts[l - 1], d2, s);
+      std::swap(d, d2);
+    }
+  }
+  return read_back_double(loss.p, s);
+}
+
+float* forward_any(tam_mlp_s* M, const float* X, long long n, int bf16, cudaStream_t s) {
+  if (!bf16) return forward<float>(M, X, n, M->theta.p, s);
+  if (!M->theta16_valid) {
+    to_bf16_kernel<<<ew_grid(M->n_par), 256, 0, s>>>(M->theta.p, M->theta16.p, M->n_par);
+    TAM_LAUNCH_CHECK();
+    M->theta16_valid = true;
+  }
+  return forward<__nv_bfloat16>(M, X, n, M->theta16.p, s);
+}
+
+}  // namespace
+
+void mlp_forward_device(tam_mlp_s* M, long long n, const float* X, float* Y, int bf16, cudaStream_t s) {
+  float* out = forward_any(M, X, n, bf16, s);
+  TAM_CUDA(cudaMemcpyAsync(Y, out, 4 * (size_t)n * M->n_out, cudaMemcpyDeviceToDevice, s));
+}
+int mlp_n_in(tam_mlp_s* M) { return M->n_in; }
+int mlp_n_out(tam_mlp_s* M) { return M->n_out; }
+
+}  // namespace tam
+
+using namespace tam;
+
+namespace {
+template <class F>
+int guarded_mlp(F&& f) {
+  try {
+    set_last_error("");
+    return f();
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return TAM_ERR_INTERNAL;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int tam_mlp_create(int n_in, int width, int depth, int n_out, unsigned long long seed, tam_mlp* out) {
+  return guarded_mlp([&] {
+    TAM_CHECK(out && n_in >= 1 && n_in <= 128 && width >= 1 && width <= 128 && depth >= 1 && depth <= 16 &&
+                  n_out >= 1 && n_out <= 128,
+              TAM_ERR_INVALID_ARG, "tam_mlp_create: sizes out of range (1..128, depth 1..16)");
+    auto M = new tam_mlp_s();
+    cudaStream_t s = nullptr;
+    M->n_in = n_in;
+    M->width = width;
+    M->depth = depth;
+    M->n_out = n_out;
+    std::vector<int> dims{n_in};
+    for (int i = 0; i < depth; ++i) dims.push_back(width);
+    dims.push_back(n_out);
+    long long off = 0;
+    for (size_t l = 0; l + 1 < dims.size(); ++l) {
+      M->shapes.emplace_back(dims[l], dims[l + 1]);
+      M->offset.push_back(off);
+      off += (long long)dims[l] * dims[l + 1] + dims[l + 1];
+    }
+    M->n_par = off;
+    M->theta = DBuf<float>(off, s);
+    M->grad = DBuf<float>(off, s);
+    M->m1 = DBuf<float>(off, s);
+    M->m2 = DBuf<float>(off, s);
+    M->theta16 = DBuf<__nv_bfloat16>(off, s);
+    M->m1.zero();
+    M->m2.zero();
+    for (size_t l = 0; l < M->shapes.size(); ++l)
+      init_params_kernel<<<64, 256, 0, s>>>(M->theta.p, M->offset[l], M->shapes[l].first, M->shapes[l].second,
+                                            seed);
+    TAM_LAUNCH_CHECK();
+    M->shift = DBuf<float>(n_in, s);
+    M->scale = DBuf<float>(n_in, s);
+    M->out_scale = DBuf<float>(n_out, s);
+    std::vector<float> zero(n_in, 0.f), one(std::max(n_in, n_out), 1.f);
+    TAM_CUDA(cudaMemcpy(M->shift.p, zero.data(), 4 * n_in, cudaMemcpyHostToDevice));
+    TAM_CUDA(cudaMemcpy(M->scale.p, one.data(), 4 * n_in, cudaMemcpyHostToDevice));
+    TAM_CUDA(cudaMemcpy(M->out_scale.p, one.data(), 4 * n_out, cudaMemcpyHostToDevice));
+    M->red = DBuf<double>(152 * 8 * 2, s);
+    M->ticket = DBuf<unsigned int>(1, s);
+    M->ticket.zero();
+    TAM_CUDA(cudaStreamSynchronize(s));
+    *out = M;
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_destroy(tam_mlp M) {
+  return guarded_mlp([&] {
+    delete M;
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_info(tam_mlp M, long long* n_params, int* n_layers) {
+  return guarded_mlp([&] {
+    TAM_CHECK(M, TAM_ERR_INVALID_ARG, "tam_mlp_info: NULL handle");
+    if (n_params) *n_params = M->n_par;
+    if (n_layers) *n_layers = (int)M->shapes.size();
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_set_normalization(tam_mlp M, const float* shift_host, const float* scale_host,
+                              const float* out_scale_host) {
+  return guarded_mlp([&] {
+    TAM_CHECK(M && shift_host && scale_host && out_scale_host, TAM_ERR_INVALID_ARG, "tam_mlp_set_normalization: NULL");
+    TAM_CUDA(cudaMemcpy(M->shift.p, shift_host, 4 * M->n_in, cudaMemcpyHostToDevice));
+    TAM_CUDA(cudaMemcpy(M->scale.p, scale_host, 4 * M->n_in, cudaMemcpyHostToDevice));
+    TAM_CUDA(cudaMemcpy(M->out_scale.p, out_scale_host, 4 * M->n_out, cudaMemcpyHostToDevice));
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_get_params(tam_mlp M, float* theta_host) {
+  return guarded_mlp([&] {
+    TAM_CHECK(M && theta_host, TAM_ERR_INVALID_ARG, "tam_mlp_get_params: NULL");
+    TAM_CUDA(cudaMemcpy(theta_host, M->theta.p, 4 * (size_t)M->n_par, cudaMemcpyDeviceToHost));
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_set_params(tam_mlp M, const float* theta_host) {
+  return guarded_mlp([&] {
+    TAM_CHECK(M && theta_host, TAM_ERR_INVALID_ARG, "tam_mlp_set_params: NULL");
+    TAM_CUDA(cudaMemcpy(M->theta.p, theta_host, 4 * (size_t)M->n_par, cudaMemcpyHostToDevice));
+    M->theta16_valid = false;
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_forward(tam_mlp M, long long n, const float* X, float* Y, int bf16, void* stream) {
+  return guarded_mlp([&] {
+    TAM_CHECK(M && X && Y && n >= 0, TAM_ERR_INVALID_ARG, "tam_mlp_forward: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n == 0) return TAM_OK;
+    mlp_forward_device(M, n, X, Y, bf16, s);
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_loss_grad(tam_mlp M, long long n, const float* X, const float* Yt, double* loss_host, float* grad_host,
+                      void* stream) {
+  return guarded_mlp([&] {
+    TAM_CHECK(M && X && Yt && n > 0, TAM_ERR_INVALID_ARG, "tam_mlp_loss_grad: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double L = loss_and_grad(M, X, Yt, n, s);
+    if (loss_host) *loss_host = L;
+    if (grad_host) {
+      TAM_CUDA(cudaMemcpyAsync(grad_host, M->grad.p, 4 * (size_t)M->n_par, cudaMemcpyDeviceToHost, s));
+      TAM_CUDA(cudaStreamSynchronize(s));
+    }
+    return TAM_OK;
+  });
+}
+
+int tam_mlp_train_step(tam_mlp M, long long n, const float* X, const float* Yt, float lr, double* loss_host,
+                       void* stream) {
+  return guarded_mlp([&] {
+    TAM_CHECK(M && X && Yt && n > 0 && lr > 0.f, TAM_ERR_INVALID_ARG, "tam_mlp_train_step: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double L = loss_and_grad(M, X, Yt, n, s);
+    M->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)M->adam_t), c2 = 1.f - powf(b2, (float)M->adam_t);
+    adam_kernel<<<ew_grid(M->n_par), 256, 0, s>>>(M->theta.p, M->grad.p, M->m1.p, M->m2.p, M->n_par, lr, b1, b2,
+                                                  1e-8f, c1, c2);
+    TAM_LAUNCH_CHECK();
+    M->theta16_valid = false;
+    if (loss_host) *loss_host = L;
+    return TAM_OK;
+  });
+}
+
+}  // extern "C"

@@ -347,6 +347,17 @@ def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
               "omega": omega})
 
 
+def clamp_distance(pb: Problem) -> np.ndarray:
+    """Distance of every node to the clamped boundary of a named workload.
+
+    Geometry known to the generator: the disc is clamped at the bore r = 0.2,
+    the boxes at x = 0.  Used as an input feature of the learned guess.
+    """
+    if pb.name.startswith("disc"):
+        return np.hypot(pb.coords[:, 0], pb.coords[:, 1]) - 0.2
+    return pb.coords[:, 0] - pb.coords[:, 0].min()
+
+
 def mesh_quality(coords: np.ndarray, cells: np.ndarray):
     """Minimum volume and minimum dihedral angle (degrees) over the vertex tets."""
     x = coords[cells[:, :4]]

@@ -71,6 +71,17 @@ _SIGNATURES = {
     "amg_vcycle": ([_vp, _vp, _vp, _vp], _i),
     "amg_pcg_solve": ([_vp, _vp, _vp, _d, _d, _i, _pi, _pd, _vp], _i),
     "amg_destroy": ([_vp], _i),
+    "tam_mlp_create": ([_i, _i, _i, _i, ctypes.c_ulonglong, ctypes.POINTER(_vp)], _i),
+    "tam_mlp_destroy": ([_vp], _i),
+    "tam_mlp_info": ([_vp, _pll, _pi], _i),
+    "tam_mlp_set_normalization": ([_vp, _vp, _vp, _vp], _i),
+    "tam_mlp_get_params": ([_vp, _vp], _i),
+    "tam_mlp_set_params": ([_vp, _vp], _i),
+    "tam_mlp_forward": ([_vp, _ll, _vp, _vp, _i, _vp], _i),
+    "tam_mlp_loss_grad": ([_vp, _ll, _vp, _vp, _pd, _vp, _vp], _i),
+    "tam_mlp_train_step": ([_vp, _ll, _vp, _vp, ctypes.c_float, _pd, _vp], _i),
+    "tam_node_features": ([_i, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "tam_learned_guess": ([_vp, _vp, _vp, _vp, _i, _vp, _pi, _pd, _vp], _i),
     "tam_solve_elasticity_host": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp,
                                    ctypes.POINTER(AmgParams), _d, _i, _vp, _pi, _pd, _vp], _i),
 }
@@ -330,6 +341,83 @@ def tam_solve_elasticity_host(coords, cells, cell_material, mat_props, T, T_ref,
                                        _stream(stream))
     _check(st)
     return u_out, it.value, rel.value
+
+
+class Mlp:
+    """Handle of a node-wise MLP (learned initial guess)."""
+
+    def __init__(self, n_in=8, width=128, depth=3, n_out=3, seed=1):
+        h = _vp()
+        _check(lib.tam_mlp_create(n_in, width, depth, n_out, seed, ctypes.byref(h)))
+        self.handle = h
+        self.n_in, self.width, self.depth, self.n_out = n_in, width, depth, n_out
+        npar, nl = ctypes.c_longlong(), ctypes.c_int()
+        _check(lib.tam_mlp_info(h, ctypes.byref(npar), ctypes.byref(nl)))
+        self.n_params = npar.value
+
+    def set_normalization(self, shift, scale, out_scale):
+        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (shift, scale, out_scale)]
+        _check(lib.tam_mlp_set_normalization(self.handle, *[_vp(x.ctypes.data) for x in a]))
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        _check(lib.tam_mlp_get_params(self.handle, _vp(out.ctypes.data)))
+        return out
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib.tam_mlp_set_params(self.handle, _vp(t.ctypes.data)))
+
+    def forward(self, X, bf16=False, stream=None):
+        Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        _check(lib.tam_mlp_forward(self.handle, X.shape[0], _dev(X, torch.float32, "X"),
+                                   _vp(Y.data_ptr()), int(bf16), _stream(stream)))
+        return Y
+
+    def loss_grad(self, X, Y, stream=None):
+        loss = ctypes.c_double()
+        g = np.empty(self.n_params, np.float32)
+        _check(lib.tam_mlp_loss_grad(self.handle, X.shape[0], _dev(X, torch.float32, "X"),
+                                     _dev(Y, torch.float32, "Y"), ctypes.byref(loss), _vp(g.ctypes.data),
+                                     _stream(stream)))
+        return loss.value, g
+
+    def train_step(self, X, Y, lr, stream=None):
+        loss = ctypes.c_double()
+        _check(lib.tam_mlp_train_step(self.handle, X.shape[0], _dev(X, torch.float32, "X"),
+                                      _dev(Y, torch.float32, "Y"), ctypes.c_float(lr), ctypes.byref(loss),
+                                      _stream(stream)))
+        return loss.value
+
+    def destroy(self):
+        if self.handle:
+            lib.tam_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def tam_node_features(coords, cells, T=None, dist=None, stream=None):
+    F = torch.empty((coords.shape[0], 8), dtype=torch.float32, device=coords.device)
+    _check(lib.tam_node_features(coords.shape[0], _dev(coords, torch.float64, "coords"), cells.shape[0],
+                                 cells.shape[1], _dev(cells, torch.int32, "cells"), _dev(T, torch.float64, "T", True),
+                                 _dev(dist, torch.float64, "dist", True), _vp(F.data_ptr()), _stream(stream)))
+    return F
+
+
+def tam_learned_guess(net: Mlp, amg: Amg, features, rhs, x=None, bf16=True, stream=None):
+    """Returns (x, used, <r, M r> / <rhs, M rhs>)."""
+    if x is None:
+        x = torch.empty_like(rhs)
+    used, rel = ctypes.c_int(), ctypes.c_double()
+    _check(lib.tam_learned_guess(net.handle, amg.handle, _dev(features, torch.float32, "features"),
+                                 _dev(rhs, torch.float64, "rhs"), int(bf16), _dev(x, torch.float64, "x"),
+                                 ctypes.byref(used), ctypes.byref(rel), _stream(stream)))
+    return x, bool(used.value), rel.value
 
 
 def problem_to_device(pb, device="cuda"):

@@ -48,6 +48,34 @@ def test_forward_of_a_hand_evaluated_network():
     assert abs(y[0, 0] - expect) < 1e-15
 
 
+def test_node_features_recover_a_linear_temperature_gradient():
+    # for T linear in x the interpolant is exact (P1 and P2): grad T is the constant vector
+    from paper_1804_10060_gb300 import meshgen
+    for degree in (1, 2):
+        coords, cells = meshgen.box_kuhn(3, 2, 2, 1.5, 1.0, 1.0)
+        coords = meshgen.jitter_interior(coords, 0.3, 0.2, 4)
+        if degree == 2:
+            coords, cells, _ = meshgen.p1_to_p2(coords, cells)
+        a = np.array([0.3, -1.2, 2.5])
+        T = 7.0 + coords @ a
+        F = mlp.node_features(coords, cells, T, dist=coords[:, 0])
+        np.testing.assert_allclose(F[:, 4:7], np.tile(a, (coords.shape[0], 1)), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(F[:, 3], T)
+        np.testing.assert_allclose(F[:, 7], coords[:, 0])
+
+
+def test_node_features_p2_quadratic_centroid_gradient():
+    # T = x^2 on one P2 cell: grad T_h at the centroid is (2 x_c, 0, 0) exactly
+    from paper_1804_10060_gb300 import meshgen
+    X = np.array([[0.0, 0, 0], [1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0]]) * 0.8 + 0.3
+    coords, cells, _ = meshgen.p1_to_p2(X, np.array([[0, 1, 2, 3]]))
+    T = coords[:, 0] ** 2
+    F = mlp.node_features(coords, cells, T)
+    xc = X[:, 0].mean()
+    np.testing.assert_allclose(F[:, 4], 2 * xc, rtol=1e-12)
+    np.testing.assert_allclose(F[:, 5:7], 0.0, atol=1e-12)
+
+
 def test_first_adam_step_closed_form():
     rng = np.random.default_rng(1)
     theta = rng.standard_normal(20)
