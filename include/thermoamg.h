@@ -93,6 +93,17 @@ int fem_assemble_elasticity(int n_nodes, const double* coords, int n_cells, int 
                             const double* u_dirichlet, tam_matrix* K_out, double* rhs_out,
                             void* stream);
 
+/* Load vector of another load case on the mesh of an existing K (same
+ * coords/cells/materials/Dirichlet mask as K was assembled with): thermal and
+ * body loads of Eq. wf_elastic plus the lifting of u_dirichlet, Dirichlet
+ * entries = u_D; K is not modified.  Argument meaning as in
+ * fem_assemble_elasticity; rhs_out[n_nodes*3] is written.  Synchronising.
+ * Errors: INVALID_ARG, DEGENERATE_CELL, CUDA. */
+int fem_assemble_load(tam_matrix K, const double* coords, int n_cells, int nodes_per_cell,
+                      const int* cells, const int* cell_material, int n_mat, const double* mat_props,
+                      const double* T, double T_ref, const double* body_force,
+                      const double* u_dirichlet, double* rhs_out, void* stream);
+
 /* Sizes of K: block rows (= n_nodes), stored 3x3 blocks, block size (3). */
 int tam_matrix_info(tam_matrix K, int* n_block_rows, long long* nnzb, int* block_size);
 
@@ -211,6 +222,32 @@ int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double a
 
 /* Releases the hierarchy. */
 int amg_destroy(tam_amg amg);
+
+/* ------------------------------------------------------------------------
+ * Many load cases at once (an extension of the paper's per-load-case solve;
+ * the paper reuses the elastic preconditioner across time steps, Sec. 6).
+ * Each system i (hierarchy amg[i]) has n_rhs[i] (1..16) right-hand sides,
+ * B[i] and X[i] device arrays [n_rhs[i] x 3n_i] (one displacement vector per
+ * row; X holds the initial guesses in, the solutions out).  Every right-hand
+ * side runs its own CG with its own stopping test ||r|| <= max(rtol ||b||,
+ * atol); all SpMVs are multi-vector products: FP64 with K, FP32 in the
+ * V-cycle (BF16 finest values for a hierarchy built with level_precision 2;
+ * FP64 coarsest solve).  One CUDA graph advances every system by one
+ * iteration (systems on parallel branches) and is replayed until all have
+ * stopped.  The first call for a hierarchy and RHS count builds the FP32
+ * copies and workspaces and times the candidate RHS tiles of every operator
+ * (1, 2, 4 or 8 right-hand sides per thread), keeping the fastest.
+ * iters_host / rel_host (may be NULL): per right-hand side, systems in order.
+ * Synchronising.  Errors: INVALID_ARG, NOT_CONVERGED, BREAKDOWN,
+ * INDEFINITE_PRECOND, NAN, CUDA. */
+int amg_pcg_solve_batch(int n_systems, const tam_amg* amg, const int* n_rhs, const double* const* B,
+                        double* const* X, double rtol, double atol, int max_iter, int* iters_host,
+                        double* rel_host, void* stream);
+
+/* RHS tiles chosen by the autotuner for `amg`: tiles[0] = K, then (A, P, R)
+ * per smoothed level; returns the count in *n (host ints, cap entries) and the
+ * tuning time in *tune_ms_host. */
+int amg_batch_tiles(tam_amg amg, int* tiles_host, int cap, int* n, double* tune_ms_host);
 
 /* ------------------------------------------------------------------------
  * Learned initial guess (an extension; the paper has no learned component).

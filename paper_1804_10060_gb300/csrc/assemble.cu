@@ -115,7 +115,14 @@ struct AsmArgs {
   double* rhs;
   int n_cells;
   int* bad_cell;
+  int loads_only;  // 1: only the load vector (K of this mesh exists already)
 };
+
+// Does the element block (row na, column nb) contribute anything?  In
+// loads-only mode only Dirichlet columns with prescribed values do (lifting).
+__device__ __forceinline__ bool block_needed(const AsmArgs& A, int nb) {
+  return !A.loads_only || (A.dmask[nb] && A.ud);
+}
 
 // Scatter one 3x3 block (row node na, col node nb) or lift it into the load.
 __device__ __forceinline__ void scatter_block(const AsmArgs& A, int na, int nb, const double k[9]) {
@@ -127,6 +134,7 @@ __device__ __forceinline__ void scatter_block(const AsmArgs& A, int na, int nb, 
     }
     return;
   }
+  if (A.loads_only) return;
   int slot = bsearch_i32(A.col_idx, A.row_ptr[na], A.row_ptr[na + 1], nb);
   double* dst = A.vals + (size_t)slot * 9;
 #pragma unroll
@@ -159,6 +167,7 @@ __global__ void __launch_bounds__(128) assemble_p1_kernel(AsmArgs A) {
     const int na = v[a];
     if (A.dmask[na]) continue;
     for (int b = 0; b < 4; ++b) {
+      if (!block_needed(A, v[b])) continue;
       double gg = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
       double k[9];
       for (int i = 0; i < 3; ++i)
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(P2_WARPS * 32) assemble_p2_kernel(AsmArgs A) {
   for (int p = lane; p < 100; p += 32) {
     const int a = p / 10, b = p % 10;
     const int na = sv[wid][a];
-    if (A.dmask[na]) continue;
+    if (A.dmask[na] || !block_needed(A, sv[wid][b])) continue;
     double k[9];
     for (int e = 0; e < 9; ++e) k[e] = 0.0;
     for (int q = 0; q < 4; ++q) {
@@ -310,11 +319,13 @@ __global__ void dirichlet_rows_kernel(int n, const unsigned char* __restrict__ d
                                       double* __restrict__ vals, double* __restrict__ rhs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const bool orphan = inc_ptr[i + 1] == inc_ptr[i];
+  const bool orphan = inc_ptr && inc_ptr[i + 1] == inc_ptr[i];
   if (!dmask[i] && !orphan) return;
-  int slot = bsearch_i32(col_idx, row_ptr[i], row_ptr[i + 1], i);
-  double* d = vals + (size_t)slot * 9;
-  for (int e = 0; e < 9; ++e) d[e] = (e % 4 == 0) ? 1.0 : 0.0;
+  if (vals) {  // loads-only assembly leaves the existing K alone
+    int slot = bsearch_i32(col_idx, row_ptr[i], row_ptr[i + 1], i);
+    double* d = vals + (size_t)slot * 9;
+    for (int e = 0; e < 9; ++e) d[e] = (e % 4 == 0) ? 1.0 : 0.0;
+  }
   for (int r = 0; r < 3; ++r) rhs[3 * (size_t)i + r] = (dmask[i] && ud) ? ud[3 * (size_t)i + r] : 0.0;
 }
 
@@ -378,7 +389,7 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
     A.vals.zero();
     TAM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * (size_t)n_nodes, s));
     AsmArgs args{coords, cells, mat, props, T, T_ref, body, dmask, ud, A.row_ptr.p, A.col_idx.p,
-                 A.vals.p, rhs, n_cells, flag.p};
+                 A.vals.p, rhs, n_cells, flag.p, 0};
     if (n_cells > 0) {
       if (npc == 4)
         assemble_p1_kernel<<<grid_for(n_cells, 128), 128, 0, s>>>(args);
@@ -400,6 +411,42 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
     throw;
   }
   return M;
+}
+
+// Load vector of another load case on the mesh of an existing K: thermal and
+// body loads (and the lifting of prescribed displacements), Dirichlet rows
+// set to u_D; K itself is not touched.
+void assemble_loads(tam_matrix_s* K, const double* coords, int n_cells, int npc, const int* cells, const int* mat,
+                    int n_mat, const double* props, const double* T, double T_ref, const double* body,
+                    const double* ud, double* rhs, cudaStream_t s) {
+  TAM_CHECK(K && coords && props && rhs && n_mat > 0 && n_cells >= 0 && (npc == 4 || npc == 10) &&
+                (cells || n_cells == 0) && (mat || n_cells == 0),
+            TAM_ERR_INVALID_ARG, "fem_assemble_load: bad argument");
+  const int n_nodes = K->n_nodes;
+  DBuf<int> flag(2, s);
+  flag.zero();
+  const long long n_entries = (long long)n_cells * npc;
+  if (n_cells > 0) {
+    validate_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, npc, n_nodes, mat, n_cells, n_mat,
+                                                              flag.p);
+    TAM_LAUNCH_CHECK();
+    TAM_CHECK(read_back_int(flag.p, s) == 0, TAM_ERR_INVALID_ARG, "fem_assemble_load: cell or material id out of range");
+  }
+  TAM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * (size_t)n_nodes, s));
+  AsmArgs args{coords, cells, mat, props, T, T_ref, body, K->dmask.p, ud, K->A.row_ptr.p, K->A.col_idx.p,
+               nullptr, rhs, n_cells, flag.p + 1, 1};
+  if (n_cells > 0) {
+    if (npc == 4)
+      assemble_p1_kernel<<<grid_for(n_cells, 128), 128, 0, s>>>(args);
+    else
+      assemble_p2_kernel<<<grid_for(n_cells, P2_WARPS), P2_WARPS * 32, 0, s>>>(args);
+    TAM_LAUNCH_CHECK();
+  }
+  dirichlet_rows_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, K->dmask.p, nullptr, ud, nullptr, nullptr,
+                                                               nullptr, rhs);
+  TAM_LAUNCH_CHECK();
+  TAM_CHECK(read_back_int(flag.p + 1, s) == 0, TAM_ERR_DEGENERATE_CELL,
+            "fem_assemble_load: a cell has non-positive or non-finite volume");
 }
 
 }  // namespace tam

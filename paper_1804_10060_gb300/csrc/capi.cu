@@ -71,6 +71,17 @@ int fem_assemble_elasticity(int n_nodes, const double* coords, int n_cells, int 
   });
 }
 
+int fem_assemble_load(tam_matrix K, const double* coords, int n_cells, int nodes_per_cell, const int* cells,
+                      const int* cell_material, int n_mat, const double* mat_props, const double* T, double T_ref,
+                      const double* body_force, const double* u_dirichlet, double* rhs_out, void* stream) {
+  return guarded([&] {
+    assemble_loads(K, coords, n_cells, nodes_per_cell, cells, cell_material, n_mat, mat_props, T, T_ref, body_force,
+                   u_dirichlet, rhs_out, as_stream(stream));
+    TAM_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    return TAM_OK;
+  });
+}
+
 int tam_matrix_info(tam_matrix K, int* n_block_rows, long long* nnzb, int* block_size) {
   return guarded([&] {
     TAM_CHECK(K, TAM_ERR_INVALID_ARG, "tam_matrix_info: NULL handle");
@@ -231,6 +242,28 @@ int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double a
       set_last_error(msg);
     }
     return st;
+  });
+}
+
+int amg_pcg_solve_batch(int n_systems, const tam_amg* amg, const int* n_rhs, const double* const* B, double* const* X,
+                        double rtol, double atol, int max_iter, int* iters_host, double* rel_host, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(amg && n_rhs && B && X, TAM_ERR_INVALID_ARG, "amg_pcg_solve_batch: NULL argument");
+    int st = pcg_solve_batch(n_systems, amg, n_rhs, B, X, rtol, atol, max_iter, iters_host, rel_host,
+                             as_stream(stream));
+    if (st != TAM_OK) set_last_error("amg_pcg_solve_batch: a right-hand side did not converge (status per code)");
+    return st;
+  });
+}
+
+int amg_batch_tiles(tam_amg amg, int* tiles_host, int cap, int* n, double* tune_ms_host) {
+  return guarded([&] {
+    TAM_CHECK(amg, TAM_ERR_INVALID_ARG, "amg_batch_tiles: NULL handle");
+    int count = amg->multi ? 1 + 3 * (int)(amg->levels.size() - 1) : 0;
+    if (tiles_host) multi_tiles(amg, tiles_host, cap);
+    if (n) *n = std::min(count, cap);
+    if (tune_ms_host) *tune_ms_host = multi_tune_ms(amg);
+    return TAM_OK;
   });
 }
 

@@ -114,6 +114,10 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
                                   double T_ref, const double* body, const unsigned char* dmask,
                                   const double* ud, double* rhs, cudaStream_t s);
 
+void assemble_loads(tam_matrix_s* K, const double* coords, int n_cells, int npc, const int* cells, const int* mat,
+                    int n_mat, const double* props, const double* T, double T_ref, const double* body,
+                    const double* ud, double* rhs, cudaStream_t s);
+
 tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& prm, cudaStream_t s);
 
 // One V-cycle z = M^-1 r on level 0 (r, z device vectors of the fine size).
@@ -122,6 +126,11 @@ void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cud
 // level 0 and FP64 dense coarsest solve), and its set-up after amg_build.
 void vcycle_apply_low(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s);
 void build_low_precision(tam_amg_s* H, cudaStream_t s);
+
+int pcg_solve_batch(int n_sys, tam_amg_s* const* H, const int* m, const double* const* B, double* const* X,
+                    double rtol, double atol, int max_iter, int* iters, double* rel, cudaStream_t s);
+double multi_tune_ms(tam_amg_s* H);
+void multi_tiles(tam_amg_s* H, int* out, int cap);
 
 int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
               double* rel, cudaStream_t s);

@@ -363,7 +363,7 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
     }
     cudaStream_t cs;
     TAM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
     TAM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     captured_and_reset();
     g_capturing = true;
@@ -371,7 +371,10 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
       enqueue_iteration(H, x, cs);
     } catch (...) {
       g_capturing = false;
+      captured_and_reset();
       cudaStreamEndCapture(cs, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
       cudaStreamDestroy(cs);
       throw;
     }

@@ -347,6 +347,49 @@ def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
               "omega": omega})
 
 
+def load_case(pb: Problem, seed: int) -> tuple[np.ndarray, np.ndarray, float]:
+    """One more load case on pb's mesh: (T[n], body force [n,3], omega).
+
+    omega ~ U[0, 2] from numpy default_rng(seed); body force rho omega^2 (x, y, 0)
+    with rho = 1 (rotation about z).  Temperature: for the boxes the 8-mode
+    Fourier field of amplitude 1 with this seed (T_ref = 0); for the discs
+    the mesh's radial profile plus 100 times that field on coordinates scaled
+    by the disc's extent.
+    """
+    rng = np.random.default_rng(seed)
+    omega = float(rng.uniform(0.0, 2.0))
+    body = omega * omega * np.stack([pb.coords[:, 0], pb.coords[:, 1], np.zeros(pb.n_nodes)], axis=1)
+    if pb.name.startswith("disc"):
+        ext = np.ptp(pb.coords, axis=0)
+        T = pb.T + 100.0 * fourier_temperature(pb.coords, seed, scale=np.where(ext > 0, ext, 1.0))
+    else:
+        T = fourier_temperature(pb.coords, seed)
+    return T, body, omega
+
+
+# 64 load cases on 8 meshes of uneven size (56k to 2M DOF), P1 and P2, boxes and discs
+BATCH_MESHES = (
+    ("slab_box", dict(nx=64, ny=16, nz=16, degree=1)),                                 # 56,355 DOF
+    ("slab_box", dict(nx=32, ny=8, nz=8, degree=2)),                                   # 56,355
+    ("disc", dict(n_r=12, n_theta_per_blade=8, n_z=2, n_blades=48, n_r_blade=4, degree=1)),  # 51,840
+    ("disc", dict(n_r=16, n_theta_per_blade=8, n_z=2, n_blades=48, n_r_blade=6, degree=2)),  # 440,640
+    ("slab_box", dict(nx=128, ny=32, nz=32, degree=1)),                                # 421,443
+    ("slab_box", dict(nx=96, ny=24, nz=24, degree=2)),                                 # 1,390,179
+    ("disc", dict(n_r=24, n_theta_per_blade=8, n_z=4, n_blades=48, n_r_blade=8, degree=2)),  # 1,161,216
+    ("slab_box", dict(nx=216, ny=54, nz=54, degree=1)),                                # 1,969,275
+)
+
+
+def batch_problems(meshes=BATCH_MESHES, cases_per_mesh: int = 8, seed0: int = 100):
+    """[(problem, [(T, body, omega) per case])]: case k of mesh i uses seed seed0 + i*cases_per_mesh + k."""
+    out = []
+    for i, (kind, kw) in enumerate(meshes):
+        pb = slab_box_problem(**kw) if kind == "slab_box" else bladed_disc_problem(**kw)
+        cases = [load_case(pb, seed0 + i * cases_per_mesh + k) for k in range(cases_per_mesh)]
+        out.append((pb, cases))
+    return out
+
+
 def clamp_distance(pb: Problem) -> np.ndarray:
     """Distance of every node to the clamped boundary of a named workload.
 

@@ -71,6 +71,9 @@ _SIGNATURES = {
     "amg_vcycle": ([_vp, _vp, _vp, _vp], _i),
     "amg_pcg_solve": ([_vp, _vp, _vp, _d, _d, _i, _pi, _pd, _vp], _i),
     "amg_destroy": ([_vp], _i),
+    "fem_assemble_load": ([_vp, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp, _vp], _i),
+    "amg_pcg_solve_batch": ([_i, _vp, _vp, _vp, _vp, _d, _d, _i, _vp, _vp, _vp], _i),
+    "amg_batch_tiles": ([_vp, _vp, _i, _pi, _pd], _i),
     "tam_mlp_create": ([_i, _i, _i, _i, ctypes.c_ulonglong, ctypes.POINTER(_vp)], _i),
     "tam_mlp_destroy": ([_vp], _i),
     "tam_mlp_info": ([_vp, _pll, _pi], _i),
@@ -341,6 +344,55 @@ def tam_solve_elasticity_host(coords, cells, cell_material, mat_props, T, T_ref,
                                        _stream(stream))
     _check(st)
     return u_out, it.value, rel.value
+
+
+def fem_assemble_load(K: Matrix, coords, cells, cell_material, mat_props, T=None, T_ref=0.0, body_force=None,
+                      u_dirichlet=None, dirichlet_mask=None, stream=None, out=None):
+    """Load vector [n,3] of another load case on K's mesh (dirichlet_mask is K's; accepted and ignored).
+
+    out: optional contiguous float64 CUDA tensor of n*3 elements to write into.
+    """
+    if out is None:
+        rhs = torch.empty((coords.shape[0], 3), dtype=torch.float64, device=coords.device)
+    else:
+        if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == 3 * coords.shape[0]):
+            raise ValueError("out must be a contiguous float64 CUDA tensor of n*3 elements")
+        rhs = out
+    _check(lib.fem_assemble_load(
+        K.handle, _dev(coords, torch.float64, "coords"), cells.shape[0], cells.shape[1],
+        _dev(cells, torch.int32, "cells"), _dev(cell_material, torch.int32, "cell_material"), mat_props.shape[0],
+        _dev(mat_props, torch.float64, "mat_props"), _dev(T, torch.float64, "T", True), float(T_ref),
+        _dev(body_force, torch.float64, "body_force", True), _dev(u_dirichlet, torch.float64, "u_dirichlet", True),
+        _vp(rhs.data_ptr()), _stream(stream)))
+    return rhs
+
+
+def amg_pcg_solve_batch(amgs, Bs, Xs, rtol=1e-8, atol=0.0, max_iter=1000, stream=None, raise_on_error=True):
+    """Solve several systems, each with a block of right-hand sides.
+
+    amgs: list of Amg; Bs/Xs: lists of [n_rhs, 3n] float64 CUDA tensors (X: guesses in,
+    solutions out).  Returns (iterations per RHS, rel residual per RHS, status).
+    """
+    n = len(amgs)
+    hs = (_vp * n)(*[a.handle for a in amgs])
+    m = (ctypes.c_int * n)(*[int(B.shape[0]) for B in Bs])
+    bp = (_vp * n)(*[_dev(B, torch.float64, "B") for B in Bs])
+    xp = (_vp * n)(*[_dev(X, torch.float64, "X") for X in Xs])
+    tot = sum(m)
+    it = (ctypes.c_int * tot)()
+    rel = (ctypes.c_double * tot)()
+    st = lib.amg_pcg_solve_batch(n, hs, m, bp, xp, float(rtol), float(atol), int(max_iter), it, rel, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return list(it), list(rel), st
+
+
+def amg_batch_tiles(amg: Amg):
+    """(RHS tiles chosen by the autotuner: K then (A, P, R) per level, tuning time ms)."""
+    buf = (ctypes.c_int * 64)()
+    n, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib.amg_batch_tiles(amg.handle, buf, 64, ctypes.byref(n), ctypes.byref(ms)))
+    return list(buf)[:n.value], ms.value
 
 
 class Mlp:
