@@ -430,8 +430,16 @@ def native_arm(args):
 
 
 BATCH_WORKLOAD = ("64 load cases (seeded temperature field + omega ~ U[0,2] centrifugal load) on 8 meshes of "
-                  "uneven size, 51,840-1,969,275 DOF, P1/P2 boxes and bladed discs (5,547,303 DOF in all); "
-                  "FP32 V-cycle with FP64 CG, all systems in one graph-captured multi-RHS solve, rtol 1e-8")
+                  "uneven size, 45,360-1,969,275 DOF, P1/P2 boxes and bladed discs (5,546,007 DOF in all); "
+                  "FP32 V-cycle with FP64 CG, all systems in one graph-captured multi-RHS solve, rtol 1e-8; "
+                  "strength threshold 0.02 (halved per level) on the discs, 0 on the boxes")
+
+
+def mesh_params(tam, pb, **kw):
+    """AMG parameters per workload mesh: the thin bladed discs need a strength threshold."""
+    if pb.name.startswith("disc"):
+        kw = dict(dict(strength_theta=0.02, strength_theta_scale=0.5), **kw)
+    return tam.amg_params_default(**kw)
 
 
 def batched_variant(tam, meshgen, stream, flush, world, reps=2):
@@ -454,9 +462,9 @@ def batched_variant(tam, meshgen, stream, flush, world, reps=2):
             ev[0].record(stream)
             K, _ = tam.fem_assemble_elasticity(**d, stream=stream)
             ev[1].record(stream)
-            H32 = tam.amg_setup(K, d["coords"], tam.amg_params_default(level_precision=1), stream=stream)
+            H32 = tam.amg_setup(K, d["coords"], mesh_params(tam, pb, level_precision=1), stream=stream)
             ev[2].record(stream)
-            H64 = tam.amg_setup(K, d["coords"], tam.amg_params_default(), stream=stream)
+            H64 = tam.amg_setup(K, d["coords"], mesh_params(tam, pb), stream=stream)
             ev[3].record(stream)
         torch.cuda.synchronize()
         t_setup["fp32"] += ev[0].elapsed_time(ev[2])
@@ -547,15 +555,20 @@ def batched_variant(tam, meshgen, stream, flush, world, reps=2):
             "tiles": tiles}
 
 
-LEARNED_TRAIN = dict(n_r=12, n_theta_per_blade=4, n_z=2, n_blades=96, n_r_blade=4, degree=2)    # 368,640 DOF
-LEARNED_EVAL = dict(n_r=64, n_theta_per_blade=12, n_z=6, n_blades=96, n_r_blade=16, degree=2)
+# near-isotropic 96-blade P2 discs, blades half a pitch wide at every resolution
+# (meshgen.isotropic_disc_kwargs(96, t, 2, blade_fraction=0.5))
+LEARNED_TRAIN = dict(n_r=49, n_theta_per_blade=2, n_z=5, n_blades=96, n_r_blade=8, degree=2,
+                     blade_fraction=0.5)                                          # 1,406,592 DOF
+LEARNED_EVAL = dict(n_r=148, n_theta_per_blade=6, n_z=15, n_blades=96, n_r_blade=24, degree=2,
+                    blade_fraction=0.5)                                           # 34,819,200 DOF
 LEARNED_WORKLOAD = ("learned initial guess: node-wise MLP 8->128->128->128->3 (FP32 weights, BF16 inference) on "
                     "(coords, T, grad T, clamp distance), trained by the library's kernels on {n_train} AMG-PCG "
-                    "solves of 368,640-DOF 96-blade P2 discs (seeds 5000+); evaluated on a {n_eval:,}-DOF 96-blade "
-                    "P2 disc (seed 7), FP64 AMG-PCG to rtol 1e-8 from the guarded guess vs from zero")
+                    "solves of 1,406,592-DOF 96-blade P2 discs (seeds 5000+); evaluated on a {n_eval:,}-DOF 96-blade "
+                    "P2 disc (seed 7), FP64 AMG-PCG (strength threshold 0.02, halved per level) to rtol 1e-8 from "
+                    "the guarded guess vs from zero")
 
 
-def learned_variant(tam, meshgen, stream, world, n_train=24, train_steps=1500, eval_kw=None):
+def learned_variant(tam, meshgen, stream, world, n_train=16, train_steps=1500, eval_kw=None):
     """Train the guess network on small discs, then time the large disc's solve from zero and from the guess.
 
     Both solves reuse one resident K and hierarchy; the guess arm's time
@@ -567,7 +580,7 @@ def learned_variant(tam, meshgen, stream, world, n_train=24, train_steps=1500, e
     from paper_1804_10060_gb300 import learned
     t0 = time.perf_counter()
     train = [meshgen.bladed_disc_problem(**LEARNED_TRAIN, seed=5000 + k) for k in range(n_train)]
-    X, Y = learned.training_set(train)
+    X, Y = learned.training_set(train, mesh_params(tam, train[0]))
     net = tam.Mlp(8, 128, 3, 3, seed=7)
     net.set_normalization(*learned.normalization(X, Y))
     torch.cuda.synchronize()
@@ -580,7 +593,7 @@ def learned_variant(tam, meshgen, stream, world, n_train=24, train_steps=1500, e
     dist = torch.from_numpy(meshgen.clamp_distance(pb)).cuda()
     with torch.cuda.stream(stream):
         K, rhs = tam.fem_assemble_elasticity(**d, stream=stream)
-        H = tam.amg_setup(K, d["coords"], tam.amg_params_default(), stream=stream)
+        H = tam.amg_setup(K, d["coords"], mesh_params(tam, pb), stream=stream)
     torch.cuda.synchronize()
     rec = {}
 
@@ -615,12 +628,16 @@ def learned_variant(tam, meshgen, stream, world, n_train=24, train_steps=1500, e
     with torch.cuda.stream(stream):
         F = tam.tam_node_features(d["coords"], d["cells"], d["T"], dist, stream=stream)
         raw = net.forward(F, bf16=True, stream=stream).double()
+        raw32 = net.forward(F, bf16=False, stream=stream).double()
+        _, used32, energy32 = tam.tam_learned_guess(net, H, F, rhs, bf16=False, stream=stream)
     torch.cuda.synchronize()
     nx0 = float(torch.linalg.norm(x0))
     out = {"workload": LEARNED_WORKLOAD.format(n_train=n_train, n_eval=pb.n_dof), "n_dof": pb.n_dof,
            "value": world * pb.n_dof / (ms1 * 1e-3), "unit": "DOF/s", "ms_per_solve": ms1,
            "iterations": it1, "final_rel_resid": rel1, "guess_used": bool(used), "guess_energy_ratio": energy,
            "guess_rel_l2_error": float(torch.linalg.norm(raw.reshape(x0.shape) - x0)) / nx0,
+           "fp32_inference": {"guess_used": bool(used32), "guess_energy_ratio": energy32,
+                              "guess_rel_l2_error": float(torch.linalg.norm(raw32.reshape(x0.shape) - x0)) / nx0},
            "max_rel_l2_vs_zero_start_solution": float(torch.linalg.norm(x1 - x0)) / nx0,
            "from_zero": {"value": world * pb.n_dof / (ms0 * 1e-3), "unit": "DOF/s", "ms_per_solve": ms0,
                          "iterations": it0, "final_rel_resid": rel0},
@@ -698,9 +715,8 @@ def main():
         from paper_1804_10060_gb300 import thermoamg as tam
         stream = torch.cuda.Stream()
         ekw = LEARNED_EVAL
-        if args.dims:   # smaller evaluation disc: n_r x n_theta_per_blade x n_z
-            a, b_, c = (int(v) for v in args.dims.split("x"))
-            ekw = dict(LEARNED_EVAL, n_r=a, n_theta_per_blade=b_, n_z=c)
+        if args.dims:   # smaller near-isotropic evaluation disc: angular cells per blade
+            ekw = meshgen.isotropic_disc_kwargs(96, int(args.dims), 2, blade_fraction=0.5)
         print(json.dumps(learned_variant(tam, meshgen, stream, 1, eval_kw=ekw)), flush=True)
         return
     if args.impl == "reference":

@@ -167,6 +167,7 @@ typedef struct amg_params {
   int use_rotations;       /* 1: six rigid-body modes; 0: three translations only; default 1         */
   int level_precision;     /* V-cycle storage/arithmetic: 0 FP64; 1 FP32; 2 FP32 with BF16 finest-level
                               values.  The outer CG and the coarsest dense solve stay FP64; default 0 */
+  double strength_theta_scale; /* level l uses strength_theta * strength_theta_scale^l; default 1      */
 } amg_params;
 
 /* Fills *p with the defaults above. */

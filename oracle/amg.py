@@ -319,7 +319,7 @@ class Hierarchy:
     params: dict = field(default_factory=dict)
 
 
-DEFAULTS = dict(theta=0.0, degree=2, cheb_lo=0.1, cheb_hi=1.1, eig_steps=10,
+DEFAULTS = dict(theta=0.0, theta_scale=1.0, degree=2, cheb_lo=0.1, cheb_hi=1.1, eig_steps=10,
                 coarse_max_dofs=2000, coarse_min_dofs=500, aggressive_levels=1, small_level_dofs=0,
                 small_level_degree=16, max_levels=10, droptol=1e-10)
 
@@ -350,7 +350,7 @@ def setup(A, B, bs=3, **kw):
         levels.append(L)
         if A.shape[0] <= prm["coarse_max_dofs"] or lev == prm["max_levels"] - 1:
             break
-        nbrs = strength_graph(A, bs, prm["theta"])
+        nbrs = strength_graph(A, bs, prm["theta"] * prm["theta_scale"] ** lev)
         agg, n_agg = aggregate_level(nbrs, lev, B.shape[1], prm["coarse_min_dofs"],
                                      prm["aggressive_levels"])
         if n_agg == 0 or n_agg >= A.shape[0] // bs:

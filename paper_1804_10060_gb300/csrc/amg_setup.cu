@@ -728,7 +728,8 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
   TAM_CHECK(prm.smoother_degree >= 1 && prm.smoother_degree <= 8 && prm.eig_iters >= 1 && prm.eig_iters <= 64 &&
                 prm.max_levels >= 1 && prm.max_levels <= 20 && prm.coarse_max_dofs >= 1 && prm.coarse_min_dofs >= 0 && prm.aggressive_levels >= 0 &&
                 prm.small_level_dofs >= 0 && prm.small_level_degree >= 1 && prm.small_level_degree <= 32 &&
-                prm.cheb_hi > prm.cheb_lo && prm.cheb_lo > 0 && prm.strength_theta >= 0,
+                prm.cheb_hi > prm.cheb_lo && prm.cheb_lo > 0 && prm.strength_theta >= 0 &&
+                prm.strength_theta_scale >= 0,
             TAM_ERR_INVALID_ARG, "amg_setup: parameter out of range");
   auto H = new tam_amg_s();
   PhaseTimer T;
@@ -778,9 +779,10 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
         // distance-1 below; an aggressive aggregation that would leave too
         // small a coarse grid is redone with distance-1 roots
         const bool aggressive = lev < prm.aggressive_levels;
-        L.n_agg = aggregate(L, lev, prm.strength_theta, aggressive ? 2 : 1, s);
+        const double theta = prm.strength_theta * std::pow(prm.strength_theta_scale, (double)lev);
+        L.n_agg = aggregate(L, lev, theta, aggressive ? 2 : 1, s);
         if (aggressive && prm.coarse_min_dofs > 0 && (long long)L.n_agg * k < prm.coarse_min_dofs)
-          L.n_agg = aggregate(L, lev, prm.strength_theta, 1, s);
+          L.n_agg = aggregate(L, lev, theta, 1, s);
       }
       if (last || L.n_agg == 0 || L.n_agg >= L.n_rows) {
         L.n_agg = 0;
@@ -794,7 +796,10 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       tentative(L, B.p, 1e-10, Bc, s);
       // P = (I - omega D^-1 A) P_tent, computed on the pattern of A P_tent
       T.mark(3, s);
-      bsr_spgemm(*L.A, L.Pt, L.P, s);
+      // hierarchies stored in FP32 (level_precision > 0) also form their
+      // products in FP32 arithmetic: the values end up rounded to FP32 anyway
+      const bool fp32 = prm.level_precision > 0;
+      bsr_spgemm(*L.A, L.Pt, L.P, s, fp32);
       smooth_prolongator_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p,
                                                                         L.n_rows, L.bs, k, L.dinv.p, L.consts.p,
                                                                         L.agg.p, L.Pt.row_ptr.p, L.Pt.vals.p);
@@ -804,10 +809,10 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       {
         Bsr AP;
         T.mark(5, s);
-        bsr_spgemm(*L.A, L.P, AP, s);
+        bsr_spgemm(*L.A, L.P, AP, s, fp32);
         H->levels.emplace_back();
         Level& C = H->levels[lev + 1];
-        bsr_spgemm(L.R, AP, C.A_own, s);
+        bsr_spgemm(L.R, AP, C.A_own, s, fp32);
         C.A = &C.A_own;
         C.AS = &C.AS_own;
         C.Aop = SpOp{&C.A_own, &C.AS_own, choose_lpr(C.A_own)};

@@ -139,6 +139,7 @@ int amg_params_default(amg_params* p) {
     p->max_levels = 10;
     p->use_rotations = 1;
     p->level_precision = 0;
+    p->strength_theta_scale = 1.0;
     return TAM_OK;
   });
 }

@@ -4,9 +4,10 @@
 // The paper has no learned component.  The network maps per-node features
 // (coordinates, temperature, temperature gradient, distance to the clamped
 // boundary) to a displacement guess that seeds AMG-PCG; the solver always
-// iterates to the tolerance from it, and a guess whose residual exceeds the
-// load (||b - K x0|| > ||b||) is replaced by zero, so the network can cost
-// iterations but never accuracy.
+// iterates to the tolerance from it, and a guess whose preconditioned
+// residual energy <r, M r> is not below that of the zero guess is replaced by
+// zero (tam_learned_guess), so the network can cost iterations but never
+// accuracy.
 //
 // Layers: tanh hidden layers, linear output.  Inputs are standardised,
 // (x - shift) * scale, inside the first layer; outputs are multiplied by
@@ -226,10 +227,12 @@ void dense(const float* A, long long n, int K, int N, const TW* W, const float* 
   TAM_LAUNCH_CHECK();
 }
 
-void ensure_workspace(tam_mlp_s* M, long long n, cudaStream_t s) {
+// keep_all: every layer's activations (training needs them for the backward
+// pass); otherwise only the two ping-pong buffers are sized.
+void ensure_workspace(tam_mlp_s* M, long long n, bool keep_all, cudaStream_t s) {
   size_t need = 0;
   for (auto& sh : M->shapes) need += (size_t)n * sh.second;
-  if (need > M->act_cap) {
+  if (keep_all && need > M->act_cap) {
     M->act = DBuf<float>(need, s);
     M->act_cap = need;
   }
@@ -241,12 +244,14 @@ void ensure_workspace(tam_mlp_s* M, long long n, cudaStream_t s) {
   }
 }
 
-// forward into the workspace; returns the output pointer ([n x n_out])
+// forward into the workspace; returns the output pointer ([n x n_out]).
+// keep_all: layer l's output stays in the activation buffer for the backward
+// pass; otherwise the layers alternate between the two ping-pong buffers.
 template <typename TW>
-float* forward(tam_mlp_s* M, const float* X, long long n, const TW* theta, cudaStream_t s) {
-  ensure_workspace(M, n, s);
+float* forward(tam_mlp_s* M, const float* X, long long n, const TW* theta, bool keep_all, cudaStream_t s) {
+  ensure_workspace(M, n, keep_all, s);
   const float* in = X;
-  float* o = M->act.p;
+  float* o = keep_all ? M->act.p : M->dbuf[0].p;
   const int L = (int)M->shapes.size();
   for (int l = 0; l < L; ++l) {
     const int a = M->shapes[l].first, b = M->shapes[l].second;
@@ -264,13 +269,13 @@ float* forward(tam_mlp_s* M, const float* X, long long n, const TW* theta, cudaS
       else dense<TW, 1, false, false>(in, n, a, b, W, bias, M, nullptr, o, s);
     }
     in = o;
-    o += (size_t)n * b;
+    o = keep_all ? o + (size_t)n * b : M->dbuf[(l + 1) & 1].p;
   }
   return const_cast<float*>(in);
 }
 
 double loss_and_grad(tam_mlp_s* M, const float* X, const float* Y, long long n, cudaStream_t s) {
-  float* pred = forward<float>(M, X, n, M->theta.p, s);
+  float* pred = forward<float>(M, X, n, M->theta.p, true, s);
   M->grad.zero();
   const int L = (int)M->shapes.size();
   GridReduce gr{reinterpret_cast<double*>(M->red.p), M->ticket.p};
@@ -308,13 +313,13 @@ double loss_and_grad(tam_mlp_s* M, const float* X, const float* Y, long long n, 
 }
 
 float* forward_any(tam_mlp_s* M, const float* X, long long n, int bf16, cudaStream_t s) {
-  if (!bf16) return forward<float>(M, X, n, M->theta.p, s);
+  if (!bf16) return forward<float>(M, X, n, M->theta.p, false, s);
   if (!M->theta16_valid) {
     to_bf16_kernel<<<ew_grid(M->n_par), 256, 0, s>>>(M->theta.p, M->theta16.p, M->n_par);
     TAM_LAUNCH_CHECK();
     M->theta16_valid = true;
   }
-  return forward<__nv_bfloat16>(M, X, n, M->theta16.p, s);
+  return forward<__nv_bfloat16>(M, X, n, M->theta16.p, false, s);
 }
 
 }  // namespace

@@ -238,7 +238,10 @@ __global__ void expand_rows_kernel(const int* __restrict__ rp, int n_rows, int* 
   for (int p = rp[i]; p < rp[i + 1]; ++p) row_of[p] = i;
 }
 
-template <int M, int K, int N>
+// Acc: arithmetic and accumulation type (double; float for hierarchies that
+// are stored in FP32 anyway, where the FP32 pipe is 64x faster).  Inputs and
+// outputs stay FP64 arrays either way.
+template <int M, int K, int N, typename Acc>
 __global__ void __launch_bounds__(128)
 spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
                          const int* __restrict__ yrp, const int* __restrict__ yci, const double* __restrict__ yv,
@@ -247,9 +250,9 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nnzc) return;
   const int i = crow[t], c = cci[t];
-  double acc[M * N];
+  Acc acc[M * N];
 #pragma unroll
-  for (int e = 0; e < M * N; ++e) acc[e] = 0.0;
+  for (int e = 0; e < M * N; ++e) acc[e] = Acc(0);
   const int pe = xrp[i + 1];
   for (int p = xrp[i]; p < pe; ++p) {
     const int j = xci[p];
@@ -262,14 +265,14 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
     if (lo < end && yci[lo] == c) {
       const double* __restrict__ xb = xv + (size_t)p * M * K;
       const double* __restrict__ yb = yv + (size_t)lo * K * N;
-      double xr[M * K];
+      Acc xr[M * K];
 #pragma unroll
-      for (int e = 0; e < M * K; ++e) xr[e] = xb[e];
+      for (int e = 0; e < M * K; ++e) xr[e] = (Acc)xb[e];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        double yr[N];
+        Acc yr[N];
 #pragma unroll
-        for (int s2 = 0; s2 < N; ++s2) yr[s2] = yb[k * N + s2];
+        for (int s2 = 0; s2 < N; ++s2) yr[s2] = (Acc)yb[k * N + s2];
 #pragma unroll
         for (int r = 0; r < M; ++r)
 #pragma unroll
@@ -279,7 +282,7 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   }
   double* out = cv + (size_t)t * M * N;
 #pragma unroll
-  for (int e = 0; e < M * N; ++e) out[e] = acc[e];
+  for (int e = 0; e < M * N; ++e) out[e] = (double)acc[e];
 }
 
 // Row-stationary numeric pass for tall X blocks (M = 6: R (A P) and the coarse
@@ -293,26 +296,27 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
 constexpr int RS_WARPS = 4;
 constexpr int RS_ACC_BYTES = 16384;
 
-template <int M, int K, int N>
+template <int M, int K, int N, typename Acc>
 __global__ void __launch_bounds__(RS_WARPS * 32)
 spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
                          const double* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
                          double* __restrict__ cv) {
   constexpr int MN = M * N;
-  constexpr int W = RS_ACC_BYTES / (MN * 8);
-  extern __shared__ double sm[];
+  constexpr int W = RS_ACC_BYTES / (MN * (int)sizeof(Acc));
+  extern __shared__ double sm_d[];
+  Acc* sm = reinterpret_cast<Acc*>(sm_d);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * RS_WARPS + wid;
   if (row >= n_rows) return;
-  double* acc = sm + (size_t)wid * (RS_ACC_BYTES / 8);
-  int* wcols = reinterpret_cast<int*>(sm + (size_t)RS_WARPS * (RS_ACC_BYTES / 8)) + wid * W;
+  Acc* acc = sm + (size_t)wid * (RS_ACC_BYTES / sizeof(Acc));
+  int* wcols = reinterpret_cast<int*>(sm + (size_t)RS_WARPS * (RS_ACC_BYTES / sizeof(Acc))) + wid * W;
   const int cs = crp[row], ce = crp[row + 1];
   const int xs = xrp[row], xe = xrp[row + 1];
   for (int w0 = cs; w0 < ce; w0 += W) {
     const int wn = min(W, ce - w0);
     for (int i = lane; i < wn; i += 32) wcols[i] = cci[w0 + i];
-    for (int i = lane; i < wn * MN; i += 32) acc[i] = 0.0;
+    for (int i = lane; i < wn * MN; i += 32) acc[i] = Acc(0);
     __syncwarp();
     const int clo = wcols[0], chi = wcols[wn - 1];
     for (int p = xs; p < xe; ++p) {
@@ -342,42 +346,42 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
           const int mid = (lo + hi) >> 1;
           if (wcols[mid] < c) lo = mid + 1; else hi = mid;
         }
-        double xr[K];
+        Acc xr[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) xr[k] = __ldg(xb + r * K + k);
+        for (int k = 0; k < K; ++k) xr[k] = (Acc)__ldg(xb + r * K + k);
         const double* __restrict__ yb = yv + (size_t)q * K * N;
-        double* a = acc + lo * MN + r * N;
+        Acc* a = acc + lo * MN + r * N;
 #pragma unroll
         for (int s2 = 0; s2 < N; ++s2) {
-          double t = a[s2];
+          Acc t = a[s2];
 #pragma unroll
-          for (int k = 0; k < K; ++k) t = fma(xr[k], __ldg(yb + k * N + s2), t);
+          for (int k = 0; k < K; ++k) t = fma(xr[k], (Acc)__ldg(yb + k * N + s2), t);
           a[s2] = t;
         }
       }
       __syncwarp();
     }
-    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = acc[i];
+    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = (double)acc[i];
     __syncwarp();
   }
 }
 
-template <int M, int K, int N>
+template <int M, int K, int N, typename Acc>
 void launch_numeric(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
   if (C.nnzb == 0) return;
   // 3-row blocks (A P_tent, A P on the finest level) keep the output-stationary
   // pass: with only 3 rows per item the row-stationary warp idles (measured
   // 2x slower on the 256x64x64 box).
   if (M == 6) {
-    constexpr int W = RS_ACC_BYTES / (M * N * 8);
+    constexpr int W = RS_ACC_BYTES / (M * N * (int)sizeof(Acc));
     const size_t smem = (size_t)RS_WARPS * (RS_ACC_BYTES + W * 4);
     static bool attr_set = false;
     if (!attr_set) {
-      TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_rs_kernel<M, K, N>,
+      TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_rs_kernel<M, K, N, Acc>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_set = true;
     }
-    spgemm_numeric_rs_kernel<M, K, N><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
+    spgemm_numeric_rs_kernel<M, K, N, Acc><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
         X.row_ptr.p, X.col_idx.p, X.vals.p, X.n_rows, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, C.row_ptr.p,
         C.col_idx.p, C.vals.p);
     TAM_LAUNCH_CHECK();
@@ -386,7 +390,7 @@ void launch_numeric(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
   DBuf<int> crow((size_t)C.nnzb, s);
   expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
   TAM_LAUNCH_CHECK();
-  spgemm_numeric_os_kernel<M, K, N><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
+  spgemm_numeric_os_kernel<M, K, N, Acc><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
       X.row_ptr.p, X.col_idx.p, X.vals.p, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, crow.p, C.col_idx.p, C.nnzb,
       C.vals.p);
   TAM_LAUNCH_CHECK();
@@ -394,7 +398,13 @@ void launch_numeric(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
 
 }  // namespace
 
-void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
+template <int M, int K, int N>
+void launch_numeric_any(const Bsr& X, const Bsr& Y, Bsr& C, bool fp32, cudaStream_t s) {
+  if (fp32) launch_numeric<M, K, N, float>(X, Y, C, s);
+  else launch_numeric<M, K, N, double>(X, Y, C, s);
+}
+
+void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, bool fp32) {
   TAM_CHECK(X.bc == Y.br && X.n_cols == Y.n_rows, TAM_ERR_INTERNAL, "spgemm: shape mismatch");
   C.n_rows = X.n_rows;
   C.n_cols = Y.n_cols;
@@ -419,12 +429,12 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
                                                             overflow.p);
   TAM_LAUNCH_CHECK();
   const int m = X.br, k = X.bc, n = Y.bc;
-  if (m == 3 && k == 3 && n == 6) launch_numeric<3, 3, 6>(X, Y, C, s);
-  else if (m == 6 && k == 3 && n == 6) launch_numeric<6, 3, 6>(X, Y, C, s);
-  else if (m == 6 && k == 6 && n == 6) launch_numeric<6, 6, 6>(X, Y, C, s);
-  else if (m == 3 && k == 3 && n == 3) launch_numeric<3, 3, 3>(X, Y, C, s);
-  else if (m == 6 && k == 6 && n == 3) launch_numeric<6, 6, 3>(X, Y, C, s);
-  else if (m == 3 && k == 6 && n == 6) launch_numeric<3, 6, 6>(X, Y, C, s);
+  if (m == 3 && k == 3 && n == 6) launch_numeric_any<3, 3, 6>(X, Y, C, fp32, s);
+  else if (m == 6 && k == 3 && n == 6) launch_numeric_any<6, 3, 6>(X, Y, C, fp32, s);
+  else if (m == 6 && k == 6 && n == 6) launch_numeric_any<6, 6, 6>(X, Y, C, fp32, s);
+  else if (m == 3 && k == 3 && n == 3) launch_numeric_any<3, 3, 3>(X, Y, C, fp32, s);
+  else if (m == 6 && k == 6 && n == 3) launch_numeric_any<6, 6, 3>(X, Y, C, fp32, s);
+  else if (m == 3 && k == 6 && n == 6) launch_numeric_any<3, 6, 6>(X, Y, C, fp32, s);
   else throw Error(TAM_ERR_UNSUPPORTED, "spgemm: block shape not instantiated");
 }
 

@@ -54,7 +54,8 @@ void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s);
 void bsr_transpose(const Bsr& A, Bsr& R, cudaStream_t s);
 
 // C = X * Y for block sparse X (m x k blocks) and Y (k x n blocks).
-void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s);
+// C = X Y (block shapes 3/6).  fp32: FP32 products and sums (FP64 in and out).
+void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, bool fp32 = false);
 
 // ---------------------------------------------------------------------------
 // Thread-per-row SELL SpMV with a fused epilogue.

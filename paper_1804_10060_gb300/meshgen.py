@@ -241,23 +241,31 @@ def slab_box_problem(nx: int = 256, ny: int = 64, nz: int = 64, seed: int = 2024
 def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
                         n_blades: int = 48, n_r_blade: int = 6, degree: int = 2,
                         seed: int = 7, omega: float = 1.0, rho: float = 1.0,
-                        jitter: float = 0.15) -> Problem:
+                        jitter: float = 0.15, blade_fraction: float = 0.375) -> Problem:
     """Synthetic turbine disc: annulus r in [0.2, 1], thickness 0.1, plus blades.
 
     A structured polar hex grid (n_r radial, n_blades*n_theta_per_blade
-    angular, n_z axial layers) covers the annulus.  Every blade pitch has 3 of
-    its n_theta_per_blade angular cells extruded radially from r=1 to r=1.3
-    with n_r_blade layers (straight-sided rectangular blades of width
-    3/8 of the pitch, about 0.05 at r=1 for 48 blades).  Hexes are split into
+    angular, n_z axial layers) covers the annulus.  In every blade pitch the
+    first round(blade_fraction * n_theta_per_blade) (at least 1) angular
+    cells are extruded radially from r=1 to r=1.3 with n_r_blade layers
+    (straight-sided blades; 3/8 of the pitch, about 0.05 wide at r=1, for
+    48 blades and 8 cells per pitch).  Meshes of one geometry at several
+    resolutions need blade_fraction * n_theta_per_blade to be an integer for
+    each of them.  Hexes are split into
     Kuhn tets, interior nodes jittered by up to jitter*h (seeded), then made
-    P2 if degree == 2.  T = 300 + 500 r^2 + 10 N(0,1) smoothed by one
-    neighbour average (seed), T_ref = 300.  Centrifugal body force
+    P2 if degree == 2.  T = 300 + 500 r^2 + 10 F(x), F the 8-mode Fourier
+    field of fourier_temperature with seed + 1 on the box [-1.3, 1.3]^2 x
+    [-0.05, 0.05] (scale (2.6, 2.6, 0.1)): a seeded perturbation that does
+    not depend on the mesh, so refined meshes discretise the same problem.
+    T_ref = 300.  Centrifugal body force
     rho omega^2 (x, y, 0) about z.  Clamped at the bore r = 0.2.
     Material: E=1, nu=0.3, alpha=1e-5.
     """
     n_t = n_blades * n_theta_per_blade
     r_in, r_out, r_tip, thick = 0.2, 1.0, 1.3, 0.1
-    # geometric radial spacing keeps cells near-isotropic: dr ~ r dtheta
+    # geometric radial spacing: dr / (r dtheta) = ln(r_out / r_in) n_t / (2 pi n_r)
+    # is the same for every ring, and 1 (square cells in plan view) for the
+    # n_r that isotropic_disc_kwargs picks
     r_nodes = np.concatenate([np.geomspace(r_in, r_out, n_r + 1),
                               np.geomspace(r_out, r_tip, n_r_blade + 1)[1:]])
     n_rr = r_nodes.size
@@ -266,7 +274,8 @@ def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
     # node lattice (z, theta, r) -> id; theta periodic
     idx = -np.ones((n_z + 1, n_t, n_rr), np.int64)
     # which hexes exist: annulus all; blade layers only for blade columns
-    in_blade_col = (np.arange(n_t) % n_theta_per_blade) < 3
+    blade_cols = min(n_theta_per_blade, max(1, int(round(blade_fraction * n_theta_per_blade))))
+    in_blade_col = (np.arange(n_t) % n_theta_per_blade) < blade_cols
     hex_exists = np.zeros((n_z, n_t, n_rr - 1), bool)
     hex_exists[:, :, :n_r] = True
     hex_exists[:, in_blade_col, n_r:] = True
@@ -323,19 +332,8 @@ def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
     order = np.lexsort((qr, qz, qt))
     coords, cells, _ = renumber_nodes(coords, cells, order)
     rad = np.hypot(coords[:, 0], coords[:, 1])
-    # temperature: radial profile plus smoothed seeded noise
-    noise = np.random.default_rng(seed + 1).standard_normal(coords.shape[0]) * 10.0
-    sm = np.zeros_like(noise)
-    deg_ = np.zeros_like(noise)
-    cv = cells[:, :4]
-    for a in range(4):
-        for b in range(4):
-            np.add.at(sm, cv[:, a], noise[cv[:, b]])
-            np.add.at(deg_, cv[:, a], 1.0)
-    sm_full = noise.copy()
-    has = deg_ > 0
-    sm_full[has] = sm[has] / deg_[has]
-    T = 300.0 + 500.0 * rad ** 2 + sm_full
+    # temperature: radial profile plus a smooth seeded perturbation
+    T = 300.0 + 500.0 * rad ** 2 + 10.0 * fourier_temperature(coords, seed + 1, scale=(2.6, 2.6, 0.1))
     body = rho * omega ** 2 * np.stack([coords[:, 0], coords[:, 1], np.zeros(coords.shape[0])], axis=1)
     mask = (rad <= r_in + 1e-9).astype(np.uint8)
     return Problem(
@@ -345,6 +343,20 @@ def bladed_disc_problem(n_r: int = 16, n_theta_per_blade: int = 8, n_z: int = 2,
         dirichlet_mask=mask, u_dirichlet=None,
         meta={"n_r": n_r, "n_theta": n_t, "n_z": n_z, "degree": degree, "seed": seed,
               "omega": omega})
+
+
+def isotropic_disc_kwargs(n_blades: int = 48, n_theta_per_blade: int = 8, degree: int = 2, **extra) -> dict:
+    """bladed_disc_problem arguments whose cells are near-isotropic.
+
+    With dtheta = 2 pi / (n_blades n_theta_per_blade): n_r = ln(1 / 0.2) / dtheta
+    rings on the annulus and n_r_blade = ln(1.3) / dtheta on the blades make
+    dr = r dtheta everywhere; n_z = 0.1 / (0.6 dtheta) layers make dz equal
+    to r dtheta at the mid radius r = 0.6 (at least 2 layers).
+    """
+    dth = 2.0 * np.pi / (n_blades * n_theta_per_blade)
+    return dict(n_r=max(1, int(round(np.log(5.0) / dth))), n_theta_per_blade=n_theta_per_blade,
+                n_z=max(2, int(round(0.1 / (0.6 * dth)))), n_blades=n_blades,
+                n_r_blade=max(1, int(round(np.log(1.3) / dth))), degree=degree, **extra)
 
 
 def load_case(pb: Problem, seed: int) -> tuple[np.ndarray, np.ndarray, float]:
@@ -367,16 +379,20 @@ def load_case(pb: Problem, seed: int) -> tuple[np.ndarray, np.ndarray, float]:
     return T, body, omega
 
 
-# 64 load cases on 8 meshes of uneven size (56k to 2M DOF), P1 and P2, boxes and discs
+# 64 load cases on 8 meshes of uneven size (45k to 2M DOF), P1 and P2, boxes and
+# bladed discs (near-isotropic cells, see isotropic_disc_kwargs; blades half a pitch wide)
 BATCH_MESHES = (
-    ("slab_box", dict(nx=64, ny=16, nz=16, degree=1)),                                 # 56,355 DOF
-    ("slab_box", dict(nx=32, ny=8, nz=8, degree=2)),                                   # 56,355
-    ("disc", dict(n_r=12, n_theta_per_blade=8, n_z=2, n_blades=48, n_r_blade=4, degree=1)),  # 51,840
-    ("disc", dict(n_r=16, n_theta_per_blade=8, n_z=2, n_blades=48, n_r_blade=6, degree=2)),  # 440,640
-    ("slab_box", dict(nx=128, ny=32, nz=32, degree=1)),                                # 421,443
-    ("slab_box", dict(nx=96, ny=24, nz=24, degree=2)),                                 # 1,390,179
-    ("disc", dict(n_r=24, n_theta_per_blade=8, n_z=4, n_blades=48, n_r_blade=8, degree=2)),  # 1,161,216
-    ("slab_box", dict(nx=216, ny=54, nz=54, degree=1)),                                # 1,969,275
+    ("slab_box", dict(nx=64, ny=16, nz=16, degree=1)),                  # 56,355 DOF
+    ("slab_box", dict(nx=32, ny=8, nz=8, degree=2)),                    # 56,355
+    ("disc", dict(n_r=29, n_theta_per_blade=4, n_z=3, n_blades=28, n_r_blade=5, degree=1,
+                  blade_fraction=0.5)),                                 # 45,360
+    ("disc", dict(n_r=25, n_theta_per_blade=4, n_z=3, n_blades=24, n_r_blade=4, degree=2,
+                  blade_fraction=0.5)),                                 # 225,792
+    ("slab_box", dict(nx=128, ny=32, nz=32, degree=1)),                 # 421,443
+    ("slab_box", dict(nx=96, ny=24, nz=24, degree=2)),                  # 1,390,179
+    ("disc", dict(n_r=49, n_theta_per_blade=4, n_z=5, n_blades=48, n_r_blade=8, degree=2,
+                  blade_fraction=0.5)),                                 # 1,381,248
+    ("slab_box", dict(nx=216, ny=54, nz=54, degree=1)),                 # 1,969,275
 )
 
 

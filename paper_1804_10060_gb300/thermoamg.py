@@ -45,6 +45,7 @@ class AmgParams(ctypes.Structure):
         ("max_levels", ctypes.c_int),
         ("use_rotations", ctypes.c_int),
         ("level_precision", ctypes.c_int),
+        ("strength_theta_scale", ctypes.c_double),
     ]
 
 

@@ -41,20 +41,80 @@ def test_low_precision_vcycle_keeps_fp64_accuracy(problem, precision):
     assert it <= it64 + 3, (it, it64)
 
 
-@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (2, 5e-2)])
-def test_low_precision_vcycle_matches_fp64_vcycle(precision, tol):
+@pytest.mark.parametrize("precision,tol", [(1, 1e-4), (2, 5e-2)])
+def test_low_precision_vcycle_matches_oracle_vcycle(precision, tol):
+    """The reduced-precision V-cycle vs the oracle's FP64 V-cycle on the same operators.
+
+    A hierarchy built for level_precision >= 1 forms its products in FP32
+    (covered by test_fp32_setup_products_match_oracle), so it is not the FP64
+    hierarchy; its exported operators (FP64 arrays holding those values) feed
+    the oracle's V-cycle, and the FP32 arithmetic of the V-cycle must agree
+    within its own rounding amplified by the V-cycle: FP32 unit roundoff
+    (6e-8) times the coarse operators' conditioning, whose smallest
+    (near-rigid-body) modes the FP32 products perturb -- measured 5.8e-5 on
+    this box, bound 1e-4.  BF16 finest values: 5e-2.
+    """
+    from gpu_util import bsr_to_csr
+    from oracle import amg as oamg
+    tam = need_gpu()
+    pb = meshgen.slab_box_problem(32, 8, 8)
+    d = tam.problem_to_device(pb)
+    K, rhs = tam.fem_assemble_elasticity(**d)
+    H = tam.amg_setup(K, d["coords"], tam.amg_params_default(level_precision=precision, coarse_max_dofs=60))
+    info = tam.amg_info(H)
+    nl = info["n_levels"]
+    assert nl >= 3
+
+    def ex(lev, which):
+        e = tam.amg_level_export(H, lev, which)
+        return bsr_to_csr(e["row_ptr"], e["col_idx"], e["vals"], e["n_cols"])
+
+    levels = []
+    for lev in range(nl):
+        A = ex(lev, 0)
+        L = oamg.Level(A=A, bs=info["block"][lev], dinv=oamg.point_dinv(A), lam=info["lambda"][lev])
+        if lev < nl - 1:
+            L.P, L.R = ex(lev, 1), ex(lev, 2)
+        levels.append(L)
+    Ho = oamg.Hierarchy(levels=levels, coarse_inv=oamg.coarse_inverse(levels[-1].A), params=dict(oamg.DEFAULTS))
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(pb.n_dof)
+    z = tam.amg_vcycle(H, torch.from_numpy(r).cuda()).cpu().numpy()
+    zo = oamg.vcycle(Ho, r)
+    rel = np.linalg.norm(z - zo) / np.linalg.norm(zo)
+    assert rel <= tol, rel
+    # still a positive operator on random vectors
+    assert float(r @ z) > 0
+
+
+def test_fp32_setup_products_match_oracle():
+    """A hierarchy stored in FP32 forms its SpGEMM products in FP32 arithmetic.
+
+    Aggregation (theta = 0: every nonzero block is strong) and the level sizes
+    are those of the FP64 setup; every smoothed prolongator and Galerkin
+    product matches the oracle's FP64 formula applied to the same level
+    inputs within FP32 rounding of sums of a few hundred products.
+    """
+    from gpu_util import bsr_to_csr, sparse_rel
+    from oracle import amg as oamg
     tam = need_gpu()
     pb = meshgen.slab_box_problem(32, 8, 8)
     d = tam.problem_to_device(pb)
     K, rhs = tam.fem_assemble_elasticity(**d)
     prm = dict(coarse_max_dofs=60)
     H64 = tam.amg_setup(K, d["coords"], tam.amg_params_default(**prm))
-    Hlo = tam.amg_setup(K, d["coords"], tam.amg_params_default(level_precision=precision, **prm))
-    assert tam.amg_info(H64)["rows"] == tam.amg_info(Hlo)["rows"]
-    r = torch.randn(pb.n_nodes, 3, dtype=torch.float64, device="cuda")
-    z64 = tam.amg_vcycle(H64, r)
-    zlo = tam.amg_vcycle(Hlo, r)
-    rel = float(torch.linalg.norm(zlo - z64) / torch.linalg.norm(z64))
-    assert rel <= tol, rel
-    # still a positive operator on random vectors
-    assert float((r * zlo).sum()) > 0
+    H32 = tam.amg_setup(K, d["coords"], tam.amg_params_default(level_precision=1, **prm))
+    info = tam.amg_info(H32)
+    assert info["rows"] == tam.amg_info(H64)["rows"]
+
+    def ex(lev, which):
+        e = tam.amg_level_export(H32, lev, which)
+        return bsr_to_csr(e["row_ptr"], e["col_idx"], e["vals"], e["n_cols"])
+
+    for lev in range(info["n_levels"] - 1):
+        assert np.array_equal(tam.amg_level_aggregates(H32, lev).cpu().numpy(),
+                              tam.amg_level_aggregates(H64, lev).cpu().numpy())
+        A, Pt, P = ex(lev, 0), ex(lev, 3), ex(lev, 1)
+        assert sparse_rel(P, oamg.smooth_prolongator(A, Pt, info["lambda"][lev])) <= 1e-5, lev
+        Ac, _ = oamg.galerkin(A, P)
+        assert sparse_rel(ex(lev + 1, 0), Ac) <= 1e-5, lev
