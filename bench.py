@@ -630,12 +630,17 @@ def learned_variant(tam, meshgen, stream, world, n_train=16, train_steps=1500, e
         raw = net.forward(F, bf16=True, stream=stream).double()
         raw32 = net.forward(F, bf16=False, stream=stream).double()
         _, used32, energy32 = tam.tam_learned_guess(net, H, F, rhs, bf16=False, stream=stream)
+        _, used0, energy0 = tam.tam_learned_guess(net, H, F, rhs, bf16=True, smooth_degree=0, stream=stream)
+        xs, _, _ = tam.tam_learned_guess(net, H, F, rhs, bf16=True, stream=stream)
     torch.cuda.synchronize()
     nx0 = float(torch.linalg.norm(x0))
     out = {"workload": LEARNED_WORKLOAD.format(n_train=n_train, n_eval=pb.n_dof), "n_dof": pb.n_dof,
            "value": world * pb.n_dof / (ms1 * 1e-3), "unit": "DOF/s", "ms_per_solve": ms1,
            "iterations": it1, "final_rel_resid": rel1, "guess_used": bool(used), "guess_energy_ratio": energy,
            "guess_rel_l2_error": float(torch.linalg.norm(raw.reshape(x0.shape) - x0)) / nx0,
+           "smoothed_guess_rel_l2_error": float(torch.linalg.norm(xs - x0)) / nx0,
+           "guess_smoothing": "8 Chebyshev-Jacobi steps on K over [0.1, 1.1] lambda_max(D^-1 K)",
+           "unsmoothed": {"guess_used": bool(used0), "guess_energy_ratio": energy0},
            "fp32_inference": {"guess_used": bool(used32), "guess_energy_ratio": energy32,
                               "guess_rel_l2_error": float(torch.linalg.norm(raw32.reshape(x0.shape) - x0)) / nx0},
            "max_rel_l2_vs_zero_start_solution": float(torch.linalg.norm(x1 - x0)) / nx0,

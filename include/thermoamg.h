@@ -168,6 +168,9 @@ typedef struct amg_params {
   int level_precision;     /* V-cycle storage/arithmetic: 0 FP64; 1 FP32; 2 FP32 with BF16 finest-level
                               values.  The outer CG and the coarsest dense solve stay FP64; default 0 */
   double strength_theta_scale; /* level l uses strength_theta * strength_theta_scale^l; default 1      */
+  int setup_fp64;          /* products of the setup (A P_tent, A P, R (A P)) in plain FP64 arithmetic (1)
+                              or in double-float, two FP32 values per operand with error-free transforms,
+                              about 2^-48 relative, several times faster on GB300 (0, default)         */
 } amg_params;
 
 /* Fills *p with the defaults above. */
@@ -294,13 +297,16 @@ int tam_node_features(int n_nodes, const double* coords, int n_cells, int nodes_
 
 /* x[3n] = the network's guess for K x = rhs (K of the hierarchy `amg`; 8
  * features in, 3 displacements out), Dirichlet rows set to their prescribed
- * values.  The guess is kept only if its preconditioned residual energy
+ * values, then smooth_degree (0..64; 0 = none) Chebyshev-Jacobi steps on
+ * K x = rhs over [0.1, 1.1] lambda_max(D^-1 K), which remove the rough part of
+ * the network's error.  The guess is kept only if its preconditioned residual energy
  * <r, M r> (r = rhs - K x, M one V-cycle of `amg`) is below <rhs, M rhs>, the
  * zero guess's; otherwise x = 0.  used_host (may be NULL) tells which;
  * energy_ratio_host (may be NULL) receives <r, M r> / <rhs, M rhs>.
  * Synchronising. */
 int tam_learned_guess(tam_mlp mlp, tam_amg amg, const float* features, const double* rhs, int bf16,
-                      double* x, int* used_host, double* energy_ratio_host, void* stream);
+                      int smooth_degree, double* x, int* used_host, double* energy_ratio_host,
+                      void* stream);
 
 /* ------------------------------------------------------------------------
  * One-call host-buffer path: copies the mesh and fields from host memory

@@ -796,10 +796,8 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       tentative(L, B.p, 1e-10, Bc, s);
       // P = (I - omega D^-1 A) P_tent, computed on the pattern of A P_tent
       T.mark(3, s);
-      // hierarchies stored in FP32 (level_precision > 0) also form their
-      // products in FP32 arithmetic: the values end up rounded to FP32 anyway
-      const bool fp32 = prm.level_precision > 0;
-      bsr_spgemm(*L.A, L.Pt, L.P, s, fp32);
+      const SpgemmArith arith = prm.setup_fp64 ? SpgemmArith::kFp64 : SpgemmArith::kDoubleFloat;
+      bsr_spgemm(*L.A, L.Pt, L.P, s, arith);
       smooth_prolongator_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p,
                                                                         L.n_rows, L.bs, k, L.dinv.p, L.consts.p,
                                                                         L.agg.p, L.Pt.row_ptr.p, L.Pt.vals.p);
@@ -809,10 +807,10 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       {
         Bsr AP;
         T.mark(5, s);
-        bsr_spgemm(*L.A, L.P, AP, s, fp32);
+        bsr_spgemm(*L.A, L.P, AP, s, arith);
         H->levels.emplace_back();
         Level& C = H->levels[lev + 1];
-        bsr_spgemm(L.R, AP, C.A_own, s, fp32);
+        bsr_spgemm(L.R, AP, C.A_own, s, arith);
         C.A = &C.A_own;
         C.AS = &C.AS_own;
         C.Aop = SpOp{&C.A_own, &C.AS_own, choose_lpr(C.A_own)};

@@ -126,6 +126,8 @@ void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cud
 // level 0 and FP64 dense coarsest solve), and its set-up after amg_build.
 void vcycle_apply_low(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s);
 void build_low_precision(tam_amg_s* H, cudaStream_t s);
+// x <- degree Chebyshev-Jacobi steps on K x = b from x over [lo, hi] * lambda_max(D^-1 K)
+void smooth_fine(tam_amg_s* H, const double* b, double* x, int degree, double lo, double hi, cudaStream_t s);
 
 int pcg_solve_batch(int n_sys, tam_amg_s* const* H, const int* m, const double* const* B, double* const* X,
                     double rtol, double atol, int max_iter, int* iters, double* rel, cudaStream_t s);

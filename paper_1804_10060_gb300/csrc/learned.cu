@@ -115,18 +115,23 @@ extern "C" int tam_node_features(int n_nodes, const double* coords, int n_cells,
   }
 }
 
-// The guess is kept only if it lowers the preconditioned residual energy
-// <r, M r> (r = rhs - K x, M = one AMG V-cycle) below that of the zero guess
-// <rhs, M rhs> -- the quantity CG's error is measured in up to the
-// preconditioner, unlike ||r||, which a guess with small but rough errors can
-// inflate while still saving iterations.
+// The network's output is first smoothed by smooth_degree Chebyshev-Jacobi
+// steps on K x = rhs (over [0.1, 1.1] lambda_max(D^-1 K)): a node-wise
+// network leaves a small but rough error, which K amplifies, and a point
+// smoother removes exactly those components.  The guess is then kept only if
+// it lowers the preconditioned residual energy <r, M r> (r = rhs - K x,
+// M = one AMG V-cycle) below that of the zero guess <rhs, M rhs> -- the
+// quantity CG's error is measured in up to the preconditioner.
 extern "C" int tam_learned_guess(tam_mlp_s* M, tam_amg H, const float* features, const double* rhs, int bf16,
-                                 double* x, int* used_host, double* energy_ratio_host, void* stream) {
+                                 int smooth_degree, double* x, int* used_host, double* energy_ratio_host,
+                                 void* stream) {
   try {
     set_last_error("");
     TAM_CHECK(M && H && features && rhs && x, TAM_ERR_INVALID_ARG, "tam_learned_guess: NULL argument");
     TAM_CHECK(mlp_n_in(M) == 8 && mlp_n_out(M) == 3, TAM_ERR_INVALID_ARG,
               "tam_learned_guess: the network must map 8 node features to 3 displacements");
+    TAM_CHECK(smooth_degree >= 0 && smooth_degree <= 64, TAM_ERR_INVALID_ARG,
+              "tam_learned_guess: smooth_degree must be 0..64");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     tam_matrix_s* K = H->K;
     const int n = K->n_nodes;
@@ -135,6 +140,7 @@ extern "C" int tam_learned_guess(tam_mlp_s* M, tam_amg H, const float* features,
     mlp_forward_device(M, n, features, Y.p, bf16, s);
     guess_to_x_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, Y.p, K->dmask.p, rhs, x);
     TAM_LAUNCH_CHECK();
+    if (smooth_degree > 0) smooth_fine(H, rhs, x, smooth_degree, 0.1, 1.1, s);
     DBuf<double> r((size_t)N, s), z((size_t)N, s), part(1216, s), out(2, s);
     DBuf<unsigned int> ticket(1, s);
     ticket.zero();

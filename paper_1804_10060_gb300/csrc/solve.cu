@@ -16,6 +16,7 @@
 // graph of one iteration can be replayed without host round trips.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "handles.cuh"
 
@@ -263,6 +264,23 @@ void prolong_add(const Level& L, const double* xc, double* x, const int* stop, c
   else spop_apply<3, 3>(L.Pop, xc, EpiAdd<3>{x, nr, stop}, s);
 }
 
+// Chebyshev coefficients (c_d, c_r) for `degree` steps on the absolute
+// interval [l0, l1], laid out like Level::consts from index 2 (same
+// three-term recurrence as the level smoothers).
+std::vector<double> cheb_coefficients(double l0, double l1, int degree) {
+  std::vector<double> c(2 + 2 * (size_t)degree, 0.0);
+  const double theta = 0.5 * (l1 + l0), delta = 0.5 * (l1 - l0), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  c[3] = 1.0 / theta;
+  for (int i = 1; i < degree; ++i) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    c[2 + 2 * i] = rn * rho;
+    c[3 + 2 * i] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  return c;
+}
+
 // V-cycle on level l with rhs b; the result lands in *out (level 0: caller's z)
 void vcycle_level(tam_amg_s* H, int l, const double* b, double* out, const int* stop, cudaStream_t s) {
   Level& L = H->levels[l];
@@ -413,6 +431,27 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   int status = host.status;
   if (status == TAM_OK && !host.stop) status = TAM_ERR_NOT_CONVERGED;
   return status;
+}
+
+// x <- `degree` Chebyshev-Jacobi steps on the finest system K x = b starting
+// from x, over [lo, hi] * lambda_max(D^-1 K): removes the rough error
+// components of an initial guess (those the point smoother acts on) at the
+// cost of `degree` SpMVs with K.
+void smooth_fine(tam_amg_s* H, const double* b, double* x, int degree, double lo, double hi, cudaStream_t s) {
+  TAM_CHECK(degree >= 1 && degree <= 64 && hi > lo && lo > 0, TAM_ERR_INVALID_ARG, "smooth_fine: bad degree or interval");
+  Level& L = H->levels[0];
+  const long long N = (long long)L.n_rows * L.bs;
+  const std::vector<double> c = cheb_coefficients(lo * L.lambda_host, hi * L.lambda_host, degree);
+  DBuf<double> coef(c.size(), s);
+  TAM_CUDA(cudaMemcpyAsync(coef.p, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice, s));
+  TAM_CUDA(cudaStreamSynchronize(s));  // c is a host temporary
+  double* cur = x;
+  double* nxt = L.xb.p;
+  for (int k = 0; k < degree; ++k) {
+    spop_apply<3, 3>(L.Aop, cur, EpiCheb<3>{b, cur, L.dinv.p, coef.p + 2 + 2 * k, L.d.p, nxt, L.n_rows, nullptr}, s);
+    std::swap(cur, nxt);
+  }
+  if (cur != x) TAM_CUDA(cudaMemcpyAsync(x, cur, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, s));
 }
 
 }  // namespace tam

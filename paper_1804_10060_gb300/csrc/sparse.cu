@@ -238,21 +238,68 @@ __global__ void expand_rows_kernel(const int* __restrict__ rp, int n_rows, int* 
   for (int p = rp[i]; p < rp[i + 1]; ++p) row_of[p] = i;
 }
 
-// Acc: arithmetic and accumulation type (double; float for hierarchies that
-// are stored in FP32 anyway, where the FP32 pipe is 64x faster).  Inputs and
-// outputs stay FP64 arrays either way.
-template <int M, int K, int N, typename Acc>
+// Arithmetic of the numeric passes.
+//
+// Both policies read operands of type V and accumulate in A; out() gives the
+// FP64 result.  F64 is plain FP64.  DF ("double-float") keeps every operand
+// as an unevaluated sum hi + lo of two FP32 values (split once, before the
+// product) and accumulates in the same form: the product of the high parts is
+// made exact with an FMA, the two cross terms are added to its error, and the
+// sum with the accumulator uses Knuth's TwoSum, so each product-accumulate is
+// accurate to about 2^-48 of the magnitudes involved.  GB300 issues FP32 FMAs
+// at 64 times its FP64 rate, and these kernels run the FP64 pipe at ~98% in
+// the F64 form, so the ~12 FP32 operations per multiply-add are the cheaper
+// way to the same accuracy class.  __fadd_rn/__fmul_rn keep the compiler from
+// contracting the error-free transforms into FMAs.
+struct ArithF64 {
+  using V = double;
+  using A = double;
+  __device__ static A zero() { return 0.0; }
+  __device__ static void fma(A& a, V x, V y) { a = ::fma(x, y, a); }
+  __device__ static double out(A a) { return a; }
+};
+
+struct ArithDF {
+  using V = float2;
+  using A = float2;
+  __device__ static A zero() { return make_float2(0.f, 0.f); }
+  __device__ static void fma(A& a, V x, V y) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = fmaf(x.x, y.x, -p);        // exact: x.x * y.x = p + e
+    e = fmaf(x.x, y.y, e);
+    e = fmaf(x.y, y.x, e);
+    const float s = __fadd_rn(a.x, p);   // TwoSum(a.x, p) = s + err exactly
+    const float bp = __fadd_rn(s, -a.x);
+    const float err = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
+    a.x = s;
+    a.y = __fadd_rn(a.y, __fadd_rn(err, e));
+  }
+  __device__ static double out(A a) { return (double)a.x + (double)a.y; }
+};
+
+// Split FP64 values into (hi, lo) FP32 pairs: hi = fl32(v), lo = fl32(v - hi).
+__global__ void split_df_kernel(const double* __restrict__ in, float2* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    const float hi = __double2float_rn(v);
+    out[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+}
+
+template <int M, int K, int N, class Ar>
 __global__ void __launch_bounds__(128)
-spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
-                         const int* __restrict__ yrp, const int* __restrict__ yci, const double* __restrict__ yv,
+spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
+                         const int* __restrict__ yrp, const int* __restrict__ yci, const typename Ar::V* __restrict__ yv,
                          const int* __restrict__ crow, const int* __restrict__ cci, long long nnzc,
                          double* __restrict__ cv) {
+  using V = typename Ar::V;
+  using A = typename Ar::A;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nnzc) return;
   const int i = crow[t], c = cci[t];
-  Acc acc[M * N];
+  A acc[M * N];
 #pragma unroll
-  for (int e = 0; e < M * N; ++e) acc[e] = Acc(0);
+  for (int e = 0; e < M * N; ++e) acc[e] = Ar::zero();
   const int pe = xrp[i + 1];
   for (int p = xrp[i]; p < pe; ++p) {
     const int j = xci[p];
@@ -263,60 +310,62 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
       if (yci[mid] < c) lo = mid + 1; else hi = mid;
     }
     if (lo < end && yci[lo] == c) {
-      const double* __restrict__ xb = xv + (size_t)p * M * K;
-      const double* __restrict__ yb = yv + (size_t)lo * K * N;
-      Acc xr[M * K];
+      const V* __restrict__ xb = xv + (size_t)p * M * K;
+      const V* __restrict__ yb = yv + (size_t)lo * K * N;
+      V xr[M * K];
 #pragma unroll
-      for (int e = 0; e < M * K; ++e) xr[e] = (Acc)xb[e];
+      for (int e = 0; e < M * K; ++e) xr[e] = xb[e];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        Acc yr[N];
+        V yr[N];
 #pragma unroll
-        for (int s2 = 0; s2 < N; ++s2) yr[s2] = (Acc)yb[k * N + s2];
+        for (int s2 = 0; s2 < N; ++s2) yr[s2] = yb[k * N + s2];
 #pragma unroll
         for (int r = 0; r < M; ++r)
 #pragma unroll
-          for (int s2 = 0; s2 < N; ++s2) acc[r * N + s2] = fma(xr[r * K + k], yr[s2], acc[r * N + s2]);
+          for (int s2 = 0; s2 < N; ++s2) Ar::fma(acc[r * N + s2], xr[r * K + k], yr[s2]);
       }
     }
   }
   double* out = cv + (size_t)t * M * N;
 #pragma unroll
-  for (int e = 0; e < M * N; ++e) out[e] = (double)acc[e];
+  for (int e = 0; e < M * N; ++e) out[e] = Ar::out(acc[e]);
 }
 
 // Row-stationary numeric pass for tall X blocks (M = 6: R (A P) and the coarse
 // levels): one warp per output row, the row's output blocks accumulated in
 // shared memory a window of W columns at a time.  For each X entry (i, j) the
 // lanes take the (Y-row entry q, block row r) items: item (q, r) computes row
-// r of X_ij Y_jq (K*N FMAs) and adds it to output block col(q).  Columns in a
-// Y row are distinct, so the items of one X entry never touch the same
-// accumulator element and no atomics are needed; X entries are processed one
-// after the other.  Most of the warp does useful FP64 work (items = M * |Y row|).
+// r of X_ij Y_jq (K*N multiply-adds) and adds it to output block col(q).
+// Columns in a Y row are distinct, so the items of one X entry never touch the
+// same accumulator element and no atomics are needed; X entries are processed
+// one after the other.  Most of the warp does useful work (items = M * |Y row|).
 constexpr int RS_WARPS = 4;
 constexpr int RS_ACC_BYTES = 16384;
 
-template <int M, int K, int N, typename Acc>
+template <int M, int K, int N, class Ar>
 __global__ void __launch_bounds__(RS_WARPS * 32)
-spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const double* __restrict__ xv,
+spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
-                         const double* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
+                         const typename Ar::V* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
                          double* __restrict__ cv) {
+  using V = typename Ar::V;
+  using A = typename Ar::A;
   constexpr int MN = M * N;
-  constexpr int W = RS_ACC_BYTES / (MN * (int)sizeof(Acc));
+  constexpr int W = RS_ACC_BYTES / (MN * (int)sizeof(A));
   extern __shared__ double sm_d[];
-  Acc* sm = reinterpret_cast<Acc*>(sm_d);
+  A* sm = reinterpret_cast<A*>(sm_d);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * RS_WARPS + wid;
   if (row >= n_rows) return;
-  Acc* acc = sm + (size_t)wid * (RS_ACC_BYTES / sizeof(Acc));
-  int* wcols = reinterpret_cast<int*>(sm + (size_t)RS_WARPS * (RS_ACC_BYTES / sizeof(Acc))) + wid * W;
+  A* acc = sm + (size_t)wid * (RS_ACC_BYTES / sizeof(A));
+  int* wcols = reinterpret_cast<int*>(sm + (size_t)RS_WARPS * (RS_ACC_BYTES / sizeof(A))) + wid * W;
   const int cs = crp[row], ce = crp[row + 1];
   const int xs = xrp[row], xe = xrp[row + 1];
   for (int w0 = cs; w0 < ce; w0 += W) {
     const int wn = min(W, ce - w0);
     for (int i = lane; i < wn; i += 32) wcols[i] = cci[w0 + i];
-    for (int i = lane; i < wn * MN; i += 32) acc[i] = Acc(0);
+    for (int i = lane; i < wn * MN; i += 32) acc[i] = Ar::zero();
     __syncwarp();
     const int clo = wcols[0], chi = wcols[wn - 1];
     for (int p = xs; p < xe; ++p) {
@@ -336,7 +385,7 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
         }
         qe = lo;
       }
-      const double* __restrict__ xb = xv + (size_t)p * M * K;
+      const V* __restrict__ xb = xv + (size_t)p * M * K;
       const int items = (qe - qs) * M;
       for (int it = lane; it < items; it += 32) {
         const int q = qs + it / M, r = it % M;
@@ -346,65 +395,78 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
           const int mid = (lo + hi) >> 1;
           if (wcols[mid] < c) lo = mid + 1; else hi = mid;
         }
-        Acc xr[K];
+        V xr[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) xr[k] = (Acc)__ldg(xb + r * K + k);
-        const double* __restrict__ yb = yv + (size_t)q * K * N;
-        Acc* a = acc + lo * MN + r * N;
+        for (int k = 0; k < K; ++k) xr[k] = xb[r * K + k];
+        const V* __restrict__ yb = yv + (size_t)q * K * N;
+        A* a = acc + lo * MN + r * N;
 #pragma unroll
         for (int s2 = 0; s2 < N; ++s2) {
-          Acc t = a[s2];
+          A t = a[s2];
 #pragma unroll
-          for (int k = 0; k < K; ++k) t = fma(xr[k], (Acc)__ldg(yb + k * N + s2), t);
+          for (int k = 0; k < K; ++k) Ar::fma(t, xr[k], yb[k * N + s2]);
           a[s2] = t;
         }
       }
       __syncwarp();
     }
-    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = (double)acc[i];
+    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = Ar::out(acc[i]);
     __syncwarp();
   }
 }
 
-template <int M, int K, int N, typename Acc>
-void launch_numeric(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s) {
+template <int M, int K, int N, class Ar>
+void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const typename Ar::V* yv, Bsr& C,
+                    cudaStream_t s) {
   if (C.nnzb == 0) return;
   // 3-row blocks (A P_tent, A P on the finest level) keep the output-stationary
   // pass: with only 3 rows per item the row-stationary warp idles (measured
   // 2x slower on the 256x64x64 box).
   if (M == 6) {
-    constexpr int W = RS_ACC_BYTES / (M * N * (int)sizeof(Acc));
+    constexpr int W = RS_ACC_BYTES / (M * N * (int)sizeof(typename Ar::A));
     const size_t smem = (size_t)RS_WARPS * (RS_ACC_BYTES + W * 4);
     static bool attr_set = false;
     if (!attr_set) {
-      TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_rs_kernel<M, K, N, Acc>,
+      TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_rs_kernel<M, K, N, Ar>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_set = true;
     }
-    spgemm_numeric_rs_kernel<M, K, N, Acc><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
-        X.row_ptr.p, X.col_idx.p, X.vals.p, X.n_rows, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, C.row_ptr.p,
-        C.col_idx.p, C.vals.p);
+    spgemm_numeric_rs_kernel<M, K, N, Ar><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
+        X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, C.vals.p);
     TAM_LAUNCH_CHECK();
     return;
   }
   DBuf<int> crow((size_t)C.nnzb, s);
   expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
   TAM_LAUNCH_CHECK();
-  spgemm_numeric_os_kernel<M, K, N, Acc><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
-      X.row_ptr.p, X.col_idx.p, X.vals.p, Y.row_ptr.p, Y.col_idx.p, Y.vals.p, crow.p, C.col_idx.p, C.nnzb,
-      C.vals.p);
+  spgemm_numeric_os_kernel<M, K, N, Ar><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
+      X.row_ptr.p, X.col_idx.p, xv, Y.row_ptr.p, Y.col_idx.p, yv, crow.p, C.col_idx.p, C.nnzb, C.vals.p);
   TAM_LAUNCH_CHECK();
+}
+
+DBuf<float2> split_values(const Bsr& B, cudaStream_t s) {
+  const long long n = B.nnzb * (long long)B.block_elems();
+  DBuf<float2> out((size_t)std::max(1LL, n), s);
+  if (n > 0) {
+    split_df_kernel<<<std::min<unsigned>(grid_for(n, 256), 152u * 16u), 256, 0, s>>>(B.vals.p, out.p, n);
+    TAM_LAUNCH_CHECK();
+  }
+  return out;
 }
 
 }  // namespace
 
 template <int M, int K, int N>
-void launch_numeric_any(const Bsr& X, const Bsr& Y, Bsr& C, bool fp32, cudaStream_t s) {
-  if (fp32) launch_numeric<M, K, N, float>(X, Y, C, s);
-  else launch_numeric<M, K, N, double>(X, Y, C, s);
+void launch_numeric_any(const Bsr& X, const Bsr& Y, Bsr& C, SpgemmArith arith, cudaStream_t s) {
+  if (arith == SpgemmArith::kFp64) {
+    launch_numeric<M, K, N, ArithF64>(X, X.vals.p, Y, Y.vals.p, C, s);
+  } else {
+    DBuf<float2> xs = split_values(X, s), ys = split_values(Y, s);
+    launch_numeric<M, K, N, ArithDF>(X, xs.p, Y, ys.p, C, s);
+  }
 }
 
-void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, bool fp32) {
+void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith arith) {
   TAM_CHECK(X.bc == Y.br && X.n_cols == Y.n_rows, TAM_ERR_INTERNAL, "spgemm: shape mismatch");
   C.n_rows = X.n_rows;
   C.n_cols = Y.n_cols;
@@ -429,12 +491,12 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, bool fp32) {
                                                             overflow.p);
   TAM_LAUNCH_CHECK();
   const int m = X.br, k = X.bc, n = Y.bc;
-  if (m == 3 && k == 3 && n == 6) launch_numeric_any<3, 3, 6>(X, Y, C, fp32, s);
-  else if (m == 6 && k == 3 && n == 6) launch_numeric_any<6, 3, 6>(X, Y, C, fp32, s);
-  else if (m == 6 && k == 6 && n == 6) launch_numeric_any<6, 6, 6>(X, Y, C, fp32, s);
-  else if (m == 3 && k == 3 && n == 3) launch_numeric_any<3, 3, 3>(X, Y, C, fp32, s);
-  else if (m == 6 && k == 6 && n == 3) launch_numeric_any<6, 6, 3>(X, Y, C, fp32, s);
-  else if (m == 3 && k == 6 && n == 6) launch_numeric_any<3, 6, 6>(X, Y, C, fp32, s);
+  if (m == 3 && k == 3 && n == 6) launch_numeric_any<3, 3, 6>(X, Y, C, arith, s);
+  else if (m == 6 && k == 3 && n == 6) launch_numeric_any<6, 3, 6>(X, Y, C, arith, s);
+  else if (m == 6 && k == 6 && n == 6) launch_numeric_any<6, 6, 6>(X, Y, C, arith, s);
+  else if (m == 3 && k == 3 && n == 3) launch_numeric_any<3, 3, 3>(X, Y, C, arith, s);
+  else if (m == 6 && k == 6 && n == 3) launch_numeric_any<6, 6, 3>(X, Y, C, arith, s);
+  else if (m == 3 && k == 6 && n == 6) launch_numeric_any<3, 6, 6>(X, Y, C, arith, s);
   else throw Error(TAM_ERR_UNSUPPORTED, "spgemm: block shape not instantiated");
 }
 

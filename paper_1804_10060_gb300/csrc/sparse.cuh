@@ -54,8 +54,12 @@ void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s);
 void bsr_transpose(const Bsr& A, Bsr& R, cudaStream_t s);
 
 // C = X * Y for block sparse X (m x k blocks) and Y (k x n blocks).
-// C = X Y (block shapes 3/6).  fp32: FP32 products and sums (FP64 in and out).
-void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, bool fp32 = false);
+// Arithmetic of the SpGEMM numeric pass: plain FP64, or double-float (each
+// FP64 operand split into two FP32 values, products and sums in FP32 with
+// error-free transforms, about 2^-48 relative; FP64 in and out).
+enum class SpgemmArith { kFp64, kDoubleFloat };
+// C = X Y (block shapes 3/6).
+void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith arith = SpgemmArith::kDoubleFloat);
 
 // ---------------------------------------------------------------------------
 // Thread-per-row SELL SpMV with a fused epilogue.

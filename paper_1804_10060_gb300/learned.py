@@ -4,7 +4,8 @@ Every numerical step runs in libthermoamg: the training targets are
 displacements the AMG-PCG solver itself computes (to rtol 1e-8), the features
 come from tam_node_features, the network is trained by tam_mlp_train_step
 (hand-written forward/backward/Adam kernels) and evaluated by
-tam_learned_guess, which discards a guess whose residual exceeds the load.
+tam_learned_guess, which smooths the network's output and discards it unless
+its preconditioned residual energy is below the zero guess's.
 This module only chooses data, batches and the learning-rate schedule.
 """
 from __future__ import annotations
@@ -66,7 +67,7 @@ def train(net: tam.Mlp, X, Y, steps=1500, batch=32768, lr=3e-3, seed=0, log_ever
     return hist
 
 
-def evaluate(net: tam.Mlp, pb, params=None, rtol=1e-8, bf16=True):
+def evaluate(net: tam.Mlp, pb, params=None, rtol=1e-8, bf16=True, smooth_degree=8):
     """Iterations from zero vs from the learned guess on one problem (same tolerance)."""
     d = tam.problem_to_device(pb)
     K, rhs = tam.fem_assemble_elasticity(**d)
@@ -78,7 +79,7 @@ def evaluate(net: tam.Mlp, pb, params=None, rtol=1e-8, bf16=True):
     # the raw network output's error, before the guard
     raw = net.forward(F, bf16=bf16).double()
     raw_err = float(torch.linalg.norm(raw - x0) / torch.linalg.norm(x0))
-    xg, used, energy = tam.tam_learned_guess(net, H, F, rhs, bf16=bf16)
+    xg, used, energy = tam.tam_learned_guess(net, H, F, rhs, bf16=bf16, smooth_degree=smooth_degree)
     x1 = xg.clone()
     it1, rel1, _ = tam.amg_pcg_solve(H, rhs, x1, rtol=rtol, max_iter=1000)
     err = float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))

@@ -46,6 +46,7 @@ class AmgParams(ctypes.Structure):
         ("use_rotations", ctypes.c_int),
         ("level_precision", ctypes.c_int),
         ("strength_theta_scale", ctypes.c_double),
+        ("setup_fp64", ctypes.c_int),
     ]
 
 
@@ -85,7 +86,7 @@ _SIGNATURES = {
     "tam_mlp_loss_grad": ([_vp, _ll, _vp, _vp, _pd, _vp, _vp], _i),
     "tam_mlp_train_step": ([_vp, _ll, _vp, _vp, ctypes.c_float, _pd, _vp], _i),
     "tam_node_features": ([_i, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
-    "tam_learned_guess": ([_vp, _vp, _vp, _vp, _i, _vp, _pi, _pd, _vp], _i),
+    "tam_learned_guess": ([_vp, _vp, _vp, _vp, _i, _i, _vp, _pi, _pd, _vp], _i),
     "tam_solve_elasticity_host": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp,
                                    ctypes.POINTER(AmgParams), _d, _i, _vp, _pi, _pd, _vp], _i),
 }
@@ -462,13 +463,14 @@ def tam_node_features(coords, cells, T=None, dist=None, stream=None):
     return F
 
 
-def tam_learned_guess(net: Mlp, amg: Amg, features, rhs, x=None, bf16=True, stream=None):
-    """Returns (x, used, <r, M r> / <rhs, M rhs>)."""
+def tam_learned_guess(net: Mlp, amg: Amg, features, rhs, x=None, bf16=True, smooth_degree=8, stream=None):
+    """Returns (x, used, <r, M r> / <rhs, M rhs>) after smooth_degree smoothing steps."""
     if x is None:
         x = torch.empty_like(rhs)
     used, rel = ctypes.c_int(), ctypes.c_double()
     _check(lib.tam_learned_guess(net.handle, amg.handle, _dev(features, torch.float32, "features"),
-                                 _dev(rhs, torch.float64, "rhs"), int(bf16), _dev(x, torch.float64, "x"),
+                                 _dev(rhs, torch.float64, "rhs"), int(bf16), int(smooth_degree),
+                                 _dev(x, torch.float64, "x"),
                                  ctypes.byref(used), ctypes.byref(rel), _stream(stream)))
     return x, bool(used.value), rel.value
 
