@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-case batched variant")
     ap.add_argument("--batched-only", action="store_true", help="run only the batched variant and print it")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initial-guess variant")
+    ap.add_argument("--setup-fp64", action="store_true",
+                    help="--one-step: setup products in plain FP64 instead of double-float")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-guess variant and print it")
     ap.add_argument("--dims", default=None, help="override box hexes, e.g. 64x16x16 (testing only)")
     ap.add_argument("--one-step", action="store_true",
@@ -685,11 +687,11 @@ def one_step(args):
     pb = meshgen.slab_box_problem(*dims)
     d = tam.problem_to_device(pb)
     K, rhs = tam.fem_assemble_elasticity(**d)
-    H = tam.amg_setup(K, d["coords"])
+    H = tam.amg_setup(K, d["coords"], tam.amg_params_default(setup_fp64=int(args.setup_fp64)))
     x = torch.zeros_like(rhs)
     it, rel, _ = tam.amg_pcg_solve(H, rhs, x, rtol=1e-8, max_iter=1000)
     torch.cuda.synchronize()
-    print(json.dumps({"one_step": True, "dims": dims, "iterations": it, "rel": rel,
+    print(json.dumps({"one_step": True, "dims": dims, "setup_fp64": args.setup_fp64, "iterations": it, "rel": rel,
                       "levels": tam.amg_info(H)["rows"], "launches": tam.kernel_launches()}))
 
 

@@ -170,7 +170,8 @@ typedef struct amg_params {
   double strength_theta_scale; /* level l uses strength_theta * strength_theta_scale^l; default 1      */
   int setup_fp64;          /* products of the setup (A P_tent, A P, R (A P)) in plain FP64 arithmetic (1)
                               or in double-float, two FP32 values per operand with error-free transforms,
-                              about 2^-48 relative, several times faster on GB300 (0, default)         */
+                              about 2^-47 relative, faster on GB300 (0, default); double-float loses
+                              accuracy on operand entries below about 2^-100 in magnitude            */
 } amg_params;
 
 /* Fills *p with the defaults above. */

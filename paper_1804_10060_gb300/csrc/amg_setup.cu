@@ -797,7 +797,13 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       // P = (I - omega D^-1 A) P_tent, computed on the pattern of A P_tent
       T.mark(3, s);
       const SpgemmArith arith = prm.setup_fp64 ? SpgemmArith::kFp64 : SpgemmArith::kDoubleFloat;
-      bsr_spgemm(*L.A, L.Pt, L.P, s, arith);
+      // double-float: A is split once for both of its products, and A P stays
+      // split (its only use is R (A P))
+      DBuf<float2> As;
+      if (arith == SpgemmArith::kDoubleFloat) As = split_values(*L.A, s);
+      SpgemmSplit spA;
+      spA.x = As.p;
+      bsr_spgemm(*L.A, L.Pt, L.P, s, arith, spA);
       smooth_prolongator_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p,
                                                                         L.n_rows, L.bs, k, L.dinv.p, L.consts.p,
                                                                         L.agg.p, L.Pt.row_ptr.p, L.Pt.vals.p);
@@ -806,11 +812,17 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       bsr_transpose(L.P, L.R, s);
       {
         Bsr AP;
+        DBuf<float2> APs;
         T.mark(5, s);
-        bsr_spgemm(*L.A, L.P, AP, s, arith);
+        SpgemmSplit spAP;
+        spAP.x = As.p;
+        if (arith == SpgemmArith::kDoubleFloat) spAP.c = &APs;
+        bsr_spgemm(*L.A, L.P, AP, s, arith, spAP);
         H->levels.emplace_back();
         Level& C = H->levels[lev + 1];
-        bsr_spgemm(L.R, AP, C.A_own, s, arith);
+        SpgemmSplit spR;
+        spR.y = APs.p;
+        bsr_spgemm(L.R, AP, C.A_own, s, arith, spR);
         C.A = &C.A_own;
         C.AS = &C.AS_own;
         C.Aop = SpOp{&C.A_own, &C.AS_own, choose_lpr(C.A_own)};

@@ -251,12 +251,48 @@ __global__ void expand_rows_kernel(const int* __restrict__ rp, int n_rows, int* 
 // the F64 form, so the ~12 FP32 operations per multiply-add are the cheaper
 // way to the same accuracy class.  __fadd_rn/__fmul_rn keep the compiler from
 // contracting the error-free transforms into FMAs.
+// IEEE-754 bit manipulations (integer pipe only: GB300's FP64 pipe, which also
+// executes FP64<->FP32 conversions, is the scarce resource here).
+//
+// split_bits: v = hi + lo exactly up to the last 5 bits of the 29 mantissa
+// bits below hi's 24 (relative error <= 2^-47): hi keeps the sign, the
+// exponent and the top 23 stored mantissa bits of v (truncation); lo is the
+// remaining 29-bit tail, normalised and truncated to 24 bits.  |v| < 2^-126
+// (zero, FP64 values below FP32's normal range) gives (0, 0); a tail below
+// FP32's normal range gives lo = 0.
+__device__ __forceinline__ float2 split_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int ef = (int)((b >> 52) & 0x7ff) - 1023 + 127;  // FP32 biased exponent of hi
+  if (ef <= 0) return make_float2(0.f, 0.f);
+  if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(m >> 29));
+  const unsigned low = (unsigned)(m & 0x1fffffffull);  // weight 2^(E - 52) per unit
+  if (low == 0) return make_float2(hi, 0.f);
+  const int lz = __clz(low);                            // 3..31
+  const int el = ef - 52 + (31 - lz);                   // FP32 biased exponent of lo
+  if (el <= 0) return make_float2(hi, 0.f);
+  const unsigned frac = (unsigned)(((unsigned long long)low << (lz + 1)) & 0xffffffffull) >> 9;
+  return make_float2(hi, __uint_as_float(sign | ((unsigned)el << 23) | frac));
+}
+
+// Exact FP32 -> FP64 (zero and FP32 subnormals give 0; inf/nan keep their class).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xff;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ed = e == 255 ? 0x7ffull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 struct ArithF64 {
   using V = double;
   using A = double;
   __device__ static A zero() { return 0.0; }
   __device__ static void fma(A& a, V x, V y) { a = ::fma(x, y, a); }
-  __device__ static double out(A a) { return a; }
+  __device__ static void store(double* p, A a) { *p = a; }
 };
 
 struct ArithDF {
@@ -274,24 +310,25 @@ struct ArithDF {
     a.x = s;
     a.y = __fadd_rn(a.y, __fadd_rn(err, e));
   }
-  __device__ static double out(A a) { return (double)a.x + (double)a.y; }
+  __device__ static void store(double* p, A a) { *p = f2d_bits(a.x) + f2d_bits(a.y); }
+  // kept split for a following double-float product: renormalised (Fast2Sum)
+  __device__ static void store(float2* p, A a) {
+    const float s = __fadd_rn(a.x, a.y);
+    *p = make_float2(s, __fadd_rn(a.y, -__fadd_rn(s, -a.x)));
+  }
 };
 
-// Split FP64 values into (hi, lo) FP32 pairs: hi = fl32(v), lo = fl32(v - hi).
 __global__ void split_df_kernel(const double* __restrict__ in, float2* __restrict__ out, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double v = in[i];
-    const float hi = __double2float_rn(v);
-    out[i] = make_float2(hi, __double2float_rn(v - (double)hi));
-  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = split_bits(in[i]);
 }
 
-template <int M, int K, int N, class Ar>
+template <int M, int K, int N, class Ar, typename OutT>
 __global__ void __launch_bounds__(128)
 spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          const int* __restrict__ yrp, const int* __restrict__ yci, const typename Ar::V* __restrict__ yv,
                          const int* __restrict__ crow, const int* __restrict__ cci, long long nnzc,
-                         double* __restrict__ cv) {
+                         OutT* __restrict__ cv) {
   using V = typename Ar::V;
   using A = typename Ar::A;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -327,9 +364,9 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
       }
     }
   }
-  double* out = cv + (size_t)t * M * N;
+  OutT* out = cv + (size_t)t * M * N;
 #pragma unroll
-  for (int e = 0; e < M * N; ++e) out[e] = Ar::out(acc[e]);
+  for (int e = 0; e < M * N; ++e) Ar::store(out + e, acc[e]);
 }
 
 // Row-stationary numeric pass for tall X blocks (M = 6: R (A P) and the coarse
@@ -343,12 +380,12 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
 constexpr int RS_WARPS = 4;
 constexpr int RS_ACC_BYTES = 16384;
 
-template <int M, int K, int N, class Ar>
+template <int M, int K, int N, class Ar, typename OutT>
 __global__ void __launch_bounds__(RS_WARPS * 32)
 spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
                          const typename Ar::V* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
-                         double* __restrict__ cv) {
+                         OutT* __restrict__ cv) {
   using V = typename Ar::V;
   using A = typename Ar::A;
   constexpr int MN = M * N;
@@ -410,14 +447,14 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
       }
       __syncwarp();
     }
-    for (int i = lane; i < wn * MN; i += 32) cv[(size_t)w0 * MN + i] = Ar::out(acc[i]);
+    for (int i = lane; i < wn * MN; i += 32) Ar::store(cv + (size_t)w0 * MN + i, acc[i]);
     __syncwarp();
   }
 }
 
-template <int M, int K, int N, class Ar>
+template <int M, int K, int N, class Ar, typename OutT>
 void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const typename Ar::V* yv, Bsr& C,
-                    cudaStream_t s) {
+                    OutT* cv, cudaStream_t s) {
   if (C.nnzb == 0) return;
   // 3-row blocks (A P_tent, A P on the finest level) keep the output-stationary
   // pass: with only 3 rows per item the row-stationary warp idles (measured
@@ -427,22 +464,24 @@ void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const 
     const size_t smem = (size_t)RS_WARPS * (RS_ACC_BYTES + W * 4);
     static bool attr_set = false;
     if (!attr_set) {
-      TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_rs_kernel<M, K, N, Ar>,
+      TAM_CUDA(cudaFuncSetAttribute(spgemm_numeric_rs_kernel<M, K, N, Ar, OutT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_set = true;
     }
-    spgemm_numeric_rs_kernel<M, K, N, Ar><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
-        X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, C.vals.p);
+    spgemm_numeric_rs_kernel<M, K, N, Ar, OutT><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
+        X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv);
     TAM_LAUNCH_CHECK();
     return;
   }
   DBuf<int> crow((size_t)C.nnzb, s);
   expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
   TAM_LAUNCH_CHECK();
-  spgemm_numeric_os_kernel<M, K, N, Ar><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
-      X.row_ptr.p, X.col_idx.p, xv, Y.row_ptr.p, Y.col_idx.p, yv, crow.p, C.col_idx.p, C.nnzb, C.vals.p);
+  spgemm_numeric_os_kernel<M, K, N, Ar, OutT><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
+      X.row_ptr.p, X.col_idx.p, xv, Y.row_ptr.p, Y.col_idx.p, yv, crow.p, C.col_idx.p, C.nnzb, cv);
   TAM_LAUNCH_CHECK();
 }
+
+}  // namespace
 
 DBuf<float2> split_values(const Bsr& B, cudaStream_t s) {
   const long long n = B.nnzb * (long long)B.block_elems();
@@ -454,19 +493,29 @@ DBuf<float2> split_values(const Bsr& B, cudaStream_t s) {
   return out;
 }
 
-}  // namespace
-
 template <int M, int K, int N>
-void launch_numeric_any(const Bsr& X, const Bsr& Y, Bsr& C, SpgemmArith arith, cudaStream_t s) {
+void launch_numeric_any(const Bsr& X, const Bsr& Y, Bsr& C, SpgemmArith arith, const SpgemmSplit& sp,
+                        cudaStream_t s) {
   if (arith == SpgemmArith::kFp64) {
-    launch_numeric<M, K, N, ArithF64>(X, X.vals.p, Y, Y.vals.p, C, s);
+    C.vals = DBuf<double>((size_t)C.nnzb * C.block_elems(), s);
+    launch_numeric<M, K, N, ArithF64>(X, X.vals.p, Y, Y.vals.p, C, C.vals.p, s);
+    return;
+  }
+  DBuf<float2> xs, ys;
+  const float2* xv = sp.x;
+  const float2* yv = sp.y;
+  if (!xv) xs = split_values(X, s), xv = xs.p;
+  if (!yv) ys = split_values(Y, s), yv = ys.p;
+  if (sp.c) {
+    *sp.c = DBuf<float2>((size_t)std::max<long long>(1, C.nnzb * (long long)C.block_elems()), s);
+    launch_numeric<M, K, N, ArithDF>(X, xv, Y, yv, C, sp.c->p, s);
   } else {
-    DBuf<float2> xs = split_values(X, s), ys = split_values(Y, s);
-    launch_numeric<M, K, N, ArithDF>(X, xs.p, Y, ys.p, C, s);
+    C.vals = DBuf<double>((size_t)C.nnzb * C.block_elems(), s);
+    launch_numeric<M, K, N, ArithDF>(X, xv, Y, yv, C, C.vals.p, s);
   }
 }
 
-void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith arith) {
+void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith arith, const SpgemmSplit& sp) {
   TAM_CHECK(X.bc == Y.br && X.n_cols == Y.n_rows, TAM_ERR_INTERNAL, "spgemm: shape mismatch");
   C.n_rows = X.n_rows;
   C.n_cols = Y.n_cols;
@@ -485,18 +534,17 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
   TAM_CHECK(read_back_int(overflow.p, s) == 0, TAM_ERR_INTERNAL,
             "spgemm: an output row exceeds 1536 blocks");
   C.col_idx = DBuf<int>((size_t)C.nnzb, s);
-  C.vals = DBuf<double>((size_t)C.nnzb * C.block_elems(), s);
   spgemm_symbolic_kernel<true><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
                                                             Y.col_idx.p, nullptr, C.row_ptr.p, C.col_idx.p,
                                                             overflow.p);
   TAM_LAUNCH_CHECK();
   const int m = X.br, k = X.bc, n = Y.bc;
-  if (m == 3 && k == 3 && n == 6) launch_numeric_any<3, 3, 6>(X, Y, C, arith, s);
-  else if (m == 6 && k == 3 && n == 6) launch_numeric_any<6, 3, 6>(X, Y, C, arith, s);
-  else if (m == 6 && k == 6 && n == 6) launch_numeric_any<6, 6, 6>(X, Y, C, arith, s);
-  else if (m == 3 && k == 3 && n == 3) launch_numeric_any<3, 3, 3>(X, Y, C, arith, s);
-  else if (m == 6 && k == 6 && n == 3) launch_numeric_any<6, 6, 3>(X, Y, C, arith, s);
-  else if (m == 3 && k == 6 && n == 6) launch_numeric_any<3, 6, 6>(X, Y, C, arith, s);
+  if (m == 3 && k == 3 && n == 6) launch_numeric_any<3, 3, 6>(X, Y, C, arith, sp, s);
+  else if (m == 6 && k == 3 && n == 6) launch_numeric_any<6, 3, 6>(X, Y, C, arith, sp, s);
+  else if (m == 6 && k == 6 && n == 6) launch_numeric_any<6, 6, 6>(X, Y, C, arith, sp, s);
+  else if (m == 3 && k == 3 && n == 3) launch_numeric_any<3, 3, 3>(X, Y, C, arith, sp, s);
+  else if (m == 6 && k == 6 && n == 3) launch_numeric_any<6, 6, 3>(X, Y, C, arith, sp, s);
+  else if (m == 3 && k == 6 && n == 6) launch_numeric_any<3, 6, 6>(X, Y, C, arith, sp, s);
   else throw Error(TAM_ERR_UNSUPPORTED, "spgemm: block shape not instantiated");
 }
 

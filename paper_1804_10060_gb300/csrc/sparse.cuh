@@ -58,8 +58,20 @@ void bsr_transpose(const Bsr& A, Bsr& R, cudaStream_t s);
 // FP64 operand split into two FP32 values, products and sums in FP32 with
 // error-free transforms, about 2^-48 relative; FP64 in and out).
 enum class SpgemmArith { kFp64, kDoubleFloat };
+// Double-float operands and result kept split: x / y are X's / Y's values
+// already split (NULL: split here); c (not NULL): C's values are written split
+// into *c and C.vals stays empty (for a product that only feeds another
+// double-float product).  Ignored for kFp64.
+struct SpgemmSplit {
+  const float2* x = nullptr;
+  const float2* y = nullptr;
+  DBuf<float2>* c = nullptr;
+};
+// FP64 values split into (hi, lo) FP32 pairs with integer operations only.
+DBuf<float2> split_values(const Bsr& B, cudaStream_t s);
 // C = X Y (block shapes 3/6).
-void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith arith = SpgemmArith::kDoubleFloat);
+void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith arith = SpgemmArith::kDoubleFloat,
+                const SpgemmSplit& sp = SpgemmSplit());
 
 // ---------------------------------------------------------------------------
 // Thread-per-row SELL SpMV with a fused epilogue.
