@@ -2,6 +2,8 @@
 // transpose and the block SpGEMM C = X * Y used for A P_tent and R (A P).
 #include <algorithm>
 
+#include <type_traits>
+
 #include "sparse.cuh"
 
 namespace tam {
@@ -377,11 +379,35 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
 // Columns in a Y row are distinct, so the items of one X entry never touch the
 // same accumulator element and no atomics are needed; X entries are processed
 // one after the other.  Most of the warp does useful work (items = M * |Y row|).
+// CNT consecutive 8-byte values (double or float2) into registers with
+// 16-byte loads (CNT even; p 16-byte aligned: block sizes 18 and 36 values).
+template <int CNT, typename V>
+__device__ __forceinline__ void load_block(const V* __restrict__ p, V (&out)[CNT]) {
+  static_assert(sizeof(V) == 8 && CNT % 2 == 0, "load_block: 8-byte values, even count");
+  if constexpr (std::is_same<V, double>::value) {
+    const double2* __restrict__ p2 = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < CNT / 2; ++i) {
+      const double2 v = __ldg(p2 + i);
+      out[2 * i] = v.x;
+      out[2 * i + 1] = v.y;
+    }
+  } else {
+    const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < CNT / 2; ++i) {
+      const float4 v = __ldg(p4 + i);
+      out[2 * i] = make_float2(v.x, v.y);
+      out[2 * i + 1] = make_float2(v.z, v.w);
+    }
+  }
+}
+
 constexpr int RS_WARPS = 4;
 constexpr int RS_ACC_BYTES = 16384;
 
 template <int M, int K, int N, class Ar, typename OutT>
-__global__ void __launch_bounds__(RS_WARPS * 32)
+__global__ void __launch_bounds__(RS_WARPS * 32, 1)
 spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
                          const typename Ar::V* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
@@ -423,26 +449,42 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
         qe = lo;
       }
       const V* __restrict__ xb = xv + (size_t)p * M * K;
-      const int items = (qe - qs) * M;
-      for (int it = lane; it < items; it += 32) {
-        const int q = qs + it / M, r = it % M;
-        const int c = yci[q];
-        int lo = 0, hi = wn - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (wcols[mid] < c) lo = mid + 1; else hi = mid;
+      // G groups of M lanes: group g takes Y entry qs + q0 + g, lane r of the
+      // group its block row r.  One lane per group finds the entry's window
+      // slot and shares it; each lane then loads the whole Y block at once
+      // (registers are free: shared memory bounds the occupancy) and
+      // accumulates row r of X_ij Y_jq.
+      constexpr int G = 32 / M;
+      const int g = lane / M, r = lane % M;
+      const int nq = qe - qs;
+      for (int q0 = 0; q0 < nq; q0 += G) {
+        const int qi = q0 + g;
+        const bool has = g < G && qi < nq;
+        int pos = 0;
+        if (has && r == 0) {
+          const int c = yci[qs + qi];
+          int lo = 0, hi = wn - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (wcols[mid] < c) lo = mid + 1; else hi = mid;
+          }
+          pos = lo;
         }
-        V xr[K];
+        pos = __shfl_sync(0xffffffffu, pos, min(g * M, 31));
+        if (has) {
+          V xr[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) xr[k] = xb[r * K + k];
-        const V* __restrict__ yb = yv + (size_t)q * K * N;
-        A* a = acc + lo * MN + r * N;
+          for (int k = 0; k < K; ++k) xr[k] = xb[r * K + k];
+          V yr[K * N];
+          load_block<K * N>(yv + (size_t)(qs + qi) * K * N, yr);
+          A* a = acc + pos * MN + r * N;
 #pragma unroll
-        for (int s2 = 0; s2 < N; ++s2) {
-          A t = a[s2];
+          for (int s2 = 0; s2 < N; ++s2) {
+            A t = a[s2];
 #pragma unroll
-          for (int k = 0; k < K; ++k) Ar::fma(t, xr[k], yb[k * N + s2]);
-          a[s2] = t;
+            for (int k = 0; k < K; ++k) Ar::fma(t, xr[k], yr[k * N + s2]);
+            a[s2] = t;
+          }
         }
       }
       __syncwarp();
@@ -459,7 +501,7 @@ void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const 
   // 3-row blocks (A P_tent, A P on the finest level) keep the output-stationary
   // pass: with only 3 rows per item the row-stationary warp idles (measured
   // 2x slower on the 256x64x64 box).
-  if (M == 6) {
+  if constexpr (M == 6) {
     constexpr int W = RS_ACC_BYTES / (M * N * (int)sizeof(typename Ar::A));
     const size_t smem = (size_t)RS_WARPS * (RS_ACC_BYTES + W * 4);
     static bool attr_set = false;
@@ -471,14 +513,14 @@ void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const 
     spgemm_numeric_rs_kernel<M, K, N, Ar, OutT><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
         X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv);
     TAM_LAUNCH_CHECK();
-    return;
+  } else {
+    DBuf<int> crow((size_t)C.nnzb, s);
+    expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
+    TAM_LAUNCH_CHECK();
+    spgemm_numeric_os_kernel<M, K, N, Ar, OutT><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
+        X.row_ptr.p, X.col_idx.p, xv, Y.row_ptr.p, Y.col_idx.p, yv, crow.p, C.col_idx.p, C.nnzb, cv);
+    TAM_LAUNCH_CHECK();
   }
-  DBuf<int> crow((size_t)C.nnzb, s);
-  expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
-  TAM_LAUNCH_CHECK();
-  spgemm_numeric_os_kernel<M, K, N, Ar, OutT><<<grid_for(C.nnzb, 128), 128, 0, s>>>(
-      X.row_ptr.p, X.col_idx.p, xv, Y.row_ptr.p, Y.col_idx.p, yv, crow.p, C.col_idx.p, C.nnzb, cv);
-  TAM_LAUNCH_CHECK();
 }
 
 }  // namespace
