@@ -172,6 +172,12 @@ typedef struct amg_params {
                               or in double-float, two FP32 values per operand with error-free transforms,
                               about 2^-47 relative, faster on GB300 (0, default); double-float loses
                               accuracy on operand entries below about 2^-100 in magnitude            */
+  int spmv_fp64;           /* products of the solve's SpMVs (outer CG, V-cycle operators): 0 (default)
+                              double-float, on split copies of the matrix values (same 8 bytes per
+                              value, about 2^-47 relative, bound by memory instead of GB300's FP64
+                              pipe), for operators of at least 2^20 blocks and plain FP64 below;
+                              1 plain FP64 everywhere; 2 double-float everywhere.  Vectors and all
+                              other arithmetic stay FP64                                            */
 } amg_params;
 
 /* Fills *p with the defaults above. */

@@ -729,7 +729,8 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
                 prm.max_levels >= 1 && prm.max_levels <= 20 && prm.coarse_max_dofs >= 1 && prm.coarse_min_dofs >= 0 && prm.aggressive_levels >= 0 &&
                 prm.small_level_dofs >= 0 && prm.small_level_degree >= 1 && prm.small_level_degree <= 32 &&
                 prm.cheb_hi > prm.cheb_lo && prm.cheb_lo > 0 && prm.strength_theta >= 0 &&
-                prm.strength_theta_scale >= 0,
+                prm.strength_theta_scale >= 0 && (prm.setup_fp64 == 0 || prm.setup_fp64 == 1) &&
+                prm.spmv_fp64 >= 0 && prm.spmv_fp64 <= 2,
             TAM_ERR_INVALID_ARG, "amg_setup: parameter out of range");
   auto H = new tam_amg_s();
   PhaseTimer T;
@@ -758,7 +759,17 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
     H->levels.emplace_back();
     H->levels[0].A = &K->A;
     H->levels[0].AS = &K->S;
-    H->levels[0].Aop = SpOp{&K->A, &K->S, choose_lpr(K->A)};
+    {
+      // K's split copies exist for its SELL form and, when its own operator
+      // runs on the block-CSR arrays, for those (see fem_assemble_elasticity)
+      const bool df0 = use_df(K->A, prm.spmv_fp64);
+      Level& L0 = H->levels[0];
+      L0.Aop = SpOp{&K->A, &K->S, choose_lpr(K->A), df0};
+      if (lpr_store_pays(L0.Aop.lpr)) {
+        build_lpr_store(K->A, L0.Aop.lpr, df0, L0.AL, s);
+        L0.Aop.L = &L0.AL;
+      }
+    }
     for (int lev = 0;; ++lev) {
       Level& L = H->levels[lev];
       L.n_rows = L.A->n_rows;
@@ -825,14 +836,40 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
         bsr_spgemm(L.R, AP, C.A_own, s, arith, spR);
         C.A = &C.A_own;
         C.AS = &C.AS_own;
-        C.Aop = SpOp{&C.A_own, &C.AS_own, choose_lpr(C.A_own)};
+        const bool cdf = use_df(C.A_own, prm.spmv_fp64);
+        C.Aop = SpOp{&C.A_own, &C.AS_own, choose_lpr(C.A_own), cdf};
         if (C.Aop.lpr == 0) bsr_to_sell(C.A_own, C.AS_own, s);
+        if (C.Aop.lpr == 0) {
+          if (cdf) build_df_values(C.AS_own, s);
+        } else if (lpr_store_pays(C.Aop.lpr)) {
+          build_lpr_store(C.A_own, C.Aop.lpr, cdf, C.AL, s);
+          C.Aop.L = &C.AL;
+        } else if (cdf) {
+          build_df_values(C.A_own, s);
+        }
       }
-      L.Pop = SpOp{&L.P, &L.PS, choose_lpr(L.P)};
-      L.Rop = SpOp{&L.R, &L.RS, choose_lpr(L.R)};
+      const bool pdf = use_df(L.P, prm.spmv_fp64);
+      L.Pop = SpOp{&L.P, &L.PS, choose_lpr(L.P), pdf};
+      L.Rop = SpOp{&L.R, &L.RS, choose_lpr(L.R), pdf};
       T.mark(6, s);
       if (L.Pop.lpr == 0) bsr_to_sell(L.P, L.PS, s);
       if (L.Rop.lpr == 0) bsr_to_sell(L.R, L.RS, s);
+      if (L.Pop.lpr == 0) {
+        if (pdf) build_df_values(L.PS, s);
+      } else if (lpr_store_pays(L.Pop.lpr)) {
+        build_lpr_store(L.P, L.Pop.lpr, pdf, L.PL, s);
+        L.Pop.L = &L.PL;
+      } else if (pdf) {
+        build_df_values(L.P, s);
+      }
+      if (L.Rop.lpr == 0) {
+        if (pdf) build_df_values(L.RS, s);
+      } else if (lpr_store_pays(L.Rop.lpr)) {
+        build_lpr_store(L.R, L.Rop.lpr, pdf, L.RL, s);
+        L.Rop.L = &L.RL;
+      } else if (pdf) {
+        build_df_values(L.R, s);
+      }
       B = std::move(Bc);
     }
     H->r = DBuf<double>((size_t)n0 * 3, s);

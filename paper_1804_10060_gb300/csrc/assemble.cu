@@ -163,18 +163,40 @@ __global__ void __launch_bounds__(128) assemble_p1_kernel(AsmArgs A) {
   if (A.body)
     for (int b = 0; b < 4; ++b)
       for (int d = 0; d < 3; ++d) fsum[d] += A.body[3 * (size_t)v[b] + d];
+  // K_ab[i][j] = lg_a[i] g_b[j] + mg_a[j] g_b[i] + delta_ij (mg_a . g_b) with
+  // lg = lam vol g, mg = mu vol g; K_ba = K_ab^T, so only a <= b is formed
+  // (FP64 is GB300's scarce pipe) and the transpose is scattered for b > a.
+  double lg[4][3], mg[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lg[a][i] = lam * vol * g[a][i];
+      mg[a][i] = mu * vol * g[a][i];
+    }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      const bool ab = !A.dmask[v[a]] && block_needed(A, v[b]);
+      const bool ba = b != a && !A.dmask[v[b]] && block_needed(A, v[a]);
+      if (!ab && !ba) continue;
+      const double mgg = mg[a][0] * g[b][0] + mg[a][1] * g[b][1] + mg[a][2] * g[b][2];
+      double k[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) k[3 * i + j] = fma(lg[a][i], g[b][j], mg[a][j] * g[b][i]) + (i == j ? mgg : 0.0);
+      if (ab) scatter_block(A, v[a], v[b], k);
+      if (ba) {
+        const double kt[9] = {k[0], k[3], k[6], k[1], k[4], k[7], k[2], k[5], k[8]};
+        scatter_block(A, v[b], v[a], kt);
+      }
+    }
+  }
   for (int a = 0; a < 4; ++a) {
     const int na = v[a];
     if (A.dmask[na]) continue;
-    for (int b = 0; b < 4; ++b) {
-      if (!block_needed(A, v[b])) continue;
-      double gg = g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2];
-      double k[9];
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-          k[3 * i + j] = vol * (lam * g[a][i] * g[b][j] + mu * g[a][j] * g[b][i] + (i == j ? mu * gg : 0.0));
-      scatter_block(A, na, v[b], k);
-    }
     // body: int f_h phi_a = vol/20 (sum_b f_b + f_a) (P1 mass matrix vol (1 + delta_ab)/20)
     for (int i = 0; i < 3; ++i) {
       double f = cT * g[a][i];
@@ -405,6 +427,10 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
     M->dmask = DBuf<unsigned char>((size_t)n_nodes, s);
     TAM_CUDA(cudaMemcpyAsync(M->dmask.p, dmask, n_nodes, cudaMemcpyDeviceToDevice, s));
     bsr_to_sell(A, M->S, s);
+    // split copies for the double-float SpMV: SELL always (the CG's own SpMVs
+    // with K use it), the block-CSR only where K's operator runs on it
+    build_df_values(M->S, s);
+    if (choose_lpr(A) != 0) build_df_values(A, s);
     TAM_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     delete M;

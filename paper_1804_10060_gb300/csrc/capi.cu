@@ -141,6 +141,7 @@ int amg_params_default(amg_params* p) {
     p->level_precision = 0;
     p->strength_theta_scale = 1.0;
     p->setup_fp64 = 0;
+    p->spmv_fp64 = 0;
     return TAM_OK;
   });
 }

@@ -45,6 +45,7 @@ struct Level {
   Bsr Pt, P, R;             // tentative prolongator, smoothed prolongator, R = P^T
   Sell PS, RS;
   SpOp Aop, Pop, Rop;       // SpMV strategy per operator (SELL thread-per-row or lanes per row)
+  LprStore AL, PL, RL;      // interleaved lanes-per-row copies of the operators that use lanes per row
   // V-cycle work vectors (n_rows*bs each)
   DBuf<double> b, xa, xb, d, t, y;  // y: the level's V-cycle result (never an internal buffer)
   double lambda_host = 0.0;

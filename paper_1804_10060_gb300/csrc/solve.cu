@@ -324,7 +324,7 @@ void precondition(tam_amg_s* H, const double* r, double* z, const int* stop, cud
 
 void spmv_outer_pq(tam_amg_s* H, cudaStream_t s) {
   GridReduce gr{H->partials.p, H->ticket.p};
-  sell_spmv<3, 3>(H->K->S, H->p.p, EpiPq<3>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s);
+  sell_spmv<3, 3>(H->K->S, H->p.p, EpiPq<3>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s, H->levels[0].Aop.df);
 }
 
 void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
@@ -369,7 +369,7 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   PcgScalars* sc = H->sc.p;
   pcg_start_kernel<<<vec_grid(N), TPB, 0, s>>>(b, N, gr, sc, rtol, atol, max_iter);
   TAM_LAUNCH_CHECK();
-  sell_spmv<3, 3>(H->K->S, x, EpiInitResidual<3>{b, H->r.p, H->K->n_nodes, gr, sc}, s);
+  sell_spmv<3, 3>(H->K->S, x, EpiInitResidual<3>{b, H->r.p, H->K->n_nodes, gr, sc}, s, H->levels[0].Aop.df);
   precondition(H, H->r.p, H->z.p, &sc->stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, sc, 1);
   TAM_LAUNCH_CHECK();
@@ -421,7 +421,7 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   }
   // final true residual
   DBuf<double> rn(1, s);
-  sell_spmv<3, 3>(H->K->S, x, EpiResNorm<3>{b, H->K->n_nodes, gr, rn.p}, s);
+  sell_spmv<3, 3>(H->K->S, x, EpiResNorm<3>{b, H->K->n_nodes, gr, rn.p}, s, H->levels[0].Aop.df);
   PcgScalars host;
   TAM_CUDA(cudaMemcpyAsync(&host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   double rr = read_back_double(rn.p, s);  // synchronises the stream

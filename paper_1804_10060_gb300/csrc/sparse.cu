@@ -75,6 +75,80 @@ void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s) {
       A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, S.n_slices, (int)A.block_elems(),
       S.slice_ptr.p, S.cols.p, S.vals.p, false);
   TAM_LAUNCH_CHECK();
+  if (S.vals_df.p) build_df_values(S, s);
+}
+
+namespace {
+__global__ void split_values_kernel(const double* __restrict__ in, float2* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = split_bits(in[i]);
+}
+
+void split_into(const double* in, long long n, DBuf<float2>& out, cudaStream_t s) {
+  if (out.n != (size_t)std::max(1LL, n)) out = DBuf<float2>((size_t)std::max(1LL, n), s);
+  if (n > 0) {
+    split_values_kernel<<<std::min<unsigned>(grid_for(n, 256), 152u * 16u), 256, 0, s>>>(in, out.p, n);
+    TAM_LAUNCH_CHECK();
+  }
+}
+}  // namespace
+
+namespace {
+__global__ void lpr_count_kernel(const int* __restrict__ rp, int n_rows, int lpr, int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_rows) cnt[i] = (rp[i + 1] - rp[i] + lpr - 1) / lpr;
+}
+
+// One warp per row; the lanes walk the row's output range in storage order
+// (coalesced writes) and gather from the block-CSR arrays.
+__global__ void lpr_fill_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                                int n_rows, int lpr, int bb, const int* __restrict__ gp, int* __restrict__ cols,
+                                double* __restrict__ vals) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= n_rows) return;
+  const int s0 = rp[i], e0 = rp[i + 1], g0 = gp[i], ng = gp[i + 1] - g0;
+  const int lastc = e0 > s0 ? ci[e0 - 1] : 0;
+  for (int k = lane; k < ng * lpr; k += 32) {
+    const int idx = s0 + k;  // group k / lpr, slot k % lpr: storage index g0 * lpr + k
+    cols[(size_t)g0 * lpr + k] = idx < e0 ? ci[idx] : lastc;
+  }
+  const long long o0 = (long long)g0 * bb * lpr, n_out = (long long)ng * bb * lpr;
+  for (long long q = lane; q < n_out; q += 32) {
+    const long long o = o0 + q;
+    const long long g = o / ((long long)bb * lpr);
+    const int rem = (int)(o - g * bb * lpr), el = rem / lpr, j = rem % lpr;
+    const int idx = s0 + (int)(g - g0) * lpr + j;
+    vals[o] = idx < e0 ? v[(size_t)idx * bb + el] : 0.0;
+  }
+}
+}  // namespace
+
+void build_lpr_store(const Bsr& A, int lpr, bool df, LprStore& L, cudaStream_t s) {
+  TAM_CHECK(lpr >= 2 && lpr <= 32 && (lpr & (lpr - 1)) == 0, TAM_ERR_INTERNAL, "lanes-per-row width must be 2..32");
+  L.lpr = lpr;
+  L.n_rows = A.n_rows;
+  L.br = A.br;
+  L.bc = A.bc;
+  L.grp_ptr = DBuf<int>((size_t)A.n_rows + 1, s);
+  lpr_count_kernel<<<grid_for(A.n_rows, 256), 256, 0, s>>>(A.row_ptr.p, A.n_rows, lpr, L.grp_ptr.p);
+  TAM_LAUNCH_CHECK();
+  exclusive_scan_i32(L.grp_ptr.p, L.grp_ptr.p, A.n_rows, s);
+  L.n_groups = read_back_int(L.grp_ptr.p + A.n_rows, s);
+  const long long n = L.n_groups * lpr;
+  L.cols = DBuf<int>((size_t)std::max(1LL, n), s);
+  L.vals = DBuf<double>((size_t)std::max(1LL, n * (long long)A.block_elems()), s);
+  lpr_fill_kernel<<<grid_for((long long)A.n_rows * 32, 256), 256, 0, s>>>(
+      A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, lpr, (int)A.block_elems(), L.grp_ptr.p, L.cols.p, L.vals.p);
+  TAM_LAUNCH_CHECK();
+  if (df) split_into(L.vals.p, n * (long long)A.block_elems(), L.vals_df, s);
+}
+
+void build_df_values(Sell& S, cudaStream_t s) {
+  split_into(S.vals.p, S.n_slots * 32 * (long long)S.br * S.bc, S.vals_df, s);
+}
+
+void build_df_values(Bsr& B, cudaStream_t s) {
+  split_into(B.vals.p, B.nnzb * (long long)B.block_elems(), B.vals_df, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -253,42 +327,6 @@ __global__ void expand_rows_kernel(const int* __restrict__ rp, int n_rows, int* 
 // the F64 form, so the ~12 FP32 operations per multiply-add are the cheaper
 // way to the same accuracy class.  __fadd_rn/__fmul_rn keep the compiler from
 // contracting the error-free transforms into FMAs.
-// IEEE-754 bit manipulations (integer pipe only: GB300's FP64 pipe, which also
-// executes FP64<->FP32 conversions, is the scarce resource here).
-//
-// split_bits: v = hi + lo exactly up to the last 5 bits of the 29 mantissa
-// bits below hi's 24 (relative error <= 2^-47): hi keeps the sign, the
-// exponent and the top 23 stored mantissa bits of v (truncation); lo is the
-// remaining 29-bit tail, normalised and truncated to 24 bits.  |v| < 2^-126
-// (zero, FP64 values below FP32's normal range) gives (0, 0); a tail below
-// FP32's normal range gives lo = 0.
-__device__ __forceinline__ float2 split_bits(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned sign = (unsigned)(b >> 63) << 31;
-  const int ef = (int)((b >> 52) & 0x7ff) - 1023 + 127;  // FP32 biased exponent of hi
-  if (ef <= 0) return make_float2(0.f, 0.f);
-  if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
-  const unsigned long long m = b & 0xfffffffffffffull;
-  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(m >> 29));
-  const unsigned low = (unsigned)(m & 0x1fffffffull);  // weight 2^(E - 52) per unit
-  if (low == 0) return make_float2(hi, 0.f);
-  const int lz = __clz(low);                            // 3..31
-  const int el = ef - 52 + (31 - lz);                   // FP32 biased exponent of lo
-  if (el <= 0) return make_float2(hi, 0.f);
-  const unsigned frac = (unsigned)(((unsigned long long)low << (lz + 1)) & 0xffffffffull) >> 9;
-  return make_float2(hi, __uint_as_float(sign | ((unsigned)el << 23) | frac));
-}
-
-// Exact FP32 -> FP64 (zero and FP32 subnormals give 0; inf/nan keep their class).
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xff;
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  if (e == 0) return __longlong_as_double((long long)sign);
-  const unsigned long long ed = e == 255 ? 0x7ffull : (unsigned long long)(e - 127 + 1023);
-  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
-}
-
 struct ArithF64 {
   using V = double;
   using A = double;
@@ -301,17 +339,7 @@ struct ArithDF {
   using V = float2;
   using A = float2;
   __device__ static A zero() { return make_float2(0.f, 0.f); }
-  __device__ static void fma(A& a, V x, V y) {
-    const float p = __fmul_rn(x.x, y.x);
-    float e = fmaf(x.x, y.x, -p);        // exact: x.x * y.x = p + e
-    e = fmaf(x.x, y.y, e);
-    e = fmaf(x.y, y.x, e);
-    const float s = __fadd_rn(a.x, p);   // TwoSum(a.x, p) = s + err exactly
-    const float bp = __fadd_rn(s, -a.x);
-    const float err = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
-    a.x = s;
-    a.y = __fadd_rn(a.y, __fadd_rn(err, e));
-  }
+  __device__ static void fma(A& a, V x, V y) { df_fma(a, x, y); }
   __device__ static void store(double* p, A a) { *p = f2d_bits(a.x) + f2d_bits(a.y); }
   // kept split for a following double-float product: renormalised (Fast2Sum)
   __device__ static void store(float2* p, A a) {
@@ -319,11 +347,6 @@ struct ArithDF {
     *p = make_float2(s, __fadd_rn(a.y, -__fadd_rn(s, -a.x)));
   }
 };
-
-__global__ void split_df_kernel(const double* __restrict__ in, float2* __restrict__ out, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = split_bits(in[i]);
-}
 
 template <int M, int K, int N, class Ar, typename OutT>
 __global__ void __launch_bounds__(128)
@@ -526,12 +549,8 @@ void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const 
 }  // namespace
 
 DBuf<float2> split_values(const Bsr& B, cudaStream_t s) {
-  const long long n = B.nnzb * (long long)B.block_elems();
-  DBuf<float2> out((size_t)std::max(1LL, n), s);
-  if (n > 0) {
-    split_df_kernel<<<std::min<unsigned>(grid_for(n, 256), 152u * 16u), 256, 0, s>>>(B.vals.p, out.p, n);
-    TAM_LAUNCH_CHECK();
-  }
+  DBuf<float2> out;
+  split_into(B.vals.p, B.nnzb * (long long)B.block_elems(), out, s);
   return out;
 }
 

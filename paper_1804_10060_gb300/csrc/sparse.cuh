@@ -10,6 +10,12 @@
 //         line, and every thread accumulates its own row with exactly br*bc
 //         FMAs per block and no cross-lane reduction -- the FP64 FMA pipe, not
 //         a shuffle tree, is the only arithmetic cost.
+//
+// Double-float ("DF"): either form may also hold vals_df, its values split
+// into (hi, lo) FP32 pairs (same 8 bytes per value).  The SpMV kernels then
+// multiply in FP32 with error-free transforms (about 2^-47 relative), which
+// GB300 issues at 64 times its FP64 FMA rate, so the SpMV is bound by memory
+// instead of the FP64 pipe; vectors and epilogues stay FP64.
 #pragma once
 
 #include <algorithm>
@@ -18,11 +24,66 @@
 
 namespace tam {
 
+// IEEE-754 bit manipulations (integer pipe only: GB300's FP64 pipe, which also
+// executes FP64<->FP32 conversions, is the scarce resource here).
+//
+// split_bits: v = hi + lo exactly up to the last 5 bits of the 29 mantissa
+// bits below hi's 24 (relative error <= 2^-47): hi keeps the sign, the
+// exponent and the top 23 stored mantissa bits of v (truncation); lo is the
+// remaining 29-bit tail, normalised and truncated to 24 bits.  |v| < 2^-126
+// (zero, FP64 values below FP32's normal range) gives (0, 0); a tail below
+// FP32's normal range gives lo = 0.
+__device__ __forceinline__ float2 split_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int ef = (int)((b >> 52) & 0x7ff) - 1023 + 127;  // FP32 biased exponent of hi
+  if (ef <= 0) return make_float2(0.f, 0.f);
+  if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(m >> 29));
+  const unsigned low = (unsigned)(m & 0x1fffffffull);  // weight 2^(E - 52) per unit
+  if (low == 0) return make_float2(hi, 0.f);
+  const int lz = __clz(low);                            // 3..31
+  const int el = ef - 52 + (31 - lz);                   // FP32 biased exponent of lo
+  if (el <= 0) return make_float2(hi, 0.f);
+  const unsigned frac = (unsigned)(((unsigned long long)low << (lz + 1)) & 0xffffffffull) >> 9;
+  return make_float2(hi, __uint_as_float(sign | ((unsigned)el << 23) | frac));
+}
+
+// Exact FP32 -> FP64 (zero and FP32 subnormals give 0; inf/nan keep their class).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xff;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ed = e == 255 ? 0x7ffull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// a += x * y in double-float: the product of the high parts made exact with
+// an FMA, the two cross terms added to its error (lo * lo, below 2^-48 of the
+// product, dropped), the sum with the accumulator by Knuth's TwoSum.
+// __fadd_rn / __fmul_rn keep the compiler from contracting the transforms.
+__device__ __forceinline__ void df_fma(float2& a, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = fmaf(x.x, y.x, -p);        // exact: x.x * y.x = p + e
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  const float s = __fadd_rn(a.x, p);   // TwoSum(a.x, p) = s + err exactly
+  const float bp = __fadd_rn(s, -a.x);
+  const float err = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
+  a.x = s;
+  a.y = __fadd_rn(a.y, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ double df_to_double(float2 a) { return f2d_bits(a.x) + f2d_bits(a.y); }
+
 struct Bsr {
   int n_rows = 0, n_cols = 0, br = 0, bc = 0;
   long long nnzb = 0;
   DBuf<int> row_ptr, col_idx;
   DBuf<double> vals;
+  DBuf<float2> vals_df;   // optional split copy of vals (SpMV only)
   size_t block_elems() const { return (size_t)br * bc; }
 };
 
@@ -32,6 +93,7 @@ struct Sell {
   DBuf<int> slice_ptr;    // [n_slices + 1]
   DBuf<int> cols;         // [n_slots * 32]
   DBuf<double> vals;      // [n_slots * 32 * br * bc]
+  DBuf<float2> vals_df;   // optional split copy of vals
 };
 
 struct SellView {
@@ -39,15 +101,21 @@ struct SellView {
   const int* __restrict__ slice_ptr;
   const int* __restrict__ cols;
   const double* __restrict__ vals;
+  const float2* __restrict__ vals_df;
 };
 
 inline SellView view(const Sell& s) {
-  return SellView{s.n_rows, s.n_slices, s.slice_ptr.p, s.cols.p, s.vals.p};
+  return SellView{s.n_rows, s.n_slices, s.slice_ptr.p, s.cols.p, s.vals.p, s.vals_df.p};
 }
+
+// (Re)builds the split copy vals_df from vals (integer operations only).
+void build_df_values(Sell& S, cudaStream_t s);
+void build_df_values(Bsr& B, cudaStream_t s);
 
 // Builds the SELL-32 copy of a Bsr (pattern + values).
 void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s);
-// Refreshes only the values of an existing SELL copy built from A.
+// Refreshes only the values of an existing SELL copy built from A (and its
+// split copy, when it has one).
 void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s);
 
 // Transpose (block transpose included): R = A^T.  Rows of R sorted by column.
@@ -82,7 +150,7 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
 // ---------------------------------------------------------------------------
 constexpr int SPMV_THREADS = 128;
 
-template <int BR, int BC, class Epi>
+template <int BR, int BC, class Epi, bool DF>
 __global__ void __launch_bounds__(SPMV_THREADS)
 sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
   __shared__ double sh[32];
@@ -95,28 +163,54 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
   if (slice < A.n_slices) {
     const int k0 = A.slice_ptr[slice], k1 = A.slice_ptr[slice + 1];
     const int* __restrict__ cp = A.cols + (size_t)k0 * 32 + lane;
-    const double* __restrict__ vp = A.vals + (size_t)k0 * 32 * BR * BC + lane;
+    if constexpr (DF) {
+      const float2* __restrict__ vp = A.vals_df + (size_t)k0 * 32 * BR * BC + lane;
+      float2 ad[BR];
+#pragma unroll
+      for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
 #pragma unroll 2
-    for (int k = k0; k < k1; ++k) {
-      const int c = __ldg(cp);
-      double xv[BC];
+      for (int k = k0; k < k1; ++k) {
+        const int c = __ldg(cp);
+        float2 xv[BC];
 #pragma unroll
-      for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
+        for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
 #pragma unroll
-      for (int r = 0; r < BR; ++r)
+        for (int r = 0; r < BR; ++r)
 #pragma unroll
-        for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vp + (r * BC + j) * 32), xv[j], acc[r]);
-      cp += 32;
-      vp += 32 * BR * BC;
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vp + (r * BC + j) * 32), xv[j]);
+        cp += 32;
+        vp += 32 * BR * BC;
+      }
+#pragma unroll
+      for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
+    } else {
+      const double* __restrict__ vp = A.vals + (size_t)k0 * 32 * BR * BC + lane;
+#pragma unroll 2
+      for (int k = k0; k < k1; ++k) {
+        const int c = __ldg(cp);
+        double xv[BC];
+#pragma unroll
+        for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vp + (r * BC + j) * 32), xv[j], acc[r]);
+        cp += 32;
+        vp += 32 * BR * BC;
+      }
     }
   }
   epi(row, acc, sh);
 }
 
+// df: use the split copy when the matrix has one (false: plain FP64).
 template <int BR, int BC, class Epi>
-void sell_spmv(const Sell& A, const double* x, Epi epi, cudaStream_t s) {
+void sell_spmv(const Sell& A, const double* x, Epi epi, cudaStream_t s, bool df = true) {
   unsigned grid = grid_for((long long)A.n_slices * 32, SPMV_THREADS);
-  sell_spmv_kernel<BR, BC, Epi><<<grid, SPMV_THREADS, 0, s>>>(view(A), x, epi);
+  if (df && A.vals_df.p)
+    sell_spmv_kernel<BR, BC, Epi, true><<<grid, SPMV_THREADS, 0, s>>>(view(A), x, epi);
+  else
+    sell_spmv_kernel<BR, BC, Epi, false><<<grid, SPMV_THREADS, 0, s>>>(view(A), x, epi);
   TAM_LAUNCH_CHECK();
 }
 
@@ -134,9 +228,10 @@ struct BsrView {
   const int* __restrict__ rp;
   const int* __restrict__ ci;
   const double* __restrict__ v;
+  const float2* __restrict__ v_df;
 };
 
-template <int BR, int BC, int LPR, class Epi>
+template <int BR, int BC, int LPR, class Epi, bool DF>
 __global__ void __launch_bounds__(SPMV_THREADS)
 bsr_vector_kernel(BsrView A, const double* __restrict__ x, Epi epi) {
   __shared__ double sh[32];
@@ -148,16 +243,116 @@ bsr_vector_kernel(BsrView A, const double* __restrict__ x, Epi epi) {
   for (int r = 0; r < BR; ++r) acc[r] = 0.0;
   if (row < A.n_rows) {
     const int pe = A.rp[row + 1];
-    for (int p = A.rp[row] + sub; p < pe; p += LPR) {
-      const int c = A.ci[p];
-      const double* __restrict__ vb = A.v + (size_t)p * BR * BC;
-      double xv[BC];
+    if constexpr (DF) {
+      float2 ad[BR];
 #pragma unroll
-      for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
+      for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
+      for (int p = A.rp[row] + sub; p < pe; p += LPR) {
+        const int c = A.ci[p];
+        const float2* __restrict__ vb = A.v_df + (size_t)p * BR * BC;
+        float2 xv[BC];
 #pragma unroll
-      for (int r = 0; r < BR; ++r)
+        for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
 #pragma unroll
-        for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vb + r * BC + j), xv[j], acc[r]);
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vb + r * BC + j), xv[j]);
+      }
+#pragma unroll
+      for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
+    } else {
+      for (int p = A.rp[row] + sub; p < pe; p += LPR) {
+        const int c = A.ci[p];
+        const double* __restrict__ vb = A.v + (size_t)p * BR * BC;
+        double xv[BC];
+#pragma unroll
+        for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vb + r * BC + j), xv[j], acc[r]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  epi((sub == 0 && row < A.n_rows) ? row : A.n_rows, acc, sh);
+}
+
+// Lanes-per-row storage: each row's blocks in groups of lpr, a group stored
+// element-major (value e of the group's block j at vals[(g * bb + e) * lpr + j])
+// so that the lpr lanes of a row read lpr consecutive values per load -- with
+// the plain block-CSR arrays each lane reads its own block and a warp's load
+// touches 32 separate sectors.  Rows are padded to whole groups with zero
+// blocks whose column is the row's last (so no new column is read).
+struct LprStore {
+  int lpr = 0, n_rows = 0, br = 0, bc = 0;
+  long long n_groups = 0;
+  DBuf<int> grp_ptr;     // [n_rows + 1], in groups
+  DBuf<int> cols;        // [n_groups * lpr]
+  DBuf<double> vals;     // [n_groups * lpr * br * bc]
+  DBuf<float2> vals_df;  // optional split copy
+};
+
+// Builds L from A for lanes-per-row width lpr (and the split copy when df).
+void build_lpr_store(const Bsr& A, int lpr, bool df, LprStore& L, cudaStream_t s);
+// The interleaved store pays for 2..8 lanes per row (level-1 Chebyshev 177 ->
+// 111 us on the 3.2M-DOF box); the 16- and 32-lane launches on the smallest
+// levels ran 1.6x slower with it and keep the block-CSR arrays.
+inline bool lpr_store_pays(int lpr) { return lpr >= 2 && lpr <= 8; }
+
+struct LprView {
+  int n_rows;
+  const int* __restrict__ gp;
+  const int* __restrict__ cols;
+  const double* __restrict__ v;
+  const float2* __restrict__ v_df;
+};
+
+template <int BR, int BC, int LPR, class Epi, bool DF>
+__global__ void __launch_bounds__(SPMV_THREADS)
+lpr_spmv_kernel(LprView A, const double* __restrict__ x, Epi epi) {
+  __shared__ double sh[32];
+  if (epi.skip()) return;
+  const int t = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int row = t / LPR, sub = t % LPR;
+  constexpr int BB = BR * BC;
+  double acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = 0.0;
+  if (row < A.n_rows) {
+    const int g0 = A.gp[row], g1 = A.gp[row + 1];
+    if constexpr (DF) {
+      float2 ad[BR];
+#pragma unroll
+      for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
+      for (int g = g0; g < g1; ++g) {
+        const int c = __ldg(A.cols + (size_t)g * LPR + sub);
+        float2 xv[BC];
+#pragma unroll
+        for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
+        const float2* __restrict__ vb = A.v_df + (size_t)g * BB * LPR + sub;
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vb + (r * BC + j) * LPR), xv[j]);
+      }
+#pragma unroll
+      for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
+    } else {
+      for (int g = g0; g < g1; ++g) {
+        const int c = __ldg(A.cols + (size_t)g * LPR + sub);
+        double xv[BC];
+#pragma unroll
+        for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
+        const double* __restrict__ vb = A.v + (size_t)g * BB * LPR + sub;
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vb + (r * BC + j) * LPR), xv[j], acc[r]);
+      }
     }
   }
 #pragma unroll
@@ -168,12 +363,25 @@ bsr_vector_kernel(BsrView A, const double* __restrict__ x, Epi epi) {
 }
 
 // A sparse operator with its SpMV strategy: SELL-32 thread-per-row (lpr == 0)
-// or LPR lanes per row over the Bsr arrays.
+// or LPR lanes per row (over the interleaved store L when built, else over the
+// Bsr arrays).
 struct SpOp {
   const Bsr* B = nullptr;
   const Sell* S = nullptr;
   int lpr = 0;
+  bool df = true;  // use the storage's split copy when it has one
+  const LprStore* L = nullptr;
 };
+
+// Double-float pays where an operator is large enough to be bound by memory;
+// on small operators (coarse levels) each lane's short dependent chain makes
+// the 12x FP32 instruction count a latency cost (measured up to 2x slower).
+// mode: amg_params.spmv_fp64 (0 auto, 1 never, 2 always).
+inline bool use_df(const Bsr& A, int mode) {
+  if (mode == 1) return false;
+  if (mode == 2) return true;
+  return A.nnzb >= (1LL << 20);
+}
 
 // Strategy: thread-per-row SELL for many short rows, else lanes per row.
 // Each lane should own >= ~16 blocks: the closing shuffle reduction costs
@@ -193,22 +401,51 @@ inline unsigned spop_grid(const SpOp& op) {
   return grid_for((long long)op.B->n_rows * op.lpr, SPMV_THREADS);
 }
 
+template <int BR, int BC, class Epi, bool DF>
+void bsr_vector_launch(const SpOp& op, const BsrView& v, const double* x, Epi epi, cudaStream_t s) {
+  const unsigned g = spop_grid(op);
+  switch (op.lpr) {
+    case 2: bsr_vector_kernel<BR, BC, 2, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    case 4: bsr_vector_kernel<BR, BC, 4, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    case 8: bsr_vector_kernel<BR, BC, 8, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    case 16: bsr_vector_kernel<BR, BC, 16, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    default: bsr_vector_kernel<BR, BC, 32, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+  }
+  TAM_LAUNCH_CHECK();
+}
+
+template <int BR, int BC, class Epi, bool DF>
+void lpr_launch(const SpOp& op, const LprView& v, const double* x, Epi epi, cudaStream_t s) {
+  const unsigned g = spop_grid(op);
+  switch (op.lpr) {
+    case 2: lpr_spmv_kernel<BR, BC, 2, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    case 4: lpr_spmv_kernel<BR, BC, 4, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    case 8: lpr_spmv_kernel<BR, BC, 8, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    case 16: lpr_spmv_kernel<BR, BC, 16, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+    default: lpr_spmv_kernel<BR, BC, 32, Epi, DF><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+  }
+  TAM_LAUNCH_CHECK();
+}
+
 template <int BR, int BC, class Epi>
 void spop_apply(const SpOp& op, const double* x, Epi epi, cudaStream_t s) {
   if (op.lpr == 0) {
-    sell_spmv<BR, BC>(*op.S, x, epi, s);
+    sell_spmv<BR, BC>(*op.S, x, epi, s, op.df);
     return;
   }
-  const BsrView v{op.B->n_rows, op.B->row_ptr.p, op.B->col_idx.p, op.B->vals.p};
-  const unsigned g = spop_grid(op);
-  switch (op.lpr) {
-    case 2: bsr_vector_kernel<BR, BC, 2, Epi><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
-    case 4: bsr_vector_kernel<BR, BC, 4, Epi><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
-    case 8: bsr_vector_kernel<BR, BC, 8, Epi><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
-    case 16: bsr_vector_kernel<BR, BC, 16, Epi><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
-    default: bsr_vector_kernel<BR, BC, 32, Epi><<<g, SPMV_THREADS, 0, s>>>(v, x, epi); break;
+  if (op.L) {
+    const LprView v{op.L->n_rows, op.L->grp_ptr.p, op.L->cols.p, op.L->vals.p, op.L->vals_df.p};
+    if (op.df && v.v_df)
+      lpr_launch<BR, BC, Epi, true>(op, v, x, epi, s);
+    else
+      lpr_launch<BR, BC, Epi, false>(op, v, x, epi, s);
+    return;
   }
-  TAM_LAUNCH_CHECK();
+  const BsrView v{op.B->n_rows, op.B->row_ptr.p, op.B->col_idx.p, op.B->vals.p, op.B->vals_df.p};
+  if (op.df && v.v_df)
+    bsr_vector_launch<BR, BC, Epi, true>(op, v, x, epi, s);
+  else
+    bsr_vector_launch<BR, BC, Epi, false>(op, v, x, epi, s);
 }
 
 // ---------------------------------------------------------------------------

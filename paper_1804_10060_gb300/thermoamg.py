@@ -47,6 +47,7 @@ class AmgParams(ctypes.Structure):
         ("level_precision", ctypes.c_int),
         ("strength_theta_scale", ctypes.c_double),
         ("setup_fp64", ctypes.c_int),
+        ("spmv_fp64", ctypes.c_int),
     ]
 
 

@@ -76,11 +76,13 @@ def test_hierarchy_matches_oracle_step_by_step(problem, coarse_min, theta):
         A_in, B, bs = Aco, Bc, 6
 
 
+@pytest.mark.parametrize("spmv_fp64", [1, 2])
 @pytest.mark.parametrize("problem", ["cube8", "slab_small"])
-def test_vcycle_matches_oracle(problem):
+def test_vcycle_matches_oracle(problem, spmv_fp64):
+    """V-cycle with its SpMVs in plain FP64 (1) or double-float everywhere (2)."""
     pb = {"cube8": lambda: meshgen.unit_cube_problem(8),
           "slab_small": lambda: meshgen.slab_box_problem(24, 8, 8)}[problem]()
-    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60)
+    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60, spmv_fp64=spmv_fp64)
     Ko, _ = fem.assemble_system(pb)
     Ho = oamg.setup(Ko, fem.rigid_body_modes(pb.coords, pb.dirichlet_mask), 3, coarse_max_dofs=60)
     assert [L.A.shape[0] for L in Ho.levels] == [r * b for r, b in zip(tam.amg_info(H)["rows"],

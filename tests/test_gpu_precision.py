@@ -115,3 +115,24 @@ def test_setup_products_match_oracle(setup_fp64):
         assert sparse_rel(P, oamg.smooth_prolongator(A, Pt, info["lambda"][lev])) <= 1e-10, lev
         Ac, _ = oamg.galerkin(A, P)
         assert sparse_rel(ex(lev + 1, 0), Ac) <= 1e-10, lev
+
+
+def test_double_float_spmv_matches_fp64_spmv():
+    """SpMVs of the solve in double-float on every operator (spmv_fp64 = 2) vs plain FP64 (1).
+
+    Double-float products are accurate to about 2^-47 of the terms, so both
+    arithmetics take the same number of iterations (+-1); their iterates then
+    differ by what the stopping point leaves (both stop at ||r|| <= 1e-8
+    ||b||; measured 1.4e-9 apart, bound 1e-7), and both match the direct
+    solve to 1e-6.
+    """
+    pb = meshgen.slab_box_problem(48, 12, 12)
+    _, _, _, _, xdf, itdf, reldf, stdf = _solve(pb, 0, spmv_fp64=2)
+    _, _, _, _, x64, it64, rel64, st64 = _solve(pb, 0, spmv_fp64=1)
+    assert stdf == 0 and st64 == 0 and reldf <= 1e-8 and rel64 <= 1e-8
+    assert abs(itdf - it64) <= 1, (itdf, it64)
+    assert float(torch.linalg.norm(xdf - x64) / torch.linalg.norm(x64)) <= 1e-7
+    Ko, fo = fem.assemble_system(pb)
+    u = linsolve.direct_solve(Ko, fo)
+    for x in (xdf, x64):
+        assert np.linalg.norm(x.cpu().numpy().ravel() - u) <= 1e-6 * np.linalg.norm(u)
