@@ -37,6 +37,10 @@ DIMS = (256, 64, 64)
 SAMPLE_DIMS = (96, 24, 24)      # bounded oracle sample (same structure, 181,875 DOF)
 FALLBACK_HBM_GBS = 6800.0       # recipe fallback when MEASURED_PEAKS.json is absent
 NOMINAL_FP64_TFLOPS = 1.25      # GB300 FP64 (nominal table)
+# DRAM bytes (read + write) of one double-float level-0 SpMV launch on the
+# 256x64x64 box: ncu capture of the same kernel on the 160x40x40 box (315.2 MB,
+# profiles/sell_spmv_box160x40x40.md) scaled by the block count (x 4.065).
+SPMV_DRAM_BYTES_FULL = 1.281e9
 
 
 def parse():
@@ -337,13 +341,7 @@ def native_arm(args):
     hbm_peak, hbm_src = peaks()
     achieved_tf = alg_flops / (spmv_ms * 1e-3) / 1e12
     achieved_gbs = alg_bytes / (spmv_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "spmv_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("bytes_per_launch_full_size")
-        except Exception:
-            traffic = None
+    traffic = SPMV_DRAM_BYTES_FULL if dims == DIMS else None
     # the SpMV multiplies in double-float on the FP32 pipe, so it is bound by
     # memory; the FP64-equivalent rate is given against GB300's FP64 peak
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -435,14 +433,11 @@ def native_arm(args):
 
 BATCH_WORKLOAD = ("64 load cases (seeded temperature field + omega ~ U[0,2] centrifugal load) on 8 meshes of "
                   "uneven size, 45,360-1,969,275 DOF, P1/P2 boxes and bladed discs (5,546,007 DOF in all); "
-                  "FP32 V-cycle with FP64 CG, all systems in one graph-captured multi-RHS solve, rtol 1e-8; "
-                  "strength threshold 0.02 (halved per level) on the discs, 0 on the boxes")
+                  "FP32 V-cycle with FP64 CG, all systems in one graph-captured multi-RHS solve, rtol 1e-8")
 
 
 def mesh_params(tam, pb, **kw):
-    """AMG parameters per workload mesh: the thin bladed discs need a strength threshold."""
-    if pb.name.startswith("disc"):
-        kw = dict(dict(strength_theta=0.02, strength_theta_scale=0.5), **kw)
+    """AMG parameters of a workload mesh (the library defaults: strength threshold 0.02, halved per level)."""
     return tam.amg_params_default(**kw)
 
 
