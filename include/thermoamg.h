@@ -151,7 +151,7 @@ int tam_matrix_destroy(tam_matrix K);
  * for robustness) but not its constants; these are the knobs.
  */
 typedef struct amg_params {
-  double strength_theta;   /* block (i,j) strong if |A_ij|_F >= theta sqrt(|A_ii|_F |A_jj|_F); default 0 */
+  double strength_theta;   /* block (i,j) strong if |A_ij|_F >= theta sqrt(|A_ii|_F |A_jj|_F); default 0.02 */
   int smoother_degree;     /* Chebyshev degree, pre and post; default 2                               */
   double cheb_lo;          /* smoothing interval [cheb_lo, cheb_hi] * lambda_max(D^-1 A); 0.1       */
   double cheb_hi;          /* 1.1                                                                    */
@@ -167,7 +167,7 @@ typedef struct amg_params {
   int use_rotations;       /* 1: six rigid-body modes; 0: three translations only; default 1         */
   int level_precision;     /* V-cycle storage/arithmetic: 0 FP64; 1 FP32; 2 FP32 with BF16 finest-level
                               values.  The outer CG and the coarsest dense solve stay FP64; default 0 */
-  double strength_theta_scale; /* level l uses strength_theta * strength_theta_scale^l; default 1      */
+  double strength_theta_scale; /* level l uses strength_theta * strength_theta_scale^l; default 0.5    */
   int setup_fp64;          /* products of the setup (A P_tent, A P, R (A P)) in plain FP64 arithmetic (1)
                               or in double-float, two FP32 values per operand with error-free transforms,
                               about 2^-47 relative, faster on GB300 (0, default); double-float loses

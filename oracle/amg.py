@@ -319,7 +319,7 @@ class Hierarchy:
     params: dict = field(default_factory=dict)
 
 
-DEFAULTS = dict(theta=0.0, theta_scale=1.0, degree=2, cheb_lo=0.1, cheb_hi=1.1, eig_steps=10,
+DEFAULTS = dict(theta=0.02, theta_scale=0.5, degree=2, cheb_lo=0.1, cheb_hi=1.1, eig_steps=10,
                 coarse_max_dofs=2000, coarse_min_dofs=500, aggressive_levels=1, small_level_dofs=0,
                 small_level_degree=16, max_levels=10, droptol=1e-10)
 

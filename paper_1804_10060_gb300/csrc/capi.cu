@@ -126,7 +126,7 @@ int tam_matrix_destroy(tam_matrix K) {
 int amg_params_default(amg_params* p) {
   return guarded([&] {
     TAM_CHECK(p, TAM_ERR_INVALID_ARG, "amg_params_default: NULL");
-    p->strength_theta = 0.0;
+    p->strength_theta = 0.02;
     p->smoother_degree = 2;
     p->cheb_lo = 0.1;
     p->cheb_hi = 1.1;
@@ -139,7 +139,7 @@ int amg_params_default(amg_params* p) {
     p->max_levels = 10;
     p->use_rotations = 1;
     p->level_precision = 0;
-    p->strength_theta_scale = 1.0;
+    p->strength_theta_scale = 0.5;
     p->setup_fp64 = 0;
     p->spmv_fp64 = 0;
     return TAM_OK;

@@ -3,7 +3,8 @@
 // advances several meshes in one CUDA-graph launch per iteration.
 //
 // Each RHS keeps its own CG scalars and stopping test (a converged RHS is
-// frozen while the others continue).  The outer SpMM with K is FP64; the
+// frozen while the others continue).  The outer SpMM with K has FP64 vectors
+// and double-float products (K's split values); the
 // V-cycle runs in FP32 (BF16 finest values when the hierarchy was built with
 // level_precision 2) with one matrix read serving `tm` right-hand sides per
 // thread -- the V-cycle is bandwidth-bound in FP32, so reading the matrix
@@ -167,9 +168,11 @@ __global__ void mdir_kernel(const double* __restrict__ z, double* __restrict__ p
 }
 
 // -------------------------------------------------------------------------
-// FP64 SpMM with K (SELL-32, thread per row, RHS chunk per blockIdx.y)
+// SpMM with K (SELL-32, thread per row, RHS chunk per blockIdx.y)
 // -------------------------------------------------------------------------
-template <class Epi>
+// DF: double-float products on K's split values (each value feeds tm
+// right-hand sides, so the FP64 version is far past GB300's FP64 rate).
+template <class Epi, bool DF>
 __global__ void __launch_bounds__(SPMV_THREADS)
 kspmm_kernel(SellView A, const double* __restrict__ x, int mp, int tm, Epi epi) {
   __shared__ double sh[32];
@@ -182,6 +185,40 @@ kspmm_kernel(SellView A, const double* __restrict__ x, int mp, int tm, Epi epi) 
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int k = 0; k < TMAX; ++k) acc[r][k] = 0.0;
+  if constexpr (DF) {
+    if (slice < A.n_slices) {
+      float2 ad[3][TMAX];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < TMAX; ++k) ad[r][k] = make_float2(0.f, 0.f);
+      const int k0 = A.slice_ptr[slice], k1 = A.slice_ptr[slice + 1];
+      for (int s = k0; s < k1; ++s) {
+        const int c = __ldg(A.cols + (size_t)s * 32 + lane);
+        const float2* __restrict__ vp = A.vals_df + (size_t)s * 32 * 9 + lane;
+        float2 v[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) v[e] = __ldg(vp + e * 32);
+#pragma unroll
+        for (int jc = 0; jc < 3; ++jc) {
+          const double* xr = x + ((size_t)c * 3 + jc) * mp + j0;
+#pragma unroll
+          for (int k = 0; k < TMAX; ++k)
+            if (k < tm) {
+              const float2 xv = split_bits(__ldg(xr + k));
+#pragma unroll
+              for (int r = 0; r < 3; ++r) df_fma(ad[r][k], v[r * 3 + jc], xv);
+            }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < TMAX; ++k) acc[r][k] = df_to_double(ad[r][k]);
+    }
+    epi(row, j0, tm, acc, sh);
+    return;
+  }
   if (slice < A.n_slices) {
     const int k0 = A.slice_ptr[slice], k1 = A.slice_ptr[slice + 1];
     for (int s = k0; s < k1; ++s) {
@@ -300,7 +337,10 @@ struct EpiStoreKM {
 template <class Epi>
 void kspmm(const Sell& S, const double* x, int mp, int tm, Epi epi, cudaStream_t s) {
   dim3 g(sell_grid(S), mp / tm);
-  kspmm_kernel<Epi><<<g, SPMV_THREADS, 0, s>>>(view(S), x, mp, tm, epi);
+  if (S.vals_df.p)
+    kspmm_kernel<Epi, true><<<g, SPMV_THREADS, 0, s>>>(view(S), x, mp, tm, epi);
+  else
+    kspmm_kernel<Epi, false><<<g, SPMV_THREADS, 0, s>>>(view(S), x, mp, tm, epi);
   TAM_LAUNCH_CHECK();
 }
 

@@ -35,7 +35,7 @@ def _export(tam, H, level, which):
     return bsr_to_csr(e["row_ptr"], e["col_idx"], e["vals"], e["n_cols"]), e
 
 
-@pytest.mark.parametrize("coarse_min,theta", [(0, 0.0), (500, 0.0), (500, 0.05)])
+@pytest.mark.parametrize("coarse_min,theta", [(0, 0.0), (500, 0.0), (500, 0.02), (500, 0.05)])
 @pytest.mark.parametrize("problem", ["cube8", "slab_small", "cube_p2", "disc_p1"])
 def test_hierarchy_matches_oracle_step_by_step(problem, coarse_min, theta):
     pb = {"cube8": lambda: meshgen.unit_cube_problem(8),
@@ -43,7 +43,8 @@ def test_hierarchy_matches_oracle_step_by_step(problem, coarse_min, theta):
           "cube_p2": lambda: meshgen.unit_cube_problem(4, 2),
           "disc_p1": lambda: meshgen.bladed_disc_problem(n_r=6, n_theta_per_blade=4, n_z=2, n_blades=12,
                                                          n_r_blade=3, degree=1)}[problem]()
-    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60, coarse_min_dofs=coarse_min, strength_theta=theta)
+    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60, coarse_min_dofs=coarse_min, strength_theta=theta,
+                               strength_theta_scale=0.5)
     info = tam.amg_info(H)
     assert info["n_levels"] >= 2
     Ko, fo = fem.assemble_system(pb)
@@ -57,7 +58,7 @@ def test_hierarchy_matches_oracle_step_by_step(problem, coarse_min, theta):
         assert abs(info["lambda"][lev] - lam_o) <= 1e-9 * lam_o
         # aggregation: unique under the priority rule -> bit-exact
         agg_g = tam.amg_level_aggregates(H, lev).cpu().numpy()
-        nbrs = oamg.strength_graph(Ag, bs, theta)
+        nbrs = oamg.strength_graph(Ag, bs, theta * 0.5 ** lev)
         agg_o, n_agg = oamg.aggregate_level(nbrs, lev, 6, coarse_min, aggressive_levels=1)
         assert np.array_equal(agg_g, agg_o), f"aggregates level {lev}"
         assert oamg.check_aggregates(agg_g, n_agg, nbrs) == []
