@@ -833,6 +833,7 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
         Level& C = H->levels[lev + 1];
         SpgemmSplit spR;
         spR.y = APs.p;
+        spR.symmetric = true;  // R = P^T and A symmetric
         bsr_spgemm(L.R, AP, C.A_own, s, arith, spR);
         C.A = &C.A_own;
         C.AS = &C.AS_own;

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1)
 spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
                          const typename Ar::V* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
-                         OutT* __restrict__ cv) {
+                         OutT* __restrict__ cv, int upper) {
   using V = typename Ar::V;
   using A = typename Ar::A;
   constexpr int MN = M * N;
@@ -446,7 +446,16 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   if (row >= n_rows) return;
   A* acc = sm + (size_t)wid * (RS_ACC_BYTES / sizeof(A));
   int* wcols = reinterpret_cast<int*>(sm + (size_t)RS_WARPS * (RS_ACC_BYTES / sizeof(A))) + wid * W;
-  const int cs = crp[row], ce = crp[row + 1];
+  int cs = crp[row];
+  const int ce = crp[row + 1];
+  if (upper) {  // symmetric C: only the blocks with column >= row (mirrored afterwards)
+    int lo = cs, hi = ce;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cci[mid] < row) lo = mid + 1; else hi = mid;
+    }
+    cs = lo;
+  }
   const int xs = xrp[row], xe = xrp[row + 1];
   for (int w0 = cs; w0 < ce; w0 += W) {
     const int wn = min(W, ce - w0);
@@ -457,7 +466,7 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
     for (int p = xs; p < xe; ++p) {
       const int j = xci[p];
       int qs = yrp[j], qe = yrp[j + 1];
-      if (wn < ce - cs) {  // restrict Y's row to the window's column range
+      if (upper || wn < ce - cs) {  // restrict Y's row to the window's column range
         int lo = qs, hi = qe;
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
@@ -517,9 +526,37 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   }
 }
 
+// Lower blocks of a symmetric C from their upper partners: C_ic = C_ci^T.
+// A missing partner (a pattern that is not symmetric) is reported, not read.
+template <int M>
+__global__ void mirror_lower_kernel(const int* __restrict__ crp, const int* __restrict__ cci, int n_rows,
+                                    double* __restrict__ cv, int* __restrict__ bad) {
+  const int row = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  for (int p = crp[row] + lane; p < crp[row + 1]; p += 32) {
+    const int c = cci[p];
+    if (c >= row) break;  // sorted: the rest of this lane's entries are upper
+    int lo = crp[c], hi = crp[c + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cci[mid] < row) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= crp[c + 1] || cci[lo] != row) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    const double* __restrict__ src = cv + (size_t)lo * M * M;  // block (c, row)
+    double* __restrict__ dst = cv + (size_t)p * M * M;
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+#pragma unroll
+      for (int k = 0; k < M; ++k) dst[r * M + k] = src[k * M + r];
+  }
+}
+
 template <int M, int K, int N, class Ar, typename OutT>
 void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const typename Ar::V* yv, Bsr& C,
-                    OutT* cv, cudaStream_t s) {
+                    OutT* cv, bool symmetric, cudaStream_t s) {
   if (C.nnzb == 0) return;
   // 3-row blocks (A P_tent, A P on the finest level) keep the output-stationary
   // pass: with only 3 rows per item the row-stationary warp idles (measured
@@ -533,9 +570,21 @@ void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const 
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_set = true;
     }
+    const bool upper = symmetric && M == N && std::is_same<OutT, double>::value;
     spgemm_numeric_rs_kernel<M, K, N, Ar, OutT><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
-        X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv);
+        X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv,
+        upper ? 1 : 0);
     TAM_LAUNCH_CHECK();
+    if constexpr (M == N && std::is_same<OutT, double>::value) {
+      if (upper) {
+        DBuf<int> bad(1, s);
+        bad.zero();
+        mirror_lower_kernel<M><<<grid_for((long long)C.n_rows * 32, 256), 256, 0, s>>>(C.row_ptr.p, C.col_idx.p,
+                                                                                         C.n_rows, cv, bad.p);
+        TAM_LAUNCH_CHECK();
+        TAM_CHECK(read_back_int(bad.p, s) == 0, TAM_ERR_INTERNAL, "spgemm: symmetric product with an unsymmetric pattern");
+      }
+    }
   } else {
     DBuf<int> crow((size_t)C.nnzb, s);
     expand_rows_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.n_rows, crow.p);
@@ -559,7 +608,7 @@ void launch_numeric_any(const Bsr& X, const Bsr& Y, Bsr& C, SpgemmArith arith, c
                         cudaStream_t s) {
   if (arith == SpgemmArith::kFp64) {
     C.vals = DBuf<double>((size_t)C.nnzb * C.block_elems(), s);
-    launch_numeric<M, K, N, ArithF64>(X, X.vals.p, Y, Y.vals.p, C, C.vals.p, s);
+    launch_numeric<M, K, N, ArithF64>(X, X.vals.p, Y, Y.vals.p, C, C.vals.p, sp.symmetric, s);
     return;
   }
   DBuf<float2> xs, ys;
@@ -569,10 +618,10 @@ void launch_numeric_any(const Bsr& X, const Bsr& Y, Bsr& C, SpgemmArith arith, c
   if (!yv) ys = split_values(Y, s), yv = ys.p;
   if (sp.c) {
     *sp.c = DBuf<float2>((size_t)std::max<long long>(1, C.nnzb * (long long)C.block_elems()), s);
-    launch_numeric<M, K, N, ArithDF>(X, xv, Y, yv, C, sp.c->p, s);
+    launch_numeric<M, K, N, ArithDF>(X, xv, Y, yv, C, sp.c->p, false, s);
   } else {
     C.vals = DBuf<double>((size_t)C.nnzb * C.block_elems(), s);
-    launch_numeric<M, K, N, ArithDF>(X, xv, Y, yv, C, C.vals.p, s);
+    launch_numeric<M, K, N, ArithDF>(X, xv, Y, yv, C, C.vals.p, sp.symmetric, s);
   }
 }
 

@@ -134,6 +134,9 @@ struct SpgemmSplit {
   const float2* x = nullptr;
   const float2* y = nullptr;
   DBuf<float2>* c = nullptr;
+  // C known to be symmetric (square blocks, R (A P) with R = P^T): only the
+  // blocks on or above the diagonal are multiplied, the rest mirrored.
+  bool symmetric = false;
 };
 // FP64 values split into (hi, lo) FP32 pairs with integer operations only.
 DBuf<float2> split_values(const Bsr& B, cudaStream_t s);
