@@ -67,7 +67,9 @@ long long tam_kernel_launches(void);
  * (T_h, f_h: nodal interpolants in the same P1/P2 space), scatters them,
  * then eliminates the Dirichlet nodes symmetrically: the load is lifted by
  * -K_{:,D} u_D, rows and columns of Dirichlet nodes are zeroed, their
- * diagonal block becomes I and their load entries u_D.
+ * diagonal block becomes I and their load entries u_D.  A node in no cell
+ * gets an identity row and a zero load (u_D if it is a Dirichlet node);
+ * n_cells = 0 gives K = I.
  *
  *  n_nodes, coords[n_nodes*3]      node coordinates (float64, xyz per node)
  *  n_cells, nodes_per_cell          4 (P1) or 10 (P2; vertices 0-3 then the

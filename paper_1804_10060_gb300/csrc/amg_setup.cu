@@ -220,21 +220,26 @@ __global__ void tridiag_lmax_kernel(const double* __restrict__ ab, const int* __
 // ---------------------------------------------------------------------------
 // Strength graph and aggregation
 // ---------------------------------------------------------------------------
-__global__ void block_norms_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
-                                   int n, int bb, double* __restrict__ nrm, double* __restrict__ dnrm) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double dn = 0.0;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+// Frobenius norm of every block (one thread per block: consecutive threads
+// read consecutive blocks), then each row's diagonal norm.
+__global__ void block_norms_kernel(const double* __restrict__ v, long long nnzb, int bb, double* __restrict__ nrm) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnzb; p += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int e = 0; e < bb; ++e) {
       double x = v[(size_t)p * bb + e];
       s += x * x;
     }
-    s = sqrt(s);
-    nrm[p] = s;
-    if (ci[p] == i) dn = s;
+    nrm[p] = sqrt(s);
   }
+}
+
+__global__ void diag_norms_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ nrm,
+                                  int n, double* __restrict__ dnrm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double dn = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) dn = nrm[p];
   dnrm[i] = dn;
 }
 
@@ -580,8 +585,10 @@ static int aggregate(Level& L, int level, double theta, int distance, cudaStream
   const int n = A.n_rows;
   DBuf<double> nrm((size_t)A.nnzb, s), dnrm(n, s);
   DBuf<unsigned char> strong((size_t)A.nnzb, s), isolated(n, s), state(n, s);
-  block_norms_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, A.vals.p, n, (int)A.block_elems(),
-                                                      nrm.p, dnrm.p);
+  block_norms_kernel<<<std::min<unsigned>(grid_for(A.nnzb, TPB), 152u * 16u), TPB, 0, s>>>(A.vals.p, A.nnzb,
+                                                                                          (int)A.block_elems(), nrm.p);
+  TAM_LAUNCH_CHECK();
+  diag_norms_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, nrm.p, n, dnrm.p);
   TAM_LAUNCH_CHECK();
   strength_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, nrm.p, dnrm.p, n, theta, strong.p,
                                                    isolated.p);

@@ -434,7 +434,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 1)
 spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
                          const typename Ar::V* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
-                         OutT* __restrict__ cv, int upper) {
+                         OutT* __restrict__ cv, int upper, const int* __restrict__ win_row,
+                         const int* __restrict__ win_w0, int n_win) {
   using V = typename Ar::V;
   using A = typename Ar::A;
   constexpr int MN = M * N;
@@ -442,8 +443,9 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   extern __shared__ double sm_d[];
   A* sm = reinterpret_cast<A*>(sm_d);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * RS_WARPS + wid;
-  if (row >= n_rows) return;
+  const int win = blockIdx.x * RS_WARPS + wid;  // one warp per (output row, column window)
+  if (win >= n_win) return;
+  const int row = win_row[win];
   A* acc = sm + (size_t)wid * (RS_ACC_BYTES / sizeof(A));
   int* wcols = reinterpret_cast<int*>(sm + (size_t)RS_WARPS * (RS_ACC_BYTES / sizeof(A))) + wid * W;
   int cs = crp[row];
@@ -457,7 +459,8 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
     cs = lo;
   }
   const int xs = xrp[row], xe = xrp[row + 1];
-  for (int w0 = cs; w0 < ce; w0 += W) {
+  {
+    const int w0 = win_w0[win];
     const int wn = min(W, ce - w0);
     for (int i = lane; i < wn; i += 32) wcols[i] = cci[w0 + i];
     for (int i = lane; i < wn * MN; i += 32) acc[i] = Ar::zero();
@@ -526,6 +529,40 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   }
 }
 
+// Column windows of the output rows (W blocks each; from the diagonal on for
+// a symmetric C): one warp per window, so that a long row -- the few, long rows
+// of a coarse Galerkin product -- is spread over many warps.
+__device__ __forceinline__ int rs_row_start(const int* __restrict__ crp, const int* __restrict__ cci, int row,
+                                            int upper) {
+  int lo = crp[row], hi = crp[row + 1];
+  if (!upper) return lo;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cci[mid] < row) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void rs_window_count_kernel(const int* __restrict__ crp, const int* __restrict__ cci, int n_rows, int upper,
+                                       int W, int* __restrict__ cnt) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_rows) return;
+  const int len = crp[row + 1] - rs_row_start(crp, cci, row, upper);
+  cnt[row] = (len + W - 1) / W;
+}
+
+__global__ void rs_window_list_kernel(const int* __restrict__ wptr, const int* __restrict__ crp,
+                                      const int* __restrict__ cci, int n_rows, int upper, int W,
+                                      int* __restrict__ win_row, int* __restrict__ win_w0) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_rows) return;
+  const int cs = rs_row_start(crp, cci, row, upper);
+  for (int k = 0, w = wptr[row]; w < wptr[row + 1]; ++k, ++w) {
+    win_row[w] = row;
+    win_w0[w] = cs + k * W;
+  }
+}
+
 // Lower blocks of a symmetric C from their upper partners: C_ic = C_ci^T.
 // A missing partner (a pattern that is not symmetric) is reported, not read.
 template <int M>
@@ -571,10 +608,22 @@ void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const 
       attr_set = true;
     }
     const bool upper = symmetric && M == N && std::is_same<OutT, double>::value;
-    spgemm_numeric_rs_kernel<M, K, N, Ar, OutT><<<grid_for(C.n_rows, RS_WARPS), RS_WARPS * 32, smem, s>>>(
-        X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv,
-        upper ? 1 : 0);
+    DBuf<int> wptr((size_t)C.n_rows + 1, s);
+    rs_window_count_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(C.row_ptr.p, C.col_idx.p, C.n_rows, upper ? 1 : 0,
+                                                                    W, wptr.p);
     TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(wptr.p, wptr.p, C.n_rows, s);
+    const int n_win = read_back_int(wptr.p + C.n_rows, s);
+    if (n_win > 0) {
+      DBuf<int> win_row((size_t)n_win, s), win_w0((size_t)n_win, s);
+      rs_window_list_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(wptr.p, C.row_ptr.p, C.col_idx.p, C.n_rows,
+                                                                     upper ? 1 : 0, W, win_row.p, win_w0.p);
+      TAM_LAUNCH_CHECK();
+      spgemm_numeric_rs_kernel<M, K, N, Ar, OutT><<<grid_for(n_win, RS_WARPS), RS_WARPS * 32, smem, s>>>(
+          X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv,
+          upper ? 1 : 0, win_row.p, win_w0.p, n_win);
+      TAM_LAUNCH_CHECK();
+    }
     if constexpr (M == N && std::is_same<OutT, double>::value) {
       if (upper) {
         DBuf<int> bad(1, s);
