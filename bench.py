@@ -632,6 +632,22 @@ def learned_variant(tam, meshgen, stream, world, n_train=16, train_steps=1500, e
         _, used0, energy0 = tam.tam_learned_guess(net, H, F, rhs, bf16=True, smooth_degree=0, stream=stream)
         xs, _, _ = tam.tam_learned_guess(net, H, F, rhs, bf16=True, stream=stream)
     torch.cuda.synchronize()
+    # the guess alone, and the network's inference in its two precisions
+    def t_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    with torch.cuda.stream(stream):
+        guess_ms = t_ms(lambda: tam.tam_learned_guess(net, H, F, rhs, bf16=True, stream=stream))
+        infer_bf16_ms = t_ms(lambda: net.forward(F, bf16=True, stream=stream))
+        infer_fp32_ms = t_ms(lambda: net.forward(F, bf16=False, stream=stream))
     nx0 = float(torch.linalg.norm(x0))
     out = {"workload": LEARNED_WORKLOAD.format(n_train=n_train, n_eval=pb.n_dof), "n_dof": pb.n_dof,
            "value": world * pb.n_dof / (ms1 * 1e-3), "unit": "DOF/s", "ms_per_solve": ms1,
@@ -646,6 +662,9 @@ def learned_variant(tam, meshgen, stream, world, n_train=16, train_steps=1500, e
            "from_zero": {"value": world * pb.n_dof / (ms0 * 1e-3), "unit": "DOF/s", "ms_per_solve": ms0,
                          "iterations": it0, "final_rel_resid": rel0},
            "speedup_vs_zero_start": ms0 / ms1,
+           "guess_ms": guess_ms,
+           "inference_ms": {"bf16_tensor_core_mma": infer_bf16_ms, "fp32_cuda_core": infer_fp32_ms,
+                            "rows": int(F.shape[0])},
            "training": {"solves": n_train, "rows": int(X.shape[0]), "steps": train_steps,
                         "data_ms": 1e3 * (t1 - t0), "train_ms": 1e3 * (t2 - t1),
                         "loss_first": hist[0], "loss_last": hist[-1]}}

@@ -17,6 +17,7 @@
 // activations and the whole layer weight matrix sit in shared memory, and each
 // thread produces 8 consecutive outputs of one row.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "handles.cuh"
@@ -211,6 +212,98 @@ __global__ void to_bf16_kernel(const float* __restrict__ in, __nv_bfloat16* __re
     out[i] = __float2bfloat16(in[i]);
 }
 
+// ---------------------------------------------------------------------------
+// BF16 inference on the tensor cores: out = epi(A W + bias) with BF16 weights
+// and BF16-rounded activations, FP32 accumulation (mma.sync m16n8k16).  A
+// block of 4 warps takes 64 rows; warp w multiplies rows 16w..16w+15 of the
+// tile by all of W.  W is kept transposed (n-major) in shared memory so that
+// the two k-consecutive values of a B fragment are one 32-bit word; the A
+// tile likewise.  K is padded to a multiple of 16 and N to a multiple of 8
+// with zeros (K, N <= 128).
+// ---------------------------------------------------------------------------
+constexpr int MMA_ROWS = 64;
+constexpr int MMA_THREADS = 128;
+constexpr int MMA_KMAX = 128, MMA_NMAX = 128;
+constexpr int MMA_LD = MMA_KMAX + 8;  // row stride in bf16 elements (staggers the banks)
+
+__device__ __forceinline__ void mma_bf16_16x8x16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                                 unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int MODE, bool STD>
+__global__ void __launch_bounds__(MMA_THREADS)
+dense_mma_kernel(const float* __restrict__ A, long long n, int K, int N, const __nv_bfloat16* __restrict__ W,
+                 const float* __restrict__ bias, const float* __restrict__ shift, const float* __restrict__ scale,
+                 const float* __restrict__ out_scale, float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __nv_bfloat16* Wt = reinterpret_cast<__nv_bfloat16*>(sm_raw);  // [Np][MMA_LD]
+  const int Kp = (K + 15) & ~15, Np = (N + 7) & ~7;
+  __nv_bfloat16* At = Wt + (size_t)Np * MMA_LD;                  // [MMA_ROWS][MMA_LD]
+  for (int e = threadIdx.x; e < Np * Kp; e += MMA_THREADS) {
+    const int nn = e / Kp, k = e % Kp;
+    Wt[nn * MMA_LD + k] = (nn < N && k < K) ? W[(size_t)k * N + nn] : __float2bfloat16(0.f);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  for (long long r0 = (long long)blockIdx.x * MMA_ROWS; r0 < n; r0 += (long long)gridDim.x * MMA_ROWS) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < MMA_ROWS * Kp; e += MMA_THREADS) {
+      const int r = e / Kp, k = e % Kp;
+      const long long row = r0 + r;
+      float a = 0.f;
+      if (row < n && k < K) {
+        a = A[row * K + k];
+        if (STD) a = (a - shift[k]) * scale[k];
+      }
+      At[r * MMA_LD + k] = __float2bfloat16(a);
+    }
+    __syncthreads();
+    float acc[MMA_NMAX / 8][4];
+#pragma unroll
+    for (int j = 0; j < MMA_NMAX / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const __nv_bfloat16* Aw = At + (warp * 16) * MMA_LD;
+    for (int k0 = 0; k0 < Kp; k0 += 16) {
+      // A fragment: (g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..), (g+8, 2t+8..)
+      const unsigned a0 = *reinterpret_cast<const unsigned*>(Aw + g * MMA_LD + k0 + 2 * t);
+      const unsigned a1 = *reinterpret_cast<const unsigned*>(Aw + (g + 8) * MMA_LD + k0 + 2 * t);
+      const unsigned a2 = *reinterpret_cast<const unsigned*>(Aw + g * MMA_LD + k0 + 2 * t + 8);
+      const unsigned a3 = *reinterpret_cast<const unsigned*>(Aw + (g + 8) * MMA_LD + k0 + 2 * t + 8);
+#pragma unroll
+      for (int j = 0; j < MMA_NMAX / 8; ++j) {
+        if (j * 8 >= Np) break;
+        // B fragment (column n = 8j + g): k = 2t..2t+1 and 2t+8..2t+9
+        const __nv_bfloat16* wb = Wt + (j * 8 + g) * MMA_LD + k0 + 2 * t;
+        mma_bf16_16x8x16(acc[j], a0, a1, a2, a3, *reinterpret_cast<const unsigned*>(wb),
+                         *reinterpret_cast<const unsigned*>(wb + 8));
+      }
+    }
+    // C fragment: (g, 2t..2t+1) and (g+8, 2t..2t+1) of each 16x8 tile
+#pragma unroll
+    for (int j = 0; j < MMA_NMAX / 8; ++j) {
+      if (j * 8 >= Np) break;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const long long row = r0 + warp * 16 + g + (h >= 2 ? 8 : 0);
+        const int c = j * 8 + 2 * t + (h & 1);
+        if (row >= n || c >= N) continue;
+        float z = acc[j][h] + (bias ? bias[c] : 0.f);
+        if (MODE == 1) z = tanhf(z);
+        else if (MODE == 2) z *= out_scale[c];
+        out[row * N + c] = z;
+      }
+    }
+  }
+}
+
+size_t dense_mma_smem(int N) {
+  return sizeof(__nv_bfloat16) * ((size_t)((N + 7) & ~7) * MMA_LD + (size_t)MMA_ROWS * MMA_LD);
+}
+
 unsigned ew_grid(long long n) { return std::min<unsigned>(grid_for(n, 256), 152u * 8u); }
 unsigned row_grid(long long n) { return std::min<unsigned>((unsigned)((n + ROWS - 1) / ROWS), 152u * 2u); }
 
@@ -219,6 +312,19 @@ size_t dense_smem(int K, int N) { return sizeof(float) * ((size_t)K * N + (size_
 template <typename TW, int MODE, bool TRANS, bool STD>
 void dense(const float* A, long long n, int K, int N, const TW* W, const float* bias, const tam_mlp_s* M,
            const float* aux, float* out, cudaStream_t s) {
+  if constexpr (std::is_same<TW, __nv_bfloat16>::value && !TRANS && (MODE == 1 || MODE == 2)) {
+    // BF16 inference: tensor cores
+    if (K <= MMA_KMAX && N <= MMA_NMAX) {
+      const size_t smem = dense_mma_smem(N);
+      TAM_CUDA(cudaFuncSetAttribute(dense_mma_kernel<MODE, STD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      const unsigned grid = std::min<unsigned>((unsigned)((n + MMA_ROWS - 1) / MMA_ROWS), 152u * 8u);
+      dense_mma_kernel<MODE, STD><<<std::max(1u, grid), MMA_THREADS, smem, s>>>(
+          A, n, K, N, W, bias, M->shift.p, M->scale.p, M->out_scale.p, out);
+      TAM_LAUNCH_CHECK();
+      return;
+    }
+  }
   const size_t smem = dense_smem(K, N);
   TAM_CUDA(cudaFuncSetAttribute(dense_kernel<TW, MODE, TRANS, STD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
