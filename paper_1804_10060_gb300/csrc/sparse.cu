@@ -242,14 +242,16 @@ constexpr int SG_WARPS = 4;
 constexpr int HT = 2048;            // hash slots per warp
 constexpr int HT_MAX = 1536;        // max unique columns per row (load 0.75)
 
-__device__ __forceinline__ bool ht_insert(int* tab, int col) {
-  unsigned h = ((unsigned)col * 2654435761u) & (HT - 1);
+// Open addressing in a table of hsz (a power of two <= HT) slots.
+__device__ __forceinline__ bool ht_insert(int* tab, int col, int hsz) {
+  const unsigned mask = (unsigned)hsz - 1u;
+  unsigned h = ((unsigned)col * 2654435761u) & mask;
   int key = col + 1;
-  for (int probe = 0; probe < HT; ++probe) {
+  for (int probe = 0; probe < hsz; ++probe) {
     int prev = atomicCAS(&tab[h], 0, key);
     if (prev == 0) return true;
     if (prev == key) return false;
-    h = (h + 1) & (HT - 1);
+    h = (h + 1) & mask;
   }
   return false;  // table full: caught by the count check
 }
@@ -265,13 +267,24 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   const int row = blockIdx.x * SG_WARPS + wid;
   if (row >= n_rows) return;
   int* tab = tab_all[wid];
-  for (int i = lane; i < HT; i += 32) tab[i] = 0;
+  const int xs = xrp[row], xe = xrp[row + 1];
+  // table sized for this row: at least twice the sum of the Y row lengths (an
+  // upper bound of the distinct columns), so that short rows -- most of them --
+  // do not clear and scan all HT slots
+  int bound = 0;
+  for (int p = xs + lane; p < xe; p += 32) {
+    const int j = xci[p];
+    bound += yrp[j + 1] - yrp[j];
+  }
+  bound = warp_sum_i(bound);
+  int hsz = 32;
+  while (hsz < 2 * bound && hsz < HT) hsz <<= 1;
+  for (int i = lane; i < hsz; i += 32) tab[i] = 0;
   __syncwarp();
   int ins = 0;
-  const int xs = xrp[row], xe = xrp[row + 1];
   for (int p = xs + lane; p < xe; p += 32) {
     int j = xci[p];
-    for (int q = yrp[j]; q < yrp[j + 1]; ++q) ins += ht_insert(tab, yci[q]) ? 1 : 0;
+    for (int q = yrp[j]; q < yrp[j + 1]; ++q) ins += ht_insert(tab, yci[q], hsz) ? 1 : 0;
   }
   __syncwarp();
   int cnt = warp_sum_i(ins);
@@ -286,7 +299,7 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   }
   // compact non-empty slots (decoded) to the front, pad, sort
   int base = 0;
-  for (int i0 = 0; i0 < HT; i0 += 32) {
+  for (int i0 = 0; i0 < hsz; i0 += 32) {
     int v = tab[i0 + lane];
     bool keep = v != 0;
     unsigned m = __ballot_sync(0xffffffffu, keep);
