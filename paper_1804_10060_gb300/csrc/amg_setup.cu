@@ -197,10 +197,21 @@ __global__ void tridiag_lmax_kernel(const double* __restrict__ ab, const int* __
     }
     return c;
   };
-  for (int it = 0; it < 200 && hi - lo > 1e-15 * fmax(fabs(hi), fabs(lo)); ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (count_below(mid) >= m) hi = mid; else lo = mid;
+  // multisection by one warp: the lanes test 32 interior points of [lo, hi]
+  // (x is above the largest Ritz value iff all m eigenvalues lie below it, a
+  // condition monotone in x), and the interval shrinks 33-fold per round
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < 60 && hi - lo > 1e-15 * fmax(fabs(hi), fabs(lo)); ++it) {
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const unsigned above = __ballot_sync(0xffffffffu, count_below(x) >= m);
+    const int first = above ? __ffs(above) - 1 : 32;  // lowest lane whose point is above
+    const double xl = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
+    const double xh = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
+    const double nlo = first > 0 ? xl : lo, nhi = first < 32 ? xh : hi;
+    lo = nlo;
+    hi = nhi;
   }
+  if (lane != 0) return;
   const double lam = 0.5 * (lo + hi);
   consts[0] = lam;
   consts[1] = 4.0 / (3.0 * lam);
@@ -573,7 +584,7 @@ static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s) {
   }
   const int deg = std::max(L.deg, 1);
   L.consts = DBuf<double>(2 + 2 * (size_t)deg, s);
-  tridiag_lmax_kernel<<<1, 1, 0, s>>>(ab.p, mdone.p, k, H->prm.cheb_lo, H->prm.cheb_hi, deg, L.consts.p);
+  tridiag_lmax_kernel<<<1, 32, 0, s>>>(ab.p, mdone.p, k, H->prm.cheb_lo, H->prm.cheb_hi, deg, L.consts.p);
   TAM_LAUNCH_CHECK();
   L.lambda_host = read_back_double(L.consts.p, s);
   TAM_CHECK(std::isfinite(L.lambda_host) && L.lambda_host > 0.0, TAM_ERR_INTERNAL,

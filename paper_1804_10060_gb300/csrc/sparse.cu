@@ -439,8 +439,8 @@ __device__ __forceinline__ void load_block(const V* __restrict__ p, V (&out)[CNT
   }
 }
 
-constexpr int RS_WARPS = 4;
-constexpr int RS_ACC_BYTES = 16384;
+constexpr int RS_WARPS = 8;
+constexpr int RS_ACC_BYTES = 8192;
 
 template <int M, int K, int N, class Ar, typename OutT>
 __global__ void __launch_bounds__(RS_WARPS * 32, 1)
