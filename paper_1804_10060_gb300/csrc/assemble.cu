@@ -68,7 +68,7 @@ pattern_kernel(int n_nodes, int npc, const int* __restrict__ cells, const int* _
   if (n_cand > PAT_CAP) {
     if (lane == 0) {
       atomicExch(overflow, 1);
-      if (!FILL) row_cnt[i] = 1;
+      if (row_cnt) row_cnt[i] = FILL ? 0 : 1;
     }
     return;
   }
@@ -91,7 +91,25 @@ pattern_kernel(int n_nodes, int npc, const int* __restrict__ cells, const int* _
   } else {
     const int r0 = row_ptr[i];
     for (int t = lane; t < cnt; t += 32) col_idx[r0 + t] = buf[t];
+    if (lane == 0 && row_cnt) row_cnt[i] = cnt;
   }
+}
+
+// Candidate count of each row (upper bound of its pattern length): self plus
+// the nodes of its incident cells; 1 for a Dirichlet row.
+__global__ void pattern_bound_kernel(int n_nodes, int npc, const int* __restrict__ inc_ptr,
+                                     const unsigned char* __restrict__ dmask, int* __restrict__ bound) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_nodes) bound[i] = dmask[i] ? 1 : 1 + (inc_ptr[i + 1] - inc_ptr[i]) * npc;
+}
+
+// Rows written at their bound offsets in tmp, packed into col_idx (warp per row).
+__global__ void pattern_pack_kernel(int n_nodes, const int* __restrict__ bptr, const int* __restrict__ tmp,
+                                    const int* __restrict__ row_ptr, int* __restrict__ col_idx) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= n_nodes) return;
+  const int src = bptr[i], dst = row_ptr[i], cnt = row_ptr[i + 1] - dst;
+  for (int t = lane; t < cnt; t += 32) col_idx[dst + t] = tmp[src + t];
 }
 
 __device__ __forceinline__ void lame(double E, double nu, double& lam, double& mu) {
@@ -395,17 +413,42 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
     A.br = A.bc = 3;
     A.row_ptr = DBuf<int>((size_t)n_nodes + 1, s);
     unsigned pg = grid_for(n_nodes, PAT_WARPS);
-    pattern_kernel<false><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
-                                                       nullptr, nullptr, flag.p + 1);
-    TAM_LAUNCH_CHECK();
-    exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
-    A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
-    TAM_CHECK(read_back_int(flag.p + 1, s) == 0, TAM_ERR_UNSUPPORTED,
-              "fem_assemble: a node has too many incident cells for the pattern builder");
-    A.col_idx = DBuf<int>((size_t)A.nnzb, s);
-    pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, nullptr,
-                                                      A.row_ptr.p, A.col_idx.p, flag.p + 1);
-    TAM_LAUNCH_CHECK();
+    if ((long long)n_nodes + (long long)npc * npc * n_cells < (1LL << 31)) {
+      // one sort pass: each row's sorted unique columns go to its candidate-
+      // bound offset in a scratch array (the bounds' sum, at most
+      // n_nodes + npc^2 n_cells, fits the int32 scan), the counts give
+      // row_ptr, then pack
+      DBuf<int> bptr((size_t)n_nodes + 1, s);
+      pattern_bound_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, npc, inc_ptr.p, dmask, bptr.p);
+      TAM_LAUNCH_CHECK();
+      exclusive_scan_i32(bptr.p, bptr.p, n_nodes, s);
+      const long long total = read_back_int(bptr.p + n_nodes, s);
+      DBuf<int> tmp((size_t)std::max(1LL, total), s);
+      pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
+                                                        bptr.p, tmp.p, flag.p + 1);
+      TAM_LAUNCH_CHECK();
+      exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
+      A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
+      TAM_CHECK(read_back_int(flag.p + 1, s) == 0, TAM_ERR_UNSUPPORTED,
+                "fem_assemble: a node has too many incident cells for the pattern builder");
+      A.col_idx = DBuf<int>((size_t)std::max(1LL, A.nnzb), s);
+      pattern_pack_kernel<<<grid_for((long long)n_nodes * 32, 256), 256, 0, s>>>(n_nodes, bptr.p, tmp.p,
+                                                                                 A.row_ptr.p, A.col_idx.p);
+      TAM_LAUNCH_CHECK();
+    } else {
+      // very large meshes: count pass, then fill pass (no scratch)
+      pattern_kernel<false><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
+                                                         nullptr, nullptr, flag.p + 1);
+      TAM_LAUNCH_CHECK();
+      exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
+      A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
+      TAM_CHECK(read_back_int(flag.p + 1, s) == 0, TAM_ERR_UNSUPPORTED,
+                "fem_assemble: a node has too many incident cells for the pattern builder");
+      A.col_idx = DBuf<int>((size_t)A.nnzb, s);
+      pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, nullptr,
+                                                        A.row_ptr.p, A.col_idx.p, flag.p + 1);
+      TAM_LAUNCH_CHECK();
+    }
     // numeric
     A.vals = DBuf<double>((size_t)A.nnzb * 9, s);
     A.vals.zero();
