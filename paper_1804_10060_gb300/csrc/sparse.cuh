@@ -394,7 +394,10 @@ inline int choose_lpr(const Bsr& A) {
   const double avg = A.n_rows > 0 ? (double)A.nnzb / A.n_rows : 0.0;
   if (A.n_rows >= 65536 && avg <= 48.0) return 0;
   int l = 2;
-  while (l < 32 && 16 * l < avg) l <<= 1;
+  // few rows (coarse levels): at least 8 blocks per lane is enough to hide
+  // the reduction; the extra lanes are what keeps the SMs busy there
+  const int per_lane = A.n_rows < 65536 ? 8 : 16;
+  while (l < 32 && per_lane * l < avg) l <<= 1;
   if (A.n_rows < 8192) l = std::max(l, 16);  // few rows: spread them over more lanes
   return l;
 }
