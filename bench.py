@@ -207,11 +207,14 @@ def cpu_baseline_obj(res, dims=SAMPLE_DIMS):
 # distributed plumbing (replicas only)
 # ---------------------------------------------------------------------------
 def dist_setup(n_gpus):
+    """(rank, world, local rank) from the launcher's environment; one process group
+    for the barrier and the max-over-ranks timing (NCCL on GPUs, gloo without)."""
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, world, local
 
 
@@ -222,13 +225,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The slowest rank's time (a step ends when every replica has finished)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(units_per_rank, ms_max, world):
+    """Whole-job throughput: every rank's units over the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / (ms_max * 1e-3)
 
 
 # ---------------------------------------------------------------------------
@@ -299,7 +309,7 @@ def native_arm(args):
     launches = tam.kernel_launches() - launches0
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world)
-    value = world * pb.n_dof / (ms * 1e-3)
+    value = job_value(pb.n_dof, ms, world)
 
     # per-phase times of one more step (events around each call)
     phases = {}
@@ -371,7 +381,7 @@ def native_arm(args):
                                       stream=stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, world)
-    e2e_val = world * pb.n_dof / (e2e_ms * 1e-3)
+    e2e_val = job_value(pb.n_dof, e2e_ms, world)
 
     # reduced-precision V-cycle variants (FP64 CG, FP64 coarse solve), same workload and accuracy target
     variants = {}
