@@ -118,7 +118,7 @@ int tam_matrix_spmv(tam_matrix K, const double* x, double* y, void* stream);
 
 /* ||b - K x||_2 into *norm_host (host double): the true residual of a
  * candidate displacement, the quantity the CG stopping test of Sec. 2.1 is
- * judged by.  b, x: [3n] float64 device vectors.  One fused SpMV + grid
+ * measured by.  b, x: [3n] float64 device vectors.  One fused SpMV + grid
  * reduction; its per-block partial sums live in scratch memory the call
  * allocates stream-ordered and frees again.  Synchronising.
  * Errors: INVALID_ARG, OOM, CUDA. */

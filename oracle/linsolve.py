@@ -3,7 +3,7 @@
 The method's result is the exact solution of the assembled system; CG and
 AMG (paper Sec. 2.1, "Iterative solvers" and "Multigrid preconditioned
 iterative solvers") only reach it faster.  These routines reach it by other
-means so that the GPU solve can be judged:
+means so that the GPU solve can be checked against them:
 
 * ``dense_solve``   -- dense Cholesky (NumPy/LAPACK), tiny systems only.
 * ``direct_solve``  -- sparse LU (SciPy SuperLU), small systems.
