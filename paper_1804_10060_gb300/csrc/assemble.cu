@@ -267,9 +267,10 @@ constexpr int P2_WARPS = 4;
 // P2: one warp per cell.  Lane 0 computes the geometry; the 4x10 gradient
 // table goes to shared memory; lanes then take the 100 (a,b) blocks.
 __global__ void __launch_bounds__(P2_WARPS * 32) assemble_p2_kernel(AsmArgs A) {
-  __shared__ double sg[P2_WARPS][4][10][3];
+  __shared__ double sg[P2_WARPS][4][10][3];  // basis gradients at the 4 stiffness points
   __shared__ double sgeo[P2_WARPS][4][3];
   __shared__ double svol[P2_WARPS];
+  __shared__ double sq[P2_WARPS][11][4];     // per load point: T_h - T_ref, f_h
   __shared__ int sv[P2_WARPS][10];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * P2_WARPS + wid;
@@ -300,54 +301,80 @@ __global__ void __launch_bounds__(P2_WARPS * 32) assemble_p2_kernel(AsmArgs A) {
     p2_grad(a, c_q4[q], g, gr);
     for (int d = 0; d < 3; ++d) sg[wid][q][a][d] = gr[d];
   }
-  __syncwarp();
   const int m = A.mat[c];
   double lam, mu;
   lame(A.props[3 * m], A.props[3 * m + 1], lam, mu);
   const double alpha = A.props[3 * m + 2];
-  const double w = 0.25 * vol;
-  for (int p = lane; p < 100; p += 32) {
-    const int a = p / 10, b = p % 10;
-    const int na = sv[wid][a];
-    if (A.dmask[na] || !block_needed(A, sv[wid][b])) continue;
+  // load values at the 11 load points, one lane each
+  const bool loads = A.T || A.body;
+  if (loads && lane < 11) {
+    const double* l = c_k11[lane];
+    double Th = 0.0, fh[3] = {0, 0, 0};
+    for (int ci = 0; ci < 10; ++ci) {
+      const double ph = p2_phi(ci, l);
+      const int nc = sv[wid][ci];
+      if (A.T) Th += ph * A.T[nc];
+      if (A.body)
+        for (int d = 0; d < 3; ++d) fh[d] += ph * A.body[3 * (size_t)nc + d];
+    }
+    sq[wid][lane][0] = A.T ? Th - A.T_ref : 0.0;
+    for (int d = 0; d < 3; ++d) sq[wid][lane][1 + d] = fh[d];
+  }
+  __syncwarp();
+  // stiffness, 4-point rule: K_ab = sum_q w (lam g_a g_b^T + mu g_b g_a^T + mu (g_a . g_b) I)
+  // for the 55 pairs a <= b, with the gradients pre-scaled by w lam and w mu;
+  // K_ba = K_ab^T is scattered for b > a (FP64 is GB300's scarce pipe)
+  const double wl = 0.25 * vol * lam, wm = 0.25 * vol * mu;
+  for (int pidx = lane; pidx < 55; pidx += 32) {
+    int a = 0, r = pidx;
+    while (r >= 10 - a) {
+      r -= 10 - a;
+      ++a;
+    }
+    const int b = a + r;
+    const int na = sv[wid][a], nb = sv[wid][b];
+    const bool ab = !A.dmask[na] && block_needed(A, nb);
+    const bool ba = b != a && !A.dmask[nb] && block_needed(A, na);
+    if (!ab && !ba) continue;
     double k[9];
+#pragma unroll
     for (int e = 0; e < 9; ++e) k[e] = 0.0;
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
       const double* ga = sg[wid][q][a];
       const double* gb = sg[wid][q][b];
-      double gg = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-          k[3 * i + j] += w * (lam * ga[i] * gb[j] + mu * ga[j] * gb[i] + (i == j ? mu * gg : 0.0));
+      const double gb0 = gb[0], gb1 = gb[1], gb2 = gb[2];
+      const double lga[3] = {wl * ga[0], wl * ga[1], wl * ga[2]};
+      const double mga[3] = {wm * ga[0], wm * ga[1], wm * ga[2]};
+      const double gbv[3] = {gb0, gb1, gb2};
+      const double mgg = mga[0] * gb0 + mga[1] * gb1 + mga[2] * gb2;
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj)
+          k[3 * ii + jj] += fma(lga[ii], gbv[jj], mga[jj] * gbv[ii]) + (ii == jj ? mgg : 0.0);
     }
-    scatter_block(A, na, sv[wid][b], k);
+    if (ab) scatter_block(A, na, nb, k);
+    if (ba) {
+      const double kt[9] = {k[0], k[3], k[6], k[1], k[4], k[7], k[2], k[5], k[8]};
+      scatter_block(A, nb, na, kt);
+    }
   }
-  // loads: lane a < 10 integrates its node's thermal and body terms
-  if (lane < 10) {
-    const int a = lane, na = sv[wid][a];
+  // loads, Keast 11-point rule: lane 3a + d sums component d of node a over the points
+  if (loads && lane < 30) {
+    const int a = lane / 3, d = lane % 3, na = sv[wid][a];
     if (!A.dmask[na]) {
       const double kT = (3.0 * lam + 2.0 * mu) * alpha;
-      double f[3] = {0, 0, 0};
+      double f = 0.0;
       for (int q = 0; q < 11; ++q) {
         const double* l = c_k11[q];
         const double wq = l[4] * vol;
-        double Th = 0.0, fh[3] = {0, 0, 0};
-        for (int cidx = 0; cidx < 10; ++cidx) {
-          double ph = p2_phi(cidx, l);
-          int nc = sv[wid][cidx];
-          if (A.T) Th += ph * A.T[nc];
-          if (A.body)
-            for (int d = 0; d < 3; ++d) fh[d] += ph * A.body[3 * (size_t)nc + d];
-        }
         double gr[3];
         p2_grad(a, l, g, gr);
-        double pa = p2_phi(a, l);
-        for (int d = 0; d < 3; ++d) {
-          if (A.T) f[d] += wq * kT * (Th - A.T_ref) * gr[d];
-          if (A.body) f[d] += wq * pa * fh[d];
-        }
+        if (A.T) f += wq * kT * sq[wid][q][0] * gr[d];
+        if (A.body) f += wq * p2_phi(a, l) * sq[wid][q][1 + d];
       }
-      for (int d = 0; d < 3; ++d) atomicAdd(&A.rhs[3 * (size_t)na + d], f[d]);
+      atomicAdd(&A.rhs[3 * (size_t)na + d], f);
     }
   }
 }
