@@ -177,8 +177,9 @@ __global__ void __launch_bounds__(SPMV_THREADS)
 kspmm_kernel(SellView A, const double* __restrict__ x, int mp, int tm, Epi epi) {
   __shared__ double sh[32];
   if (epi.skip()) return;
-  const int row = blockIdx.x * SPMV_THREADS + threadIdx.x;
-  const int slice = row >> 5, lane = row & 31;
+  const int pos = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int slice = pos >> 5, lane = pos & 31;
+  const int row = sell_row(A.perm, pos, A.n_rows);
   const int j0 = blockIdx.y * tm;
   double acc[3][TMAX];
 #pragma unroll
@@ -350,10 +351,11 @@ void kspmm(const Sell& S, const double* x, int mp, int tm, Epi epi, cudaStream_t
 template <int BR, int BC, typename TV, class Epi>
 __global__ void __launch_bounds__(SPMV_THREADS)
 msell_kernel(int n_slices, const int* __restrict__ slice_ptr, const int* __restrict__ cols, const TV* __restrict__ vals,
-             const float* __restrict__ x, int mp, int tm, Epi epi) {
+             const float* __restrict__ x, int mp, int tm, const int* __restrict__ perm, Epi epi) {
   if (epi.skip()) return;
-  const int row = blockIdx.x * SPMV_THREADS + threadIdx.x;
-  const int slice = row >> 5, lane = row & 31;
+  const int pos = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int slice = pos >> 5, lane = pos & 31;
+  const int row = sell_row(perm, pos, epi.n_rows);
   const int j0 = blockIdx.y * tm;
   float acc[BR][TMAX];
 #pragma unroll
@@ -497,7 +499,7 @@ void mspmm(const SpOpLow<TV>& o, const float* x, int mp, int tm, Epi epi, cudaSt
   if (op.lpr == 0) {
     const Sell& S = *op.S;
     dim3 g(sell_grid(S), mp / tm);
-    msell_kernel<BR, BC, TV, Epi><<<g, SPMV_THREADS, 0, s>>>(S.n_slices, S.slice_ptr.p, S.cols.p, o.vals, x, mp, tm,
+    msell_kernel<BR, BC, TV, Epi><<<g, SPMV_THREADS, 0, s>>>(S.n_slices, S.slice_ptr.p, S.cols.p, o.vals, x, mp, tm, S.perm.p,
                                                               epi);
   } else {
     const Bsr& B = *op.B;

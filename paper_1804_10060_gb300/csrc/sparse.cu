@@ -14,25 +14,47 @@ namespace tam {
 namespace {
 
 __global__ void sell_slice_len_kernel(const int* __restrict__ row_ptr, int n_rows, int n_slices,
-                                      int* __restrict__ len) {
+                                      const int* __restrict__ perm, int* __restrict__ len) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_slices) return;
   int m = 0;
-  int r1 = min(32 * s + 32, n_rows);
-  for (int r = 32 * s; r < r1; ++r) m = max(m, row_ptr[r + 1] - row_ptr[r]);
+  int p1 = min(32 * s + 32, n_rows);
+  for (int p = 32 * s; p < p1; ++p) {
+    const int r = perm ? perm[p] : p;
+    m = max(m, row_ptr[r + 1] - row_ptr[r]);
+  }
   len[s] = m;
+}
+
+// Row order for SELL-C-sigma: within each window of 256 positions, rows by
+// decreasing length (ties by row index, so the order is deterministic).  One
+// block of 256 threads per window; each thread ranks its row by counting.
+__global__ void __launch_bounds__(256) sell_sort_window_kernel(const int* __restrict__ row_ptr, int n_rows,
+                                                               int* __restrict__ perm) {
+  __shared__ int slen[256];
+  const int base = blockIdx.x * 256, t = threadIdx.x, r = base + t;
+  const int len = r < n_rows ? row_ptr[r + 1] - row_ptr[r] : -1;
+  slen[t] = len;
+  __syncthreads();
+  if (r >= n_rows) return;
+  int rank = 0;
+  for (int j = 0; j < 256; ++j) {
+    const int lj = slen[j];
+    rank += (lj > len) || (lj == len && j < t);
+  }
+  perm[base + rank] = r;
 }
 
 // One thread per (slice, lane).  Pads a row with zero blocks pointing at the
 // row's last real column (keeps the padded x reads local).
 __global__ void sell_fill_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
                                  const double* __restrict__ vals, int n_rows, int n_slices, int bb,
-                                 const int* __restrict__ slice_ptr, int* __restrict__ scols,
-                                 double* __restrict__ svals, bool with_pattern) {
+                                 const int* __restrict__ slice_ptr, const int* __restrict__ perm,
+                                 int* __restrict__ scols, double* __restrict__ svals, bool with_pattern) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int s = t >> 5, lane = t & 31;
   if (s >= n_slices) return;
-  int row = t;
+  int row = (perm && t < n_rows) ? perm[t] : t;
   int rp = 0, len = 0;
   if (row < n_rows) {
     rp = row_ptr[row];
@@ -57,23 +79,34 @@ void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s) {
   S.bc = A.bc;
   S.n_slices = (A.n_rows + 31) / 32;
   S.slice_ptr = DBuf<int>((size_t)S.n_slices + 1, s);
-  sell_slice_len_kernel<<<grid_for(S.n_slices, 256), 256, 0, s>>>(A.row_ptr.p, A.n_rows, S.n_slices,
+  sell_slice_len_kernel<<<grid_for(S.n_slices, 256), 256, 0, s>>>(A.row_ptr.p, A.n_rows, S.n_slices, nullptr,
                                                                   S.slice_ptr.p);
   TAM_LAUNCH_CHECK();
   exclusive_scan_i32(S.slice_ptr.p, S.slice_ptr.p, S.n_slices, s);
   S.n_slots = read_back_int(S.slice_ptr.p + S.n_slices, s);
+  if ((double)S.n_slots * 32.0 > 1.10 * (double)A.nnzb) {
+    // more than 10% padding in row order: sort rows by length within windows
+    S.perm = DBuf<int>((size_t)A.n_rows, s);
+    sell_sort_window_kernel<<<(A.n_rows + 255) / 256, 256, 0, s>>>(A.row_ptr.p, A.n_rows, S.perm.p);
+    TAM_LAUNCH_CHECK();
+    sell_slice_len_kernel<<<grid_for(S.n_slices, 256), 256, 0, s>>>(A.row_ptr.p, A.n_rows, S.n_slices, S.perm.p,
+                                                                    S.slice_ptr.p);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(S.slice_ptr.p, S.slice_ptr.p, S.n_slices, s);
+    S.n_slots = read_back_int(S.slice_ptr.p + S.n_slices, s);
+  }
   S.cols = DBuf<int>((size_t)S.n_slots * 32, s);
   S.vals = DBuf<double>((size_t)S.n_slots * 32 * A.block_elems(), s);
   sell_fill_kernel<<<grid_for((long long)S.n_slices * 32, 256), 256, 0, s>>>(
       A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, S.n_slices, (int)A.block_elems(),
-      S.slice_ptr.p, S.cols.p, S.vals.p, true);
+      S.slice_ptr.p, S.perm.p, S.cols.p, S.vals.p, true);
   TAM_LAUNCH_CHECK();
 }
 
 void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s) {
   sell_fill_kernel<<<grid_for((long long)S.n_slices * 32, 256), 256, 0, s>>>(
       A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, S.n_slices, (int)A.block_elems(),
-      S.slice_ptr.p, S.cols.p, S.vals.p, false);
+      S.slice_ptr.p, S.perm.p, S.cols.p, S.vals.p, false);
   TAM_LAUNCH_CHECK();
   if (S.vals_df.p) build_df_values(S, s);
 }

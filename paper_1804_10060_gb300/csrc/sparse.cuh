@@ -94,6 +94,11 @@ struct Sell {
   DBuf<int> cols;         // [n_slots * 32]
   DBuf<double> vals;      // [n_slots * 32 * br * bc]
   DBuf<float2> vals_df;   // optional split copy of vals
+  // optional row order (SELL-C-sigma): slot position p holds row perm[p]; rows
+  // are sorted by length within windows of 256 so that a slice's rows have
+  // similar lengths (P2 meshes interleave long vertex rows with short edge
+  // rows: 40% padding unsorted, 8% sorted).  Empty: position p holds row p.
+  DBuf<int> perm;
 };
 
 struct SellView {
@@ -102,10 +107,16 @@ struct SellView {
   const int* __restrict__ cols;
   const double* __restrict__ vals;
   const float2* __restrict__ vals_df;
+  const int* __restrict__ perm;
 };
 
 inline SellView view(const Sell& s) {
-  return SellView{s.n_rows, s.n_slices, s.slice_ptr.p, s.cols.p, s.vals.p, s.vals_df.p};
+  return SellView{s.n_rows, s.n_slices, s.slice_ptr.p, s.cols.p, s.vals.p, s.vals_df.p, s.perm.p};
+}
+
+// Row held by slot position pos (positions past the last row stay out of range).
+__device__ __forceinline__ int sell_row(const int* __restrict__ perm, int pos, int n_rows) {
+  return (perm && pos < n_rows) ? __ldg(perm + pos) : pos;
 }
 
 // (Re)builds the split copy vals_df from vals (integer operations only).
@@ -158,8 +169,8 @@ __global__ void __launch_bounds__(SPMV_THREADS)
 sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
   __shared__ double sh[32];
   if (epi.skip()) return;
-  const int row = blockIdx.x * SPMV_THREADS + threadIdx.x;
-  const int slice = row >> 5, lane = row & 31;
+  const int pos = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int slice = pos >> 5, lane = pos & 31;
   double acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = 0.0;
@@ -203,7 +214,7 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
       }
     }
   }
-  epi(row, acc, sh);
+  epi(sell_row(A.perm, pos, A.n_rows), acc, sh);
 }
 
 // df: use the split copy when the matrix has one (false: plain FP64).
@@ -465,11 +476,12 @@ __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162flo
 template <int BR, int BC, typename TV, class Epi>
 __global__ void __launch_bounds__(SPMV_THREADS)
 sell_spmv_f32_kernel(int n_slices, const int* __restrict__ slice_ptr, const int* __restrict__ cols,
-                     const TV* __restrict__ vals, const float* __restrict__ x, Epi epi) {
+                     const TV* __restrict__ vals, const float* __restrict__ x, const int* __restrict__ perm,
+                     int n_rows, Epi epi) {
   __shared__ double sh[32];
   if (epi.skip()) return;
-  const int row = blockIdx.x * SPMV_THREADS + threadIdx.x;
-  const int slice = row >> 5, lane = row & 31;
+  const int pos = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int slice = pos >> 5, lane = pos & 31;
   float acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = 0.f;
@@ -491,7 +503,7 @@ sell_spmv_f32_kernel(int n_slices, const int* __restrict__ slice_ptr, const int*
       vp += 32 * BR * BC;
     }
   }
-  epi(row, acc, sh);
+  epi(sell_row(perm, pos, n_rows), acc, sh);
 }
 
 template <int BR, int BC, int LPR, typename TV, class Epi>
@@ -540,7 +552,7 @@ void spop_apply_f32(const SpOpLow<TV>& o, const float* x, Epi epi, cudaStream_t 
   if (o.op.lpr == 0) {
     const Sell& S = *o.op.S;
     sell_spmv_f32_kernel<BR, BC, TV, Epi><<<g, SPMV_THREADS, 0, s>>>(S.n_slices, S.slice_ptr.p, S.cols.p, o.vals, x,
-                                                                     epi);
+                                                                     S.perm.p, S.n_rows, epi);
   } else {
     const Bsr& B = *o.op.B;
     switch (o.op.lpr) {
