@@ -266,8 +266,10 @@ void bsr_transpose(const Bsr& A, Bsr& R, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // SpGEMM C = X Y.  Symbolic: one warp per row inserts the candidate columns
 // into a shared-memory hash set (open addressing), counts, and in the fill
-// pass compacts and bitonic-sorts them.  Numeric: one thread per output block
-// (see spgemm_numeric_os_kernel).
+// pass compacts and bitonic-sorts them; narrow outputs use a column bitmap.
+// Numeric: one thread per output block for 3-row blocks
+// (spgemm_numeric_os_kernel), a warp per output row window otherwise
+// (spgemm_numeric_rs_kernel).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -292,7 +294,7 @@ __device__ __forceinline__ bool ht_insert(int* tab, int col, int hsz) {
 template <bool FILL>
 __global__ void __launch_bounds__(SG_WARPS * 32)
 spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, int n_rows,
-                       const int* __restrict__ yrp, const int* __restrict__ yci,
+                       const int* __restrict__ yrp, const int* __restrict__ yci, int n_cols,
                        int* __restrict__ row_cnt, const int* __restrict__ crp, int* __restrict__ cci,
                        int* __restrict__ overflow) {
   __shared__ int tab_all[SG_WARPS][HT];
@@ -312,6 +314,59 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   bound = warp_sum_i(bound);
   int hsz = 32;
   while (hsz < 2 * bound && hsz < HT) hsz <<= 1;
+  // Narrow outputs (the coarse levels: few columns, long rows): a bitmap of
+  // the n_cols columns instead of the hash set when it has no more words than
+  // the table has slots -- no probing, no column limit, and the set bits come
+  // out already sorted.
+  const int words = (n_cols + 31) >> 5;
+  if (words <= hsz) {
+    for (int i = lane; i < words; i += 32) tab[i] = 0;
+    __syncwarp();
+    if (bound >= 16 * (xe - xs)) {  // long Y rows: lanes over a row's entries (coalesced)
+      for (int p = xs; p < xe; ++p) {
+        const int j = xci[p];
+        for (int q = yrp[j] + lane; q < yrp[j + 1]; q += 32) {
+          const int c = yci[q];
+          atomicOr(reinterpret_cast<unsigned*>(tab) + (c >> 5), 1u << (c & 31));
+        }
+      }
+    } else {
+      for (int p = xs + lane; p < xe; p += 32) {
+        const int j = xci[p];
+        for (int q = yrp[j]; q < yrp[j + 1]; ++q) {
+          const int c = yci[q];
+          atomicOr(reinterpret_cast<unsigned*>(tab) + (c >> 5), 1u << (c & 31));
+        }
+      }
+    }
+    __syncwarp();
+    if (!FILL) {
+      int cnt = 0;
+      for (int i = lane; i < words; i += 32) cnt += __popc((unsigned)tab[i]);
+      cnt = warp_sum_i(cnt);
+      if (lane == 0) row_cnt[row] = cnt;
+      return;
+    }
+    int base = crp[row];
+    for (int i0 = 0; i0 < words; i0 += 32) {
+      unsigned w = i0 + lane < words ? (unsigned)tab[i0 + lane] : 0u;
+      const int c = __popc(w);
+      int off = c;  // inclusive scan of the lanes' counts
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, off, d);
+        if (lane >= d) off += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, off, 31);
+      off = base + off - c;
+      while (w) {
+        cci[off++] = ((i0 + lane) << 5) + (__ffs(w) - 1);
+        w &= w - 1u;
+      }
+      base += total;
+    }
+    return;
+  }
   for (int i = lane; i < hsz; i += 32) tab[i] = 0;
   __syncwarp();
   int ins = 0;
@@ -378,6 +433,7 @@ struct ArithF64 {
   using A = double;
   __device__ static A zero() { return 0.0; }
   __device__ static void fma(A& a, V x, V y) { a = ::fma(x, y, a); }
+  __device__ static void add(A& a, A b) { a += b; }
   __device__ static void store(double* p, A a) { *p = a; }
 };
 
@@ -386,6 +442,7 @@ struct ArithDF {
   using A = float2;
   __device__ static A zero() { return make_float2(0.f, 0.f); }
   __device__ static void fma(A& a, V x, V y) { df_fma(a, x, y); }
+  __device__ static void add(A& a, A b) { df_fma(a, b, make_float2(1.f, 0.f)); }  // b * 1 is exact
   __device__ static void store(double* p, A a) { *p = f2d_bits(a.x) + f2d_bits(a.y); }
   // kept split for a following double-float product: renormalised (Fast2Sum)
   __device__ static void store(float2* p, A a) {
@@ -481,7 +538,7 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
                          const typename Ar::V* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
                          OutT* __restrict__ cv, int upper, const int* __restrict__ win_row,
-                         const int* __restrict__ win_w0, int n_win) {
+                         const int* __restrict__ win_w0, int n_win, int split) {
   using V = typename Ar::V;
   using A = typename Ar::A;
   constexpr int MN = M * N;
@@ -489,7 +546,11 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
   extern __shared__ double sm_d[];
   A* sm = reinterpret_cast<A*>(sm_d);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int win = blockIdx.x * RS_WARPS + wid;  // one warp per (output row, column window)
+  // one warp per (output row, column window); with split, one block per
+  // window, its warps taking every RS_WARPS-th X entry of the row (block-uniform
+  // exit: the partial windows are summed after a __syncthreads)
+  const int win = split ? (int)blockIdx.x : (int)blockIdx.x * RS_WARPS + wid;
+  const int p0 = split ? wid : 0, pstep = split ? RS_WARPS : 1;
   if (win >= n_win) return;
   const int row = win_row[win];
   A* acc = sm + (size_t)wid * (RS_ACC_BYTES / sizeof(A));
@@ -512,7 +573,7 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
     for (int i = lane; i < wn * MN; i += 32) acc[i] = Ar::zero();
     __syncwarp();
     const int clo = wcols[0], chi = wcols[wn - 1];
-    for (int p = xs; p < xe; ++p) {
+    for (int p = xs + p0; p < xe; p += pstep) {
       const int j = xci[p];
       int qs = yrp[j], qe = yrp[j + 1];
       if (upper || wn < ce - cs) {  // restrict Y's row to the window's column range
@@ -570,8 +631,18 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
       }
       __syncwarp();
     }
-    for (int i = lane; i < wn * MN; i += 32) Ar::store(cv + (size_t)w0 * MN + i, acc[i]);
-    __syncwarp();
+    if (!split) {
+      for (int i = lane; i < wn * MN; i += 32) Ar::store(cv + (size_t)w0 * MN + i, acc[i]);
+      return;
+    }
+    __syncthreads();
+    constexpr int STRIDE = RS_ACC_BYTES / sizeof(A);
+    for (int i = threadIdx.x; i < wn * MN; i += RS_WARPS * 32) {
+      A t = sm[i];
+#pragma unroll
+      for (int w = 1; w < RS_WARPS; ++w) Ar::add(t, sm[(size_t)w * STRIDE + i]);
+      Ar::store(cv + (size_t)w0 * MN + i, t);
+    }
   }
 }
 
@@ -637,6 +708,19 @@ __global__ void mirror_lower_kernel(const int* __restrict__ crp, const int* __re
   }
 }
 
+// Windows below which a window gets a whole block: the warps two resident
+// blocks per SM hold.
+int rs_split_windows() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, n_sm = 0;
+    TAM_CUDA(cudaGetDevice(&dev));
+    TAM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    n = std::max(1, n_sm) * 2 * RS_WARPS;
+  }
+  return n;
+}
+
 template <int M, int K, int N, class Ar, typename OutT>
 void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const typename Ar::V* yv, Bsr& C,
                     OutT* cv, bool symmetric, cudaStream_t s) {
@@ -665,9 +749,13 @@ void launch_numeric(const Bsr& X, const typename Ar::V* xv, const Bsr& Y, const 
       rs_window_list_kernel<<<grid_for(C.n_rows, 256), 256, 0, s>>>(wptr.p, C.row_ptr.p, C.col_idx.p, C.n_rows,
                                                                      upper ? 1 : 0, W, win_row.p, win_w0.p);
       TAM_LAUNCH_CHECK();
-      spgemm_numeric_rs_kernel<M, K, N, Ar, OutT><<<grid_for(n_win, RS_WARPS), RS_WARPS * 32, smem, s>>>(
-          X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv,
-          upper ? 1 : 0, win_row.p, win_w0.p, n_win);
+      // Few windows (the coarse levels' products): a block per window, so
+      // that its long X row is shared by RS_WARPS warps instead of one.
+      const int split = n_win < rs_split_windows() ? 1 : 0;
+      spgemm_numeric_rs_kernel<M, K, N, Ar, OutT>
+          <<<split ? (unsigned)n_win : grid_for(n_win, RS_WARPS), RS_WARPS * 32, smem, s>>>(
+              X.row_ptr.p, X.col_idx.p, xv, X.n_rows, Y.row_ptr.p, Y.col_idx.p, yv, C.row_ptr.p, C.col_idx.p, cv,
+              upper ? 1 : 0, win_row.p, win_w0.p, n_win, split);
       TAM_LAUNCH_CHECK();
     }
     if constexpr (M == N && std::is_same<OutT, double>::value) {
@@ -731,7 +819,7 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
   overflow.zero();
   unsigned grid = grid_for(X.n_rows, SG_WARPS);
   spgemm_symbolic_kernel<false><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
-                                                             Y.col_idx.p, C.row_ptr.p, nullptr, nullptr,
+                                                             Y.col_idx.p, Y.n_cols, C.row_ptr.p, nullptr, nullptr,
                                                              overflow.p);
   TAM_LAUNCH_CHECK();
   exclusive_scan_i32(C.row_ptr.p, C.row_ptr.p, C.n_rows, s);
@@ -740,7 +828,7 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
             "spgemm: an output row exceeds 1536 blocks");
   C.col_idx = DBuf<int>((size_t)C.nnzb, s);
   spgemm_symbolic_kernel<true><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
-                                                            Y.col_idx.p, nullptr, C.row_ptr.p, C.col_idx.p,
+                                                            Y.col_idx.p, Y.n_cols, nullptr, C.row_ptr.p, C.col_idx.p,
                                                             overflow.p);
   TAM_LAUNCH_CHECK();
   const int m = X.br, k = X.bc, n = Y.bc;
