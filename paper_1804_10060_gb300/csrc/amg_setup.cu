@@ -8,6 +8,9 @@
 // six rigid-body modes on the finest level), prolongator smoothing
 // P = (I - 4/(3 lambda) D^-1 A) P_tent, R = P^T and the Galerkin product
 // A_c = R A P.  The coarsest operator is inverted densely (Gauss-Jordan).
+// The Lanczos estimate of a level runs on a second stream, concurrently with
+// the level's aggregation and tentative prolongator (only the smoothing of
+// the prolongator needs lambda_max).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -549,14 +552,16 @@ __global__ void dense_zero_inactive_kernel(double* __restrict__ D, int N, const 
 // ---------------------------------------------------------------------------
 // Host orchestration
 // ---------------------------------------------------------------------------
-static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s) {
+// Runs on its own stream s (beside the level's aggregation) with its own
+// grid-reduce scratch gr; writes lambda_max and the Chebyshev constants to
+// L.consts, which the caller allocated before the fork.
+static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s, GridReduce gr) {
   const long long N = (long long)L.n_rows * L.bs;
   const int k = std::min(std::max(H->prm.eig_iters, 1), 64);
   DBuf<double> v(N, s), vp(N, s), u(N, s), w(N, s), sv(N, s), ab(128, s), nrm(1, s);
   DBuf<int> mdone(2, s);
   ab.zero();
   TAM_CUDA(cudaMemsetAsync(mdone.p, 0, 2 * sizeof(int), s));
-  GridReduce gr{H->partials.p, H->ticket.p};
   const unsigned g = std::min<unsigned>(grid_for(N, TPB), (unsigned)H->max_grid);
   lanczos_init_kernel<<<g, TPB, 0, s>>>(L.dinv.p, N, level, sv.p, v.p, gr, nrm.p);
   TAM_LAUNCH_CHECK();
@@ -582,14 +587,56 @@ static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s) {
       TAM_LAUNCH_CHECK();
     }
   }
-  const int deg = std::max(L.deg, 1);
-  L.consts = DBuf<double>(2 + 2 * (size_t)deg, s);
-  tridiag_lmax_kernel<<<1, 32, 0, s>>>(ab.p, mdone.p, k, H->prm.cheb_lo, H->prm.cheb_hi, deg, L.consts.p);
+  tridiag_lmax_kernel<<<1, 32, 0, s>>>(ab.p, mdone.p, k, H->prm.cheb_lo, H->prm.cheb_hi, std::max(L.deg, 1),
+                                       L.consts.p);
   TAM_LAUNCH_CHECK();
-  L.lambda_host = read_back_double(L.consts.p, s);
-  TAM_CHECK(std::isfinite(L.lambda_host) && L.lambda_host > 0.0, TAM_ERR_INTERNAL,
-            "amg_setup: lambda_max estimate is not positive");
 }
+
+// A second stream for work that overlaps the main one: a level's Lanczos
+// estimate runs beside its aggregation, tentative prolongator and A P_tent,
+// which do not need lambda_max; the main stream waits for it only before the
+// prolongator smoothing.  The destructor drains the stream, so buffers the
+// side work uses must be declared before this object.
+struct SideStream {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork_ev = nullptr, done_ev = nullptr;
+  bool pending = false;
+  SideStream() {
+    cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      release();
+      TAM_CUDA(e);
+    }
+  }
+  SideStream(const SideStream&) = delete;
+  SideStream& operator=(const SideStream&) = delete;
+  void fork(cudaStream_t s) {
+    TAM_CUDA(cudaEventRecord(fork_ev, s));
+    TAM_CUDA(cudaStreamWaitEvent(s2, fork_ev, 0));
+  }
+  void done() {
+    TAM_CUDA(cudaEventRecord(done_ev, s2));
+    pending = true;
+  }
+  void join(cudaStream_t s) {
+    if (!pending) return;
+    TAM_CUDA(cudaStreamWaitEvent(s, done_ev, 0));
+    pending = false;
+  }
+  void release() {
+    if (s2) {
+      cudaStreamSynchronize(s2);
+      cudaStreamDestroy(s2);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (done_ev) cudaEventDestroy(done_ev);
+    s2 = nullptr;
+    fork_ev = done_ev = nullptr;
+  }
+  ~SideStream() { release(); }
+};
 
 static int aggregate(Level& L, int level, double theta, int distance, cudaStream_t s) {
   const Bsr& A = *L.A;
@@ -788,6 +835,12 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
         L0.Aop.L = &L0.AL;
       }
     }
+    // the Lanczos estimates' own grid-reduce scratch (they run on the side
+    // stream, concurrently with reductions on s), then the side stream itself
+    DBuf<double> lz_partials((size_t)H->max_grid * 4, s);
+    DBuf<unsigned int> lz_ticket(1, s);
+    lz_ticket.zero();
+    SideStream side;
     for (int lev = 0;; ++lev) {
       Level& L = H->levels[lev];
       L.n_rows = L.A->n_rows;
@@ -799,7 +852,10 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       point_dinv_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.A->row_ptr.p, L.A->col_idx.p, L.A->vals.p, L.n_rows,
                                                                 L.bs, L.dinv.p);
       TAM_LAUNCH_CHECK();
-      lanczos_lambda(H, L, lev, s);
+      L.consts = DBuf<double>(2 + 2 * (size_t)std::max(L.deg, 1), s);
+      side.fork(s);
+      lanczos_lambda(H, L, lev, side.s2, GridReduce{lz_partials.p, lz_ticket.p});
+      side.done();
       alloc_level_vectors(L, s);
       const bool last = (long long)L.n_rows * L.bs <= prm.coarse_max_dofs || lev == prm.max_levels - 1;
       if (!last) {
@@ -816,6 +872,8 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       if (last || L.n_agg == 0 || L.n_agg >= L.n_rows) {
         L.n_agg = 0;
         L.agg.reset();
+        T.mark(0, s);
+        side.join(s);  // before the cooperative launch of the coarse inverse
         T.mark(7, s);
         coarse_inverse(H, L, s);
         break;
@@ -833,6 +891,9 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       SpgemmSplit spA;
       spA.x = As.p;
       bsr_spgemm(*L.A, L.Pt, L.P, s, arith, spA);
+      T.mark(0, s);  // waiting for lambda_max counts as its phase
+      side.join(s);
+      T.mark(3, s);
       smooth_prolongator_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p,
                                                                         L.n_rows, L.bs, k, L.dinv.p, L.consts.p,
                                                                         L.agg.p, L.Pt.row_ptr.p, L.Pt.vals.p);
@@ -901,8 +962,14 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       build_low_precision(H, s);
     }
     T.mark(-1, s);
+    side.join(s);
     TAM_CUDA(cudaStreamSynchronize(s));
     T.finish(H->setup_ms);
+    for (Level& L : H->levels) {
+      L.lambda_host = read_back_double(L.consts.p, s);
+      TAM_CHECK(std::isfinite(L.lambda_host) && L.lambda_host > 0.0, TAM_ERR_INTERNAL,
+                "amg_setup: lambda_max estimate is not positive");
+    }
   } catch (...) {
     delete H;
     throw;
