@@ -552,6 +552,32 @@ __global__ void dense_zero_inactive_kernel(double* __restrict__ D, int N, const 
 // ---------------------------------------------------------------------------
 // Host orchestration
 // ---------------------------------------------------------------------------
+// SpMV layout of a coarse-level operator (see SpOp): SELL-32 for many short
+// rows, the interleaved store for 2-8 lanes per row, whole warps per row over
+// an 8-lane interleaved store for the few long rows of the coarsest levels,
+// else lanes per row over the block-CSR arrays.  Double-float values where
+// use_df says so, and for the whole-warp rows unless FP64 is asked for: with
+// one or two blocks per thread those kernels are bound by the FP64 pipe (the
+// multiply-adds and the closing reduction), not by memory.
+static void plan_spop(SpOp& op, Bsr& A, Sell& S, LprStore& store, int spmv_fp64, cudaStream_t s) {
+  bool df = use_df(A, spmv_fp64);
+  op = SpOp{&A, &S, choose_lpr(A), df};
+  if (op.lpr == 0) {
+    bsr_to_sell(A, S, s);
+    if (df) build_df_values(S, s);
+    return;
+  }
+  op.tpr = rows_tpr(A.n_rows, A.nnzb, op.lpr);
+  if (op.tpr && spmv_fp64 != 1) op.df = df = true;
+  const int store_lpr = op.tpr ? ROWS_LPR : (lpr_store_pays(op.lpr) ? op.lpr : 0);
+  if (store_lpr) {
+    build_lpr_store(A, store_lpr, df, store, s);
+    op.L = &store;
+  } else if (df) {
+    build_df_values(A, s);
+  }
+}
+
 // Runs on its own stream s (beside the level's aggregation) with its own
 // grid-reduce scratch gr; writes lambda_max and the Chebyshev constants to
 // L.consts, which the caller allocated before the fork.
@@ -916,40 +942,11 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
         bsr_spgemm(L.R, AP, C.A_own, s, arith, spR);
         C.A = &C.A_own;
         C.AS = &C.AS_own;
-        const bool cdf = use_df(C.A_own, prm.spmv_fp64);
-        C.Aop = SpOp{&C.A_own, &C.AS_own, choose_lpr(C.A_own), cdf};
-        if (C.Aop.lpr == 0) bsr_to_sell(C.A_own, C.AS_own, s);
-        if (C.Aop.lpr == 0) {
-          if (cdf) build_df_values(C.AS_own, s);
-        } else if (lpr_store_pays(C.Aop.lpr)) {
-          build_lpr_store(C.A_own, C.Aop.lpr, cdf, C.AL, s);
-          C.Aop.L = &C.AL;
-        } else if (cdf) {
-          build_df_values(C.A_own, s);
-        }
+        plan_spop(C.Aop, C.A_own, C.AS_own, C.AL, prm.spmv_fp64, s);
       }
-      const bool pdf = use_df(L.P, prm.spmv_fp64);
-      L.Pop = SpOp{&L.P, &L.PS, choose_lpr(L.P), pdf};
-      L.Rop = SpOp{&L.R, &L.RS, choose_lpr(L.R), pdf};
       T.mark(6, s);
-      if (L.Pop.lpr == 0) bsr_to_sell(L.P, L.PS, s);
-      if (L.Rop.lpr == 0) bsr_to_sell(L.R, L.RS, s);
-      if (L.Pop.lpr == 0) {
-        if (pdf) build_df_values(L.PS, s);
-      } else if (lpr_store_pays(L.Pop.lpr)) {
-        build_lpr_store(L.P, L.Pop.lpr, pdf, L.PL, s);
-        L.Pop.L = &L.PL;
-      } else if (pdf) {
-        build_df_values(L.P, s);
-      }
-      if (L.Rop.lpr == 0) {
-        if (pdf) build_df_values(L.RS, s);
-      } else if (lpr_store_pays(L.Rop.lpr)) {
-        build_lpr_store(L.R, L.Rop.lpr, pdf, L.RL, s);
-        L.Rop.L = &L.RL;
-      } else if (pdf) {
-        build_df_values(L.R, s);
-      }
+      plan_spop(L.Pop, L.P, L.PS, L.PL, prm.spmv_fp64, s);
+      plan_spop(L.Rop, L.R, L.RS, L.RL, prm.spmv_fp64, s);
       B = std::move(Bc);
     }
     H->r = DBuf<double>((size_t)n0 * 3, s);

@@ -132,26 +132,33 @@ __global__ void lpr_count_kernel(const int* __restrict__ rp, int n_rows, int lpr
   if (i < n_rows) cnt[i] = (rp[i + 1] - rp[i] + lpr - 1) / lpr;
 }
 
-// One warp per row; the lanes walk the row's output range in storage order
-// (coalesced writes) and gather from the block-CSR arrays.
-__global__ void lpr_fill_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
-                                int n_rows, int lpr, int bb, const int* __restrict__ gp, int* __restrict__ cols,
-                                double* __restrict__ vals) {
-  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+// Row of every group (a row's groups are consecutive).
+__global__ void lpr_group_row_kernel(const int* __restrict__ gp, int n_rows, int* __restrict__ grow) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_rows) return;
-  const int s0 = rp[i], e0 = rp[i + 1], g0 = gp[i], ng = gp[i + 1] - g0;
-  const int lastc = e0 > s0 ? ci[e0 - 1] : 0;
-  for (int k = lane; k < ng * lpr; k += 32) {
-    const int idx = s0 + k;  // group k / lpr, slot k % lpr: storage index g0 * lpr + k
-    cols[(size_t)g0 * lpr + k] = idx < e0 ? ci[idx] : lastc;
-  }
-  const long long o0 = (long long)g0 * bb * lpr, n_out = (long long)ng * bb * lpr;
-  for (long long q = lane; q < n_out; q += 32) {
-    const long long o = o0 + q;
-    const long long g = o / ((long long)bb * lpr);
-    const int rem = (int)(o - g * bb * lpr), el = rem / lpr, j = rem % lpr;
-    const int idx = s0 + (int)(g - g0) * lpr + j;
-    vals[o] = idx < e0 ? v[(size_t)idx * bb + el] : 0.0;
+  for (int g = gp[i]; g < gp[i + 1]; ++g) grow[g] = i;
+}
+
+// One warp per group: the lanes write the group's lpr columns and its
+// bb * lpr values in storage order (coalesced writes), gathering from the
+// block-CSR arrays; the split copy, when asked for, in the same pass.
+__global__ void lpr_fill_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                                int lpr, int bb, const int* __restrict__ gp, const int* __restrict__ grow,
+                                long long n_groups, int* __restrict__ cols, double* __restrict__ vals,
+                                float2* __restrict__ vals_df) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_groups) return;
+  const int i = grow[w];
+  const int s0 = rp[i] + (int)(w - gp[i]) * lpr, e0 = rp[i + 1];
+  const int lastc = e0 > rp[i] ? ci[e0 - 1] : 0;
+  if (lane < lpr) cols[w * lpr + lane] = s0 + lane < e0 ? ci[s0 + lane] : lastc;
+  const int sh = __ffs(lpr) - 1, n = bb * lpr;  // lpr a power of two
+  for (int e = lane; e < n; e += 32) {
+    const int idx = s0 + (e & (lpr - 1));
+    const double x = idx < e0 ? v[(size_t)idx * bb + (e >> sh)] : 0.0;
+    vals[w * n + e] = x;
+    if (vals_df) vals_df[w * n + e] = split_bits(x);
   }
 }
 }  // namespace
@@ -167,13 +174,18 @@ void build_lpr_store(const Bsr& A, int lpr, bool df, LprStore& L, cudaStream_t s
   TAM_LAUNCH_CHECK();
   exclusive_scan_i32(L.grp_ptr.p, L.grp_ptr.p, A.n_rows, s);
   L.n_groups = read_back_int(L.grp_ptr.p + A.n_rows, s);
-  const long long n = L.n_groups * lpr;
+  const long long n = L.n_groups * lpr, nv = n * (long long)A.block_elems();
   L.cols = DBuf<int>((size_t)std::max(1LL, n), s);
-  L.vals = DBuf<double>((size_t)std::max(1LL, n * (long long)A.block_elems()), s);
-  lpr_fill_kernel<<<grid_for((long long)A.n_rows * 32, 256), 256, 0, s>>>(
-      A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, lpr, (int)A.block_elems(), L.grp_ptr.p, L.cols.p, L.vals.p);
+  L.vals = DBuf<double>((size_t)std::max(1LL, nv), s);
+  if (df) L.vals_df = DBuf<float2>((size_t)std::max(1LL, nv), s);
+  if (L.n_groups == 0) return;
+  DBuf<int> grow((size_t)L.n_groups, s);
+  lpr_group_row_kernel<<<grid_for(A.n_rows, 256), 256, 0, s>>>(L.grp_ptr.p, A.n_rows, grow.p);
   TAM_LAUNCH_CHECK();
-  if (df) split_into(L.vals.p, n * (long long)A.block_elems(), L.vals_df, s);
+  lpr_fill_kernel<<<grid_for(L.n_groups * 32, 256), 256, 0, s>>>(
+      A.row_ptr.p, A.col_idx.p, A.vals.p, lpr, (int)A.block_elems(), L.grp_ptr.p, grow.p, L.n_groups, L.cols.p,
+      L.vals.p, df ? L.vals_df.p : nullptr);
+  TAM_LAUNCH_CHECK();
 }
 
 void build_df_values(Sell& S, cudaStream_t s) {

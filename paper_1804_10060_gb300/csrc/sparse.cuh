@@ -19,6 +19,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -74,6 +75,16 @@ __device__ __forceinline__ void df_fma(float2& a, float2 x, float2 y) {
   const float err = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
   a.x = s;
   a.y = __fadd_rn(a.y, __fadd_rn(err, e));
+}
+
+// a += b for two unevaluated sums hi + lo: TwoSum of the high parts, the
+// low parts and the rounding error added to the low part.
+__device__ __forceinline__ void df_add(float2& a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bp = __fadd_rn(s, -a.x);
+  const float err = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bp)), __fadd_rn(b.x, -bp));
+  a.x = s;
+  a.y = __fadd_rn(a.y, __fadd_rn(err, b.y));
 }
 
 __device__ __forceinline__ double df_to_double(float2 a) { return f2d_bits(a.x) + f2d_bits(a.y); }
@@ -376,6 +387,104 @@ lpr_spmv_kernel(LprView A, const double* __restrict__ x, Epi epi) {
   epi((sub == 0 && row < A.n_rows) ? row : A.n_rows, acc, sh);
 }
 
+// Few long rows (the coarse operators and their transfer operators): TPR
+// threads per row -- one to eight whole warps -- over the 8-lane interleaved
+// store, so that a level of a few hundred or thousand rows still spreads over
+// the SMs and every load is sector-coalesced.  Thread sub of a row takes lane
+// sub % 8 of the row's groups sub / 8, sub / 8 + TPR / 8, ...; each warp
+// reduces with shuffles and the row's warps meet in shared memory, summed in
+// warp order (deterministic).
+constexpr int ROWS_LPR = 8;
+constexpr int SPMV_ROW_THREADS = 256;
+
+template <int BR, int BC, int TPR, class Epi, bool DF>
+__global__ void __launch_bounds__(SPMV_ROW_THREADS)
+lpr_rows_kernel(LprView A, const double* __restrict__ x, Epi epi) {
+  static_assert(TPR % 32 == 0 && SPMV_ROW_THREADS % TPR == 0, "lpr_rows_kernel: whole warps per row");
+  constexpr int BB = BR * BC, GS = TPR / ROWS_LPR;
+  using P = typename std::conditional<DF, float2, double>::type;  // partial sums
+  __shared__ double sh[32];
+  __shared__ P part[SPMV_ROW_THREADS / 32][BR];
+  if (epi.skip()) return;  // block-uniform (a device flag)
+  const int row = blockIdx.x * (SPMV_ROW_THREADS / TPR) + threadIdx.x / TPR;
+  const int sub = threadIdx.x % TPR, ln = sub % ROWS_LPR, wid = threadIdx.x >> 5;
+  double acc[BR];
+  if constexpr (DF) {
+    // the closing reduction stays in double-float too: FP64 adds would make
+    // the FP64 pipe the limit again on these short per-thread sums
+    float2 ad[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
+    if (row < A.n_rows) {
+      const int g1 = A.gp[row + 1];
+      for (int g = A.gp[row] + sub / ROWS_LPR; g < g1; g += GS) {
+        const int c = __ldg(A.cols + (size_t)g * ROWS_LPR + ln);
+        float2 xv[BC];
+#pragma unroll
+        for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
+        const float2* __restrict__ vb = A.v_df + (size_t)g * BB * ROWS_LPR + ln;
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vb + (r * BC + j) * ROWS_LPR), xv[j]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+        df_add(ad[r], make_float2(__shfl_xor_sync(0xffffffffu, ad[r].x, o), __shfl_xor_sync(0xffffffffu, ad[r].y, o)));
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) part[wid][r] = ad[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+      acc[r] = 0.0;
+      if (sub == 0) {  // the row's first warp: part[wid .. wid + TPR / 32) are its warps
+        float2 t = part[wid][r];
+#pragma unroll
+        for (int w = 1; w < TPR / 32; ++w) df_add(t, part[wid + w][r]);
+        acc[r] = df_to_double(t);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < BR; ++r) acc[r] = 0.0;
+    if (row < A.n_rows) {
+      const int g1 = A.gp[row + 1];
+      for (int g = A.gp[row] + sub / ROWS_LPR; g < g1; g += GS) {
+        const int c = __ldg(A.cols + (size_t)g * ROWS_LPR + ln);
+        double xv[BC];
+#pragma unroll
+        for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
+        const double* __restrict__ vb = A.v + (size_t)g * BB * ROWS_LPR + ln;
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vb + (r * BC + j) * ROWS_LPR), xv[j], acc[r]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) part[wid][r] = acc[r];
+    __syncthreads();
+    if (sub == 0)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        double t = part[wid][r];
+#pragma unroll
+        for (int w = 1; w < TPR / 32; ++w) t += part[wid + w][r];
+        acc[r] = t;
+      }
+  }
+  epi((sub == 0 && row < A.n_rows) ? row : A.n_rows, acc, sh);
+}
+
 // A sparse operator with its SpMV strategy: SELL-32 thread-per-row (lpr == 0)
 // or LPR lanes per row (over the interleaved store L when built, else over the
 // Bsr arrays).
@@ -385,7 +494,29 @@ struct SpOp {
   int lpr = 0;
   bool df = true;  // use the storage's split copy when it has one
   const LprStore* L = nullptr;
+  int tpr = 0;     // > 0: lpr_rows_kernel with tpr threads per row over L (an 8-lane store)
 };
+
+// Threads per row for lpr_rows_kernel, or 0: whole warps per row where 16-32
+// lanes per row would leave the GPU with fewer than ~1,024 threads per SM,
+// as many as keep at least one block per thread.
+inline int rows_tpr(int n_rows, long long nnzb, int lpr) {
+  static long long fill = 0;
+  if (fill == 0) {
+    int dev = 0, n_sm = 0;
+    TAM_CUDA(cudaGetDevice(&dev));
+    TAM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    fill = (long long)std::max(1, n_sm) * 1024;
+  }
+  if (lpr < 16 || n_rows <= 0 || (long long)n_rows * lpr >= fill) return 0;
+  const double avg = (double)nnzb / n_rows;
+  int t = 0;
+  for (int c = 32; c <= SPMV_ROW_THREADS && avg >= c; c <<= 1) {
+    t = c;
+    if ((long long)n_rows * c >= fill) break;
+  }
+  return t;
+}
 
 // Double-float pays where an operator is large enough to be bound by memory;
 // on small operators (coarse levels) each lane's short dependent chain makes
@@ -444,10 +575,32 @@ void lpr_launch(const SpOp& op, const LprView& v, const double* x, Epi epi, cuda
   TAM_LAUNCH_CHECK();
 }
 
+template <int BR, int BC, class Epi, bool DF>
+void rows_launch(const SpOp& op, const LprView& v, const double* x, Epi epi, cudaStream_t s) {
+  TAM_CHECK(op.L->lpr == ROWS_LPR, TAM_ERR_INTERNAL, "spmv: whole-warp rows need the 8-lane store");
+  const unsigned g = grid_for(v.n_rows, SPMV_ROW_THREADS / op.tpr);
+  switch (op.tpr) {
+    case 32: lpr_rows_kernel<BR, BC, 32, Epi, DF><<<g, SPMV_ROW_THREADS, 0, s>>>(v, x, epi); break;
+    case 64: lpr_rows_kernel<BR, BC, 64, Epi, DF><<<g, SPMV_ROW_THREADS, 0, s>>>(v, x, epi); break;
+    case 128: lpr_rows_kernel<BR, BC, 128, Epi, DF><<<g, SPMV_ROW_THREADS, 0, s>>>(v, x, epi); break;
+    case 256: lpr_rows_kernel<BR, BC, 256, Epi, DF><<<g, SPMV_ROW_THREADS, 0, s>>>(v, x, epi); break;
+    default: throw Error(TAM_ERR_INTERNAL, "spmv: threads per row must be 32, 64, 128 or 256");
+  }
+  TAM_LAUNCH_CHECK();
+}
+
 template <int BR, int BC, class Epi>
 void spop_apply(const SpOp& op, const double* x, Epi epi, cudaStream_t s) {
   if (op.lpr == 0) {
     sell_spmv<BR, BC>(*op.S, x, epi, s, op.df);
+    return;
+  }
+  if (op.L && op.tpr) {
+    const LprView v{op.L->n_rows, op.L->grp_ptr.p, op.L->cols.p, op.L->vals.p, op.L->vals_df.p};
+    if (op.df && v.v_df)
+      rows_launch<BR, BC, Epi, true>(op, v, x, epi, s);
+    else
+      rows_launch<BR, BC, Epi, false>(op, v, x, epi, s);
     return;
   }
   if (op.L) {
