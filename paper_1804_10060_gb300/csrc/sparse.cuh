@@ -354,29 +354,36 @@ lpr_spmv_kernel(LprView A, const double* __restrict__ x, Epi epi) {
 #pragma unroll
       for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
       for (int g = g0; g < g1; ++g) {
+        // the group's values first (all BB loads in flight), then the gather
+        const float2* __restrict__ vb = A.v_df + (size_t)g * BB * LPR + sub;
+        float2 vv[BB];
+#pragma unroll
+        for (int e = 0; e < BB; ++e) vv[e] = __ldg(vb + e * LPR);
         const int c = __ldg(A.cols + (size_t)g * LPR + sub);
         float2 xv[BC];
 #pragma unroll
         for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
-        const float2* __restrict__ vb = A.v_df + (size_t)g * BB * LPR + sub;
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vb + (r * BC + j) * LPR), xv[j]);
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], vv[r * BC + j], xv[j]);
       }
 #pragma unroll
       for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
     } else {
       for (int g = g0; g < g1; ++g) {
+        const double* __restrict__ vb = A.v + (size_t)g * BB * LPR + sub;
+        double vv[BB];
+#pragma unroll
+        for (int e = 0; e < BB; ++e) vv[e] = __ldg(vb + e * LPR);
         const int c = __ldg(A.cols + (size_t)g * LPR + sub);
         double xv[BC];
 #pragma unroll
         for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
-        const double* __restrict__ vb = A.v + (size_t)g * BB * LPR + sub;
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vb + (r * BC + j) * LPR), xv[j], acc[r]);
+          for (int j = 0; j < BC; ++j) acc[r] = fma(vv[r * BC + j], xv[j], acc[r]);
       }
     }
   }
@@ -418,15 +425,18 @@ lpr_rows_kernel(LprView A, const double* __restrict__ x, Epi epi) {
     if (row < A.n_rows) {
       const int g1 = A.gp[row + 1];
       for (int g = A.gp[row] + sub / ROWS_LPR; g < g1; g += GS) {
+        const float2* __restrict__ vb = A.v_df + (size_t)g * BB * ROWS_LPR + ln;
+        float2 vv[BB];
+#pragma unroll
+        for (int e = 0; e < BB; ++e) vv[e] = __ldg(vb + e * ROWS_LPR);
         const int c = __ldg(A.cols + (size_t)g * ROWS_LPR + ln);
         float2 xv[BC];
 #pragma unroll
         for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
-        const float2* __restrict__ vb = A.v_df + (size_t)g * BB * ROWS_LPR + ln;
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vb + (r * BC + j) * ROWS_LPR), xv[j]);
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], vv[r * BC + j], xv[j]);
       }
     }
 #pragma unroll
@@ -454,15 +464,18 @@ lpr_rows_kernel(LprView A, const double* __restrict__ x, Epi epi) {
     if (row < A.n_rows) {
       const int g1 = A.gp[row + 1];
       for (int g = A.gp[row] + sub / ROWS_LPR; g < g1; g += GS) {
+        const double* __restrict__ vb = A.v + (size_t)g * BB * ROWS_LPR + ln;
+        double vv[BB];
+#pragma unroll
+        for (int e = 0; e < BB; ++e) vv[e] = __ldg(vb + e * ROWS_LPR);
         const int c = __ldg(A.cols + (size_t)g * ROWS_LPR + ln);
         double xv[BC];
 #pragma unroll
         for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
-        const double* __restrict__ vb = A.v + (size_t)g * BB * ROWS_LPR + ln;
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vb + (r * BC + j) * ROWS_LPR), xv[j], acc[r]);
+          for (int j = 0; j < BC; ++j) acc[r] = fma(vv[r * BC + j], xv[j], acc[r]);
       }
     }
 #pragma unroll
