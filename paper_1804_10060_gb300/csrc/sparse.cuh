@@ -256,6 +256,36 @@ struct BsrView {
   const float2* __restrict__ v_df;
 };
 
+// CNT consecutive 8-byte values of one block into registers: 16-byte loads
+// when CNT is even (block starts are then 16-byte aligned: CNT * 8 * p),
+// else 8-byte loads.
+template <int CNT, typename V>
+__device__ __forceinline__ void block_load(const V* __restrict__ p, V (&out)[CNT]) {
+  static_assert(sizeof(V) == 8, "block_load: 8-byte values");
+  if constexpr (CNT % 2 == 0) {
+    if constexpr (std::is_same<V, double>::value) {
+      const double2* __restrict__ p2 = reinterpret_cast<const double2*>(p);
+#pragma unroll
+      for (int i = 0; i < CNT / 2; ++i) {
+        const double2 v = __ldg(p2 + i);
+        out[2 * i] = v.x;
+        out[2 * i + 1] = v.y;
+      }
+    } else {
+      const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+      for (int i = 0; i < CNT / 2; ++i) {
+        const float4 v = __ldg(p4 + i);
+        out[2 * i] = make_float2(v.x, v.y);
+        out[2 * i + 1] = make_float2(v.z, v.w);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) out[i] = __ldg(p + i);
+  }
+}
+
 template <int BR, int BC, int LPR, class Epi, bool DF>
 __global__ void __launch_bounds__(SPMV_THREADS)
 bsr_vector_kernel(BsrView A, const double* __restrict__ x, Epi epi) {
@@ -273,29 +303,31 @@ bsr_vector_kernel(BsrView A, const double* __restrict__ x, Epi epi) {
 #pragma unroll
       for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
       for (int p = A.rp[row] + sub; p < pe; p += LPR) {
+        float2 vv[BR * BC];  // the whole block first (16-byte loads), then the gather
+        block_load<BR * BC>(A.v_df + (size_t)p * BR * BC, vv);
         const int c = A.ci[p];
-        const float2* __restrict__ vb = A.v_df + (size_t)p * BR * BC;
         float2 xv[BC];
 #pragma unroll
         for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vb + r * BC + j), xv[j]);
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], vv[r * BC + j], xv[j]);
       }
 #pragma unroll
       for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
     } else {
       for (int p = A.rp[row] + sub; p < pe; p += LPR) {
+        double vv[BR * BC];
+        block_load<BR * BC>(A.v + (size_t)p * BR * BC, vv);
         const int c = A.ci[p];
-        const double* __restrict__ vb = A.v + (size_t)p * BR * BC;
         double xv[BC];
 #pragma unroll
         for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) acc[r] = fma(__ldg(vb + r * BC + j), xv[j], acc[r]);
+          for (int j = 0; j < BC; ++j) acc[r] = fma(vv[r * BC + j], xv[j], acc[r]);
       }
     }
   }
@@ -510,10 +542,8 @@ struct SpOp {
   int tpr = 0;     // > 0: lpr_rows_kernel with tpr threads per row over L (an 8-lane store)
 };
 
-// Threads per row for lpr_rows_kernel, or 0: whole warps per row where 16-32
-// lanes per row would leave the GPU with fewer than ~1,024 threads per SM,
-// as many as keep at least one block per thread.
-inline int rows_tpr(int n_rows, long long nnzb, int lpr) {
+// Threads that fill the GPU (1,024 per SM) for the SpMV layout choices.
+inline long long spmv_fill_threads() {
   static long long fill = 0;
   if (fill == 0) {
     int dev = 0, n_sm = 0;
@@ -521,7 +551,16 @@ inline int rows_tpr(int n_rows, long long nnzb, int lpr) {
     TAM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     fill = (long long)std::max(1, n_sm) * 1024;
   }
-  if (lpr < 16 || n_rows <= 0 || (long long)n_rows * lpr >= fill) return 0;
+  return fill;
+}
+
+// Threads per row for lpr_rows_kernel, or 0: whole warps per row for the
+// operators that choose_lpr leaves at 16-32 lanes (too few rows to fill the
+// GPU at 8 lanes each), as many warps as fill it while every thread keeps at
+// least one block.
+inline int rows_tpr(int n_rows, long long nnzb, int lpr) {
+  const long long fill = spmv_fill_threads();
+  if (lpr < 16 || n_rows <= 0) return 0;
   const double avg = (double)nnzb / n_rows;
   int t = 0;
   for (int c = 32; c <= SPMV_ROW_THREADS && avg >= c; c <<= 1) {
@@ -554,6 +593,9 @@ inline int choose_lpr(const Bsr& A) {
   const int per_lane = A.n_rows < 65536 ? 8 : 16;
   while (l < 32 && per_lane * l < avg) l <<= 1;
   if (A.n_rows < 8192) l = std::max(l, 16);  // few rows: spread them over more lanes
+  // rows enough to fill the GPU at 8 lanes each: the coalesced 8-lane
+  // interleaved store beats 16-32 lanes over the block-CSR arrays
+  if (l > 8 && (long long)A.n_rows * 8 >= spmv_fill_threads()) l = 8;
   return l;
 }
 
