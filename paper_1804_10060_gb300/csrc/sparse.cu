@@ -288,6 +288,7 @@ namespace {
 constexpr int SG_WARPS = 4;
 constexpr int HT = 2048;            // hash slots per warp
 constexpr int HT_MAX = 1536;        // max unique columns per row (load 0.75)
+constexpr int HT_SMALL = 256;       // slots per warp when every row's bound is <= 128
 
 // Open addressing in a table of hsz (a power of two <= HT) slots.
 __device__ __forceinline__ bool ht_insert(int* tab, int col, int hsz) {
@@ -303,13 +304,15 @@ __device__ __forceinline__ bool ht_insert(int* tab, int col, int hsz) {
   return false;  // table full: caught by the count check
 }
 
-template <bool FILL>
+// HTT slots per warp: HT, or HT_SMALL when every row's bound fits (the finest
+// levels: an eighth of the shared memory, so several times the resident warps).
+template <bool FILL, int HTT>
 __global__ void __launch_bounds__(SG_WARPS * 32)
 spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, int n_rows,
                        const int* __restrict__ yrp, const int* __restrict__ yci, int n_cols,
                        int* __restrict__ row_cnt, const int* __restrict__ crp, int* __restrict__ cci,
                        int* __restrict__ overflow) {
-  __shared__ int tab_all[SG_WARPS][HT];
+  __shared__ int tab_all[SG_WARPS][HTT];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * SG_WARPS + wid;
   if (row >= n_rows) return;
@@ -325,7 +328,7 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   }
   bound = warp_sum_i(bound);
   int hsz = 32;
-  while (hsz < 2 * bound && hsz < HT) hsz <<= 1;
+  while (hsz < 2 * bound && hsz < HTT) hsz <<= 1;
   // Narrow outputs (the coarse levels: few columns, long rows): a bitmap of
   // the n_cols columns instead of the hash set when it has no more words than
   // the table has slots -- no probing, no column limit, and the set bits come
@@ -334,21 +337,15 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   if (words <= hsz) {
     for (int i = lane; i < words; i += 32) tab[i] = 0;
     __syncwarp();
-    if (bound >= 16 * (xe - xs)) {  // long Y rows: lanes over a row's entries (coalesced)
-      for (int p = xs; p < xe; ++p) {
-        const int j = xci[p];
-        for (int q = yrp[j] + lane; q < yrp[j + 1]; q += 32) {
-          const int c = yci[q];
-          atomicOr(reinterpret_cast<unsigned*>(tab) + (c >> 5), 1u << (c & 31));
-        }
-      }
-    } else {
-      for (int p = xs + lane; p < xe; p += 32) {
-        const int j = xci[p];
-        for (int q = yrp[j]; q < yrp[j + 1]; ++q) {
-          const int c = yci[q];
-          atomicOr(reinterpret_cast<unsigned*>(tab) + (c >> 5), 1u << (c & 31));
-        }
+    // sub-groups of W lanes: 32 / W X entries in flight at once, the W lanes
+    // of each striding its Y row (coalesced)
+    const int W = bound >= 8 * (xe - xs) ? 8 : 1;
+    const int sg = lane / W, l = lane % W, nsg = 32 / W;
+    for (int p = xs + sg; p < xe; p += nsg) {
+      const int j = xci[p];
+      for (int q = yrp[j] + l; q < yrp[j + 1]; q += W) {
+        const int c = yci[q];
+        atomicOr(reinterpret_cast<unsigned*>(tab) + (c >> 5), 1u << (c & 31));
       }
     }
     __syncwarp();
@@ -377,6 +374,7 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
       }
       base += total;
     }
+    if (row_cnt && lane == 0) row_cnt[row] = base - crp[row];
     return;
   }
   for (int i = lane; i < hsz; i += 32) tab[i] = 0;
@@ -388,9 +386,9 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   }
   __syncwarp();
   int cnt = warp_sum_i(ins);
-  if (cnt > HT_MAX) {
+  if (cnt > HTT / 4 * 3) {
     if (lane == 0) atomicExch(overflow, 1);
-    if (!FILL && lane == 0) row_cnt[row] = 0;
+    if (row_cnt && lane == 0) row_cnt[row] = 0;
     return;
   }
   if (!FILL) {
@@ -414,6 +412,42 @@ spgemm_symbolic_kernel(const int* __restrict__ xrp, const int* __restrict__ xci,
   warp_bitonic_sort<false>(tab, nullptr, n2);
   const int c0 = crp[row];
   for (int i = lane; i < cnt; i += 32) cci[c0 + i] = tab[i];
+  if (row_cnt && lane == 0) row_cnt[row] = cnt;
+}
+
+// Single-pass symbolic: each row's bound (the sum of its X entries' Y row
+// lengths, at least its distinct columns) ...
+__global__ void spgemm_bound_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, int n_rows,
+                                    const int* __restrict__ yrp, long long* __restrict__ bound,
+                                    int* __restrict__ max_bound) {
+  const int row = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  int b = 0;
+  for (int p = xrp[row] + lane; p < xrp[row + 1]; p += 32) {
+    const int j = xci[p];
+    b += yrp[j + 1] - yrp[j];
+  }
+  b = warp_sum_i(b);
+  if (lane == 0) {
+    bound[row] = b;
+    atomicMax(max_bound, b);
+  }
+}
+
+// ... as 32-bit offsets of the rows' scratch ranges (total checked < 2^31) ...
+__global__ void offsets_to_i32_kernel(const long long* __restrict__ in, long long n, int* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) out[i] = (int)in[i];
+}
+
+// ... and, once the fill pass has written each row's sorted columns to the
+// front of its scratch range and its count, the rows packed into C.
+__global__ void spgemm_pack_kernel(const int* __restrict__ soff, const int* __restrict__ scratch, int n_rows,
+                                   const int* __restrict__ crp, int* __restrict__ cci) {
+  const int row = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  const int s0 = soff[row], c0 = crp[row], n = crp[row + 1] - c0;
+  for (int i = lane; i < n; i += 32) cci[c0 + i] = scratch[s0 + i];
 }
 
 // Output-stationary numeric pass: one thread per output block C_ic.  It walks
@@ -829,20 +863,58 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
   C.row_ptr = DBuf<int>((size_t)C.n_rows + 1, s);
   DBuf<int> overflow(1, s);
   overflow.zero();
-  unsigned grid = grid_for(X.n_rows, SG_WARPS);
-  spgemm_symbolic_kernel<false><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
-                                                             Y.col_idx.p, Y.n_cols, C.row_ptr.p, nullptr, nullptr,
-                                                             overflow.p);
+  const unsigned grid = grid_for(X.n_rows, SG_WARPS);
+  // one pass when the rows' bounds sum below 2^31: the fill kernel writes each
+  // row's sorted columns into a scratch range of its bound and its count, and
+  // a pack kernel moves them into C; otherwise a counting pass first
+  DBuf<long long> b64((size_t)X.n_rows + 1, s);
+  DBuf<int> max_bound(1, s);
+  max_bound.zero();
+  spgemm_bound_kernel<<<grid_for((long long)X.n_rows * 32, 256), 256, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows,
+                                                                              Y.row_ptr.p, b64.p, max_bound.p);
   TAM_LAUNCH_CHECK();
-  exclusive_scan_i32(C.row_ptr.p, C.row_ptr.p, C.n_rows, s);
-  C.nnzb = read_back_int(C.row_ptr.p + C.n_rows, s);
-  TAM_CHECK(read_back_int(overflow.p, s) == 0, TAM_ERR_INTERNAL,
-            "spgemm: an output row exceeds 1536 blocks");
-  C.col_idx = DBuf<int>((size_t)C.nnzb, s);
-  spgemm_symbolic_kernel<true><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
-                                                            Y.col_idx.p, Y.n_cols, nullptr, C.row_ptr.p, C.col_idx.p,
-                                                            overflow.p);
-  TAM_LAUNCH_CHECK();
+  exclusive_scan_i64(b64.p, b64.p, X.n_rows, s);
+  const long long total_bound = read_back_ll(b64.p + X.n_rows, s);
+  const bool small_tab = 2 * read_back_int(max_bound.p, s) <= HT_SMALL;
+  if (total_bound < (1LL << 31) - 1) {
+    DBuf<int> soff((size_t)X.n_rows + 1, s);
+    offsets_to_i32_kernel<<<grid_for((long long)X.n_rows + 1, 256), 256, 0, s>>>(b64.p, X.n_rows, soff.p);
+    TAM_LAUNCH_CHECK();
+    b64.reset();
+    DBuf<int> scratch((size_t)std::max(1LL, total_bound), s);
+    if (small_tab)
+      spgemm_symbolic_kernel<true, HT_SMALL><<<grid, SG_WARPS * 32, 0, s>>>(
+          X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p, Y.col_idx.p, Y.n_cols, C.row_ptr.p, soff.p, scratch.p,
+          overflow.p);
+    else
+      spgemm_symbolic_kernel<true, HT><<<grid, SG_WARPS * 32, 0, s>>>(
+          X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p, Y.col_idx.p, Y.n_cols, C.row_ptr.p, soff.p, scratch.p,
+          overflow.p);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(C.row_ptr.p, C.row_ptr.p, C.n_rows, s);
+    C.nnzb = read_back_int(C.row_ptr.p + C.n_rows, s);
+    TAM_CHECK(read_back_int(overflow.p, s) == 0, TAM_ERR_INTERNAL,
+              "spgemm: an output row exceeds 1536 blocks");
+    C.col_idx = DBuf<int>((size_t)std::max(1LL, C.nnzb), s);
+    spgemm_pack_kernel<<<grid_for((long long)X.n_rows * 32, 256), 256, 0, s>>>(soff.p, scratch.p, X.n_rows,
+                                                                               C.row_ptr.p, C.col_idx.p);
+    TAM_LAUNCH_CHECK();
+  } else {
+    b64.reset();
+    spgemm_symbolic_kernel<false, HT><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
+                                                               Y.col_idx.p, Y.n_cols, C.row_ptr.p, nullptr, nullptr,
+                                                               overflow.p);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(C.row_ptr.p, C.row_ptr.p, C.n_rows, s);
+    C.nnzb = read_back_int(C.row_ptr.p + C.n_rows, s);
+    TAM_CHECK(read_back_int(overflow.p, s) == 0, TAM_ERR_INTERNAL,
+              "spgemm: an output row exceeds 1536 blocks");
+    C.col_idx = DBuf<int>((size_t)C.nnzb, s);
+    spgemm_symbolic_kernel<true, HT><<<grid, SG_WARPS * 32, 0, s>>>(X.row_ptr.p, X.col_idx.p, X.n_rows, Y.row_ptr.p,
+                                                              Y.col_idx.p, Y.n_cols, nullptr, C.row_ptr.p,
+                                                              C.col_idx.p, overflow.p);
+    TAM_LAUNCH_CHECK();
+  }
   const int m = X.br, k = X.bc, n = Y.bc;
   if (m == 3 && k == 3 && n == 6) launch_numeric_any<3, 3, 6>(X, Y, C, arith, sp, s);
   else if (m == 6 && k == 3 && n == 6) launch_numeric_any<6, 3, 6>(X, Y, C, arith, sp, s);

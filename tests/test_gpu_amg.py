@@ -77,12 +77,19 @@ def test_hierarchy_matches_oracle_step_by_step(problem, coarse_min, theta):
         A_in, B, bs = Aco, Bc, 6
 
 
-@pytest.mark.parametrize("spmv_fp64", [1, 2])
-@pytest.mark.parametrize("problem", ["cube8", "slab_small"])
+@pytest.mark.parametrize("spmv_fp64", [0, 1, 2])
+@pytest.mark.parametrize("problem", ["cube8", "slab_small", "cube_p2"])
 def test_vcycle_matches_oracle(problem, spmv_fp64):
-    """V-cycle with its SpMVs in plain FP64 (1) or double-float everywhere (2)."""
+    """V-cycle with its SpMVs chosen per operator (0), in plain FP64 (1) or
+    double-float everywhere (2).
+
+    The restrictions of cube8 and slab_small (9-94 rows of 34-68 blocks) and
+    the P2 cube's level 1 (143 rows of 68 blocks: Chebyshev and residual
+    SpMVs) run whole warps per row (32-64 threads) over the 8-lane store.
+    """
     pb = {"cube8": lambda: meshgen.unit_cube_problem(8),
-          "slab_small": lambda: meshgen.slab_box_problem(24, 8, 8)}[problem]()
+          "slab_small": lambda: meshgen.slab_box_problem(24, 8, 8),
+          "cube_p2": lambda: meshgen.unit_cube_problem(5, 2)}[problem]()
     tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60, spmv_fp64=spmv_fp64)
     Ko, _ = fem.assemble_system(pb)
     Ho = oamg.setup(Ko, fem.rigid_body_modes(pb.coords, pb.dirichlet_mask), 3, coarse_max_dofs=60)
