@@ -289,10 +289,13 @@ __global__ void mis_init_kernel(const unsigned char* __restrict__ isolated, int 
   if (i < n) state[i] = isolated[i] ? ST_OUT : ST_UND;
 }
 
+// A round whose predecessor left no node undecided (prev_und, null for the
+// first round) does nothing, so the host can launch several rounds per check.
 __global__ void mis_round1_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
-                                  const unsigned char* __restrict__ state, int n, int level, unsigned long long* __restrict__ m1) {
+                                  const unsigned char* __restrict__ state, int n, int level, unsigned long long* __restrict__ m1,
+                                  const int* __restrict__ prev_und) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (prev_und && *prev_und == 0)) return;
   unsigned long long m = mis_tuple(state[i], level, i);
   for (int p = rp[i]; p < rp[i + 1]; ++p)
     if (strong[p]) {
@@ -305,9 +308,10 @@ __global__ void mis_round1_kernel(const int* __restrict__ rp, const int* __restr
 
 __global__ void mis_round2_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
                                   unsigned char* __restrict__ state, const unsigned long long* __restrict__ m1, int n,
-                                  int level, int distance, int* __restrict__ undecided) {
+                                  int level, int distance, const int* __restrict__ prev_und,
+                                  int* __restrict__ undecided) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (prev_und && *prev_und == 0)) return;
   if (state[i] != ST_UND) return;
   unsigned long long m = m1[i];  // max over the closed 1-neighbourhood
   if (distance == 2)
@@ -680,22 +684,28 @@ static int aggregate(Level& L, int level, double theta, int distance, cudaStream
   mis_init_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(isolated.p, n, state.p);
   TAM_LAUNCH_CHECK();
   DBuf<unsigned long long> m1(n, s);
-  DBuf<int> und(1, s);
-  for (int it = 0; it < 1000; ++it) {
-    und.zero();
-    mis_round1_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, n, level, m1.p);
+  // und[it]: nodes still undecided after round it; rounds launched 8 at a
+  // time between host checks (a round after one that left none is a no-op)
+  constexpr int kMaxRounds = 1024, kBatch = 8;
+  DBuf<int> und(kMaxRounds, s);
+  und.zero();
+  for (int it = 0;; ++it) {
+    const int* prev = it > 0 ? und.p + it - 1 : nullptr;
+    mis_round1_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, n, level, m1.p,
+                                                       prev);
     TAM_LAUNCH_CHECK();
     mis_round2_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, m1.p, n, level,
-                                                       distance, und.p);
+                                                       distance, prev, und.p + it);
     TAM_LAUNCH_CHECK();
-    if (read_back_int(und.p, s) == 0) break;
-    TAM_CHECK(it < 999, TAM_ERR_INTERNAL, "amg_setup: MIS-2 did not terminate");
+    if ((it + 1) % kBatch == 0 || it + 1 == kMaxRounds) {
+      if (read_back_int(und.p + it, s) == 0) break;
+      TAM_CHECK(it + 1 < kMaxRounds, TAM_ERR_INTERNAL, "amg_setup: MIS-2 did not terminate");
+    }
   }
   DBuf<int> root_id((size_t)n + 1, s);
   root_flag_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(state.p, isolated.p, n, root_id.p);
   TAM_LAUNCH_CHECK();
   exclusive_scan_i32(root_id.p, root_id.p, n, s);
-  const int n_agg = read_back_int(root_id.p + n, s);
   DBuf<int> agg2(n, s), fail(1, s);
   fail.zero();
   agg_phase2_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, isolated.p, root_id.p,
@@ -705,7 +715,9 @@ static int aggregate(Level& L, int level, double theta, int distance, cudaStream
   agg_phase3_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, isolated.p, agg2.p, n, level,
                                                      L.agg.p, fail.p);
   TAM_LAUNCH_CHECK();
-  TAM_CHECK(read_back_int(fail.p, s) == 0, TAM_ERR_INTERNAL, "amg_setup: aggregation left a node unassigned");
+  int n_agg = 0, failed = 0;
+  read_back_int2(root_id.p + n, fail.p, &n_agg, &failed, s);
+  TAM_CHECK(failed == 0, TAM_ERR_INTERNAL, "amg_setup: aggregation left a node unassigned");
   return n_agg;
 }
 

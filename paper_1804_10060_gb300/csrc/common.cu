@@ -68,6 +68,24 @@ long long read_back_ll(const long long* dptr, cudaStream_t s) {
   return h.ll[0];
 }
 
+void read_back_ll_int(const long long* a, const int* b, long long* va, int* vb, cudaStream_t s) {
+  HostScalars& h = host_scalars();
+  TAM_CUDA(cudaMemcpyAsync(h.ll, a, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  TAM_CUDA(cudaMemcpyAsync(h.ll + 1, b, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TAM_CUDA(cudaStreamSynchronize(s));
+  *va = h.ll[0];
+  *vb = *reinterpret_cast<int*>(h.ll + 1);
+}
+
+void read_back_int2(const int* a, const int* b, int* va, int* vb, cudaStream_t s) {
+  HostScalars& h = host_scalars();
+  TAM_CUDA(cudaMemcpyAsync(h.ll, a, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TAM_CUDA(cudaMemcpyAsync(h.ll + 1, b, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TAM_CUDA(cudaStreamSynchronize(s));
+  *va = *reinterpret_cast<int*>(h.ll);
+  *vb = *reinterpret_cast<int*>(h.ll + 1);
+}
+
 int read_back_int(const int* dptr, cudaStream_t s) {
   HostScalars& h = host_scalars();
   TAM_CUDA(cudaMemcpyAsync(h.ll, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -97,6 +97,9 @@ HostScalars& host_scalars();  // per thread, allocated once
 
 long long read_back_ll(const long long* dptr, cudaStream_t s);
 int read_back_int(const int* dptr, cudaStream_t s);
+// Two scalars with one synchronisation.
+void read_back_ll_int(const long long* a, const int* b, long long* va, int* vb, cudaStream_t s);
+void read_back_int2(const int* a, const int* b, int* va, int* vb, cudaStream_t s);
 double read_back_double(const double* dptr, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

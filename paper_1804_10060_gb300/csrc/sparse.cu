@@ -874,8 +874,10 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
                                                                               Y.row_ptr.p, b64.p, max_bound.p);
   TAM_LAUNCH_CHECK();
   exclusive_scan_i64(b64.p, b64.p, X.n_rows, s);
-  const long long total_bound = read_back_ll(b64.p + X.n_rows, s);
-  const bool small_tab = 2 * read_back_int(max_bound.p, s) <= HT_SMALL;
+  long long total_bound = 0;
+  int max_b = 0;
+  read_back_ll_int(b64.p + X.n_rows, max_bound.p, &total_bound, &max_b, s);
+  const bool small_tab = 2 * max_b <= HT_SMALL;
   if (total_bound < (1LL << 31) - 1) {
     DBuf<int> soff((size_t)X.n_rows + 1, s);
     offsets_to_i32_kernel<<<grid_for((long long)X.n_rows + 1, 256), 256, 0, s>>>(b64.p, X.n_rows, soff.p);
@@ -892,9 +894,10 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
           overflow.p);
     TAM_LAUNCH_CHECK();
     exclusive_scan_i32(C.row_ptr.p, C.row_ptr.p, C.n_rows, s);
-    C.nnzb = read_back_int(C.row_ptr.p + C.n_rows, s);
-    TAM_CHECK(read_back_int(overflow.p, s) == 0, TAM_ERR_INTERNAL,
-              "spgemm: an output row exceeds 1536 blocks");
+    int nnzb = 0, ovf = 0;
+    read_back_int2(C.row_ptr.p + C.n_rows, overflow.p, &nnzb, &ovf, s);
+    C.nnzb = nnzb;
+    TAM_CHECK(ovf == 0, TAM_ERR_INTERNAL, "spgemm: an output row exceeds 1536 blocks");
     C.col_idx = DBuf<int>((size_t)std::max(1LL, C.nnzb), s);
     spgemm_pack_kernel<<<grid_for((long long)X.n_rows * 32, 256), 256, 0, s>>>(soff.p, scratch.p, X.n_rows,
                                                                                C.row_ptr.p, C.col_idx.p);
