@@ -498,7 +498,7 @@ struct ArithDF {
 };
 
 template <int M, int K, int N, class Ar, typename OutT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 6)
 spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, const typename Ar::V* __restrict__ xv,
                          const int* __restrict__ yrp, const int* __restrict__ yci, const typename Ar::V* __restrict__ yv,
                          const int* __restrict__ crow, const int* __restrict__ cci, long long nnzc,

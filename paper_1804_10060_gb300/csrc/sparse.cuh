@@ -195,6 +195,9 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
       for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
 #pragma unroll 2
       for (int k = k0; k < k1; ++k) {
+        float2 vv[BR * BC];  // the slot's values first, then the gather
+#pragma unroll
+        for (int e = 0; e < BR * BC; ++e) vv[e] = __ldg(vp + e * 32);
         const int c = __ldg(cp);
         float2 xv[BC];
 #pragma unroll
@@ -202,7 +205,7 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) df_fma(ad[r], __ldg(vp + (r * BC + j) * 32), xv[j]);
+          for (int j = 0; j < BC; ++j) df_fma(ad[r], vv[r * BC + j], xv[j]);
         cp += 32;
         vp += 32 * BR * BC;
       }
