@@ -365,8 +365,11 @@ msell_kernel(int n_slices, const int* __restrict__ slice_ptr, const int* __restr
   if (slice < n_slices) {
     const int k0 = slice_ptr[slice], k1 = slice_ptr[slice + 1];
     for (int s = k0; s < k1; ++s) {
-      const int c = __ldg(cols + (size_t)s * 32 + lane);
       const TV* __restrict__ vp = vals + (size_t)s * 32 * BR * BC + lane;
+      TV vv[BR * BC];  // the slot's values first, then the gathers
+#pragma unroll
+      for (int e = 0; e < BR * BC; ++e) vv[e] = vp[e * 32];
+      const int c = __ldg(cols + (size_t)s * 32 + lane);
 #pragma unroll
       for (int jc = 0; jc < BC; ++jc) {
         const float* xr = x + ((size_t)c * BC + jc) * mp + j0;
@@ -375,7 +378,7 @@ msell_kernel(int n_slices, const int* __restrict__ slice_ptr, const int* __restr
         for (int k = 0; k < TMAX; ++k) xv[k] = k < tm ? __ldg(xr + k) : 0.f;
 #pragma unroll
         for (int r = 0; r < BR; ++r) {
-          const float a = to_f32(vp[(r * BC + jc) * 32]);
+          const float a = to_f32(vv[r * BC + jc]);
 #pragma unroll
           for (int k = 0; k < TMAX; ++k) acc[r][k] = fmaf(a, xv[k], acc[r][k]);
         }
@@ -402,8 +405,11 @@ mvec_kernel(int n_rows, const int* __restrict__ rp, const int* __restrict__ ci, 
   if (row < n_rows) {
     const int pe = rp[row + 1];
     for (int p = rp[row] + sub; p < pe; p += lpr) {
-      const int c = ci[p];
       const TV* __restrict__ vb = v + (size_t)p * BR * BC;
+      TV vv[BR * BC];  // the block's values first, then the gathers
+#pragma unroll
+      for (int e = 0; e < BR * BC; ++e) vv[e] = vb[e];
+      const int c = ci[p];
 #pragma unroll
       for (int jc = 0; jc < BC; ++jc) {
         const float* xr = x + ((size_t)c * BC + jc) * mp + j0;
@@ -412,7 +418,7 @@ mvec_kernel(int n_rows, const int* __restrict__ rp, const int* __restrict__ ci, 
         for (int k = 0; k < TMAX; ++k) xv[k] = k < tm ? __ldg(xr + k) : 0.f;
 #pragma unroll
         for (int r = 0; r < BR; ++r) {
-          const float a = to_f32(vb[r * BC + jc]);
+          const float a = to_f32(vv[r * BC + jc]);
 #pragma unroll
           for (int k = 0; k < TMAX; ++k) acc[r][k] = fmaf(a, xv[k], acc[r][k]);
         }

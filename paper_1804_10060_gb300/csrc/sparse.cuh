@@ -702,6 +702,9 @@ sell_spmv_f32_kernel(int n_slices, const int* __restrict__ slice_ptr, const int*
     const TV* __restrict__ vp = vals + (size_t)k0 * 32 * BR * BC + lane;
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
+      TV vv[BR * BC];  // the slot's values first, then the gather
+#pragma unroll
+      for (int e = 0; e < BR * BC; ++e) vv[e] = vp[e * 32];
       const int c = __ldg(cp);
       float xv[BC];
 #pragma unroll
@@ -709,7 +712,7 @@ sell_spmv_f32_kernel(int n_slices, const int* __restrict__ slice_ptr, const int*
 #pragma unroll
       for (int r = 0; r < BR; ++r)
 #pragma unroll
-        for (int j = 0; j < BC; ++j) acc[r] = fmaf(to_f32(vp[(r * BC + j) * 32]), xv[j], acc[r]);
+        for (int j = 0; j < BC; ++j) acc[r] = fmaf(to_f32(vv[r * BC + j]), xv[j], acc[r]);
       cp += 32;
       vp += 32 * BR * BC;
     }
@@ -731,15 +734,18 @@ bsr_vector_f32_kernel(int n_rows, const int* __restrict__ rp, const int* __restr
   if (row < n_rows) {
     const int pe = rp[row + 1];
     for (int p = rp[row] + sub; p < pe; p += LPR) {
-      const int c = ci[p];
       const TV* __restrict__ vb = v + (size_t)p * BR * BC;
+      TV vv[BR * BC];  // the block's values first, then the gather
+#pragma unroll
+      for (int e = 0; e < BR * BC; ++e) vv[e] = vb[e];
+      const int c = ci[p];
       float xv[BC];
 #pragma unroll
       for (int j = 0; j < BC; ++j) xv[j] = __ldg(x + (size_t)c * BC + j);
 #pragma unroll
       for (int r = 0; r < BR; ++r)
 #pragma unroll
-        for (int j = 0; j < BC; ++j) acc[r] = fmaf(to_f32(vb[r * BC + j]), xv[j], acc[r]);
+        for (int j = 0; j < BC; ++j) acc[r] = fmaf(to_f32(vv[r * BC + j]), xv[j], acc[r]);
     }
   }
 #pragma unroll
