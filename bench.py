@@ -38,9 +38,9 @@ SAMPLE_DIMS = (96, 24, 24)      # bounded oracle sample (same structure, 181,875
 FALLBACK_HBM_GBS = 6800.0       # recipe fallback when MEASURED_PEAKS.json is absent
 NOMINAL_FP64_TFLOPS = 1.25      # GB300 FP64 (nominal table)
 # DRAM bytes (read + write) of one double-float level-0 SpMV launch on the
-# 256x64x64 box: ncu capture of the same kernel on the 160x40x40 box (315.2 MB,
+# 256x64x64 box: ncu capture of the same kernel on the 160x40x40 box (315.3 MB,
 # profiles/sell_spmv_box160x40x40.md) scaled by the block count (x 4.065).
-SPMV_DRAM_BYTES_FULL = 1.281e9
+SPMV_DRAM_BYTES_FULL = 1.2815e9
 
 
 def parse():
