@@ -509,36 +509,86 @@ __global__ void dense_inactive_kernel(double* __restrict__ D, int N, unsigned ch
   }
 }
 
-// In-place Gauss-Jordan inversion of an SPD matrix (no pivoting needed).  Step
-// k: (a) save column k and divide row k by the pivot p = D_kk; (b) for i != k:
-// D_ij -= D_ik(old) * D_kj(new) (j != k), D_ik = -D_ik(old) / p, and D_kk = 1/p.
-// The grid-wide barrier separates (a) from (b) and each step from the next;
-// the kernel is launched cooperatively, so all blocks are co-resident.
-__global__ void __launch_bounds__(256) gj_coop_kernel(double* __restrict__ D, int N, double* __restrict__ colk,
+// In-place Gauss-Jordan inversion of an SPD matrix (no pivoting needed),
+// blocked by panels K = [k0, k0 + b) of GJB columns.  With A = [A_KK A_KJ;
+// A_IK A_IJ], eliminating K gives [A_KK^-1, A_KK^-1 A_KJ; -A_IK A_KK^-1,
+// A_IJ - A_IK A_KK^-1 A_KJ], the state the unblocked method reaches after b
+// pivots (D_kj /= p, D_ik = -D_ik / p, D_kk = 1 / p).  Per panel:
+//   1. block 0 inverts D_KK in shared memory by unblocked Gauss-Jordan (its
+//      pivots are the unblocked method's: positive for an SPD matrix);
+//   2. the row panel D_KJ becomes D_KK^-1 D_KJ, and the column panel D_IK is
+//      saved (cpan, row-major N x GJB);
+//   3. D_IJ -= cpan D_KJ(new) and D_IK = -cpan D_KK^-1.
+// Three grid-wide barriers per panel instead of two per pivot (the barriers,
+// not the N^3 multiply-adds, dominated: 624 of them on a 312-DOF level).
+constexpr int GJB = 32;
+
+__global__ void __launch_bounds__(256) gj_coop_kernel(double* __restrict__ D, int N, double* __restrict__ cpan,
                                                       int* __restrict__ bad) {
   cg::grid_group grid = cg::this_grid();
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nth = (long long)gridDim.x * blockDim.x;
-  const long long NN = (long long)N * N;
-  for (int k = 0; k < N; ++k) {
-    const double p = D[(size_t)k * N + k];  // not written in phase (a)
-    if (tid == 0 && !(p > 0.0)) *bad = 1;
-    for (long long t = tid; t < N; t += nth)
-      if (t != k) {
-        colk[t] = D[(size_t)t * N + k];
-        D[(size_t)k * N + t] /= p;
+  __shared__ double sd[GJB][GJB + 1];  // the diagonal block (step 1), then its inverse (steps 2-3)
+  __shared__ double ck[GJB];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  for (int k0 = 0; k0 < N; k0 += GJB) {
+    const int b = min(GJB, N - k0);
+    if (blockIdx.x == 0) {  // 1.
+      for (int e = threadIdx.x; e < b * b; e += blockDim.x) sd[e / b][e % b] = D[(size_t)(k0 + e / b) * N + k0 + e % b];
+      __syncthreads();
+      for (int k = 0; k < b; ++k) {
+        const double p = sd[k][k];
+        if (threadIdx.x == 0 && !(p > 0.0)) *bad = 1;
+        if (threadIdx.x < b) ck[threadIdx.x] = sd[threadIdx.x][k];
+        __syncthreads();
+        if (threadIdx.x < b && threadIdx.x != k) sd[k][threadIdx.x] /= p;
+        __syncthreads();
+        const double inv = 1.0 / p;
+        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+          const int i = e / b, j = e % b;
+          if (i == k) {
+            if (j == k) sd[k][k] = inv;
+            continue;
+          }
+          if (j == k) sd[i][k] = -ck[i] * inv;
+          else sd[i][j] -= ck[i] * sd[k][j];
+        }
+        __syncthreads();
       }
+      for (int e = threadIdx.x; e < b * b; e += blockDim.x) D[(size_t)(k0 + e / b) * N + k0 + e % b] = sd[e / b][e % b];
+    }
     grid.sync();
-    const double inv = 1.0 / p;
-    for (long long e = tid; e < NN; e += nth) {
-      const int i = (int)(e / N), j = (int)(e % N);
-      if (i == k) {
-        if (j == k) D[(size_t)k * N + k] = inv;
-        continue;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) sd[e / b][e % b] = D[(size_t)(k0 + e / b) * N + k0 + e % b];
+    __syncthreads();
+    // 2. row panel (a thread per column outside K) and the saved column panel
+    for (int jj = tid; jj < N - b; jj += nth) {
+      const int j = jj < k0 ? jj : jj + b;
+      double old[GJB];
+#pragma unroll
+      for (int t = 0; t < GJB; ++t) old[t] = t < b ? D[(size_t)(k0 + t) * N + j] : 0.0;
+      for (int r = 0; r < b; ++r) {
+        double v = 0.0;
+#pragma unroll
+        for (int t = 0; t < GJB; ++t) v = fma(sd[r][t < b ? t : 0], t < b ? old[t] : 0.0, v);
+        D[(size_t)(k0 + r) * N + j] = v;
       }
-      const double f = colk[i];
-      if (j == k) D[(size_t)i * N + k] = -f * inv;
-      else D[(size_t)i * N + j] -= f * D[(size_t)k * N + j];
+    }
+    for (int e = tid; e < (N - b) * b; e += nth) {
+      const int ii = e / b, c = e % b, i = ii < k0 ? ii : ii + b;
+      cpan[(size_t)i * GJB + c] = D[(size_t)i * N + k0 + c];
+    }
+    grid.sync();
+    // 3. the rest and the column panel (a thread per element of the rows outside K)
+    for (int e = tid; e < (N - b) * N; e += nth) {
+      const int ii = e / N, j = e % N, i = ii < k0 ? ii : ii + b;
+      const double* __restrict__ ci = cpan + (size_t)i * GJB;
+      double v = 0.0;
+      if (j >= k0 && j < k0 + b) {
+        for (int t = 0; t < b; ++t) v = fma(ci[t], sd[t][j - k0], v);
+        D[(size_t)i * N + j] = -v;
+      } else {
+        for (int t = 0; t < b; ++t) v = fma(ci[t], D[(size_t)(k0 + t) * N + j], v);
+        D[(size_t)i * N + j] -= v;
+      }
     }
     grid.sync();
   }
@@ -769,12 +819,12 @@ static void coarse_inverse(tam_amg_s* H, const Level& L, cudaStream_t s) {
   DBuf<unsigned char> inactive(N, s);
   dense_inactive_kernel<<<N, 128, 0, s>>>(H->coarse_inv.p, N, inactive.p);
   TAM_LAUNCH_CHECK();
-  DBuf<double> colk(N, s);
+  DBuf<double> colk((size_t)N * GJB, s);
   DBuf<int> bad(1, s);
   bad.zero();
   dim3 ug(grid_for(N, TPB), N);
-  // all N pivot steps in one cooperative launch (grid-wide barrier between
-  // the two phases of a step) instead of 2N kernel launches
+  // all panels in one cooperative launch (grid-wide barriers between the
+  // three steps of a panel) instead of 3N / GJB kernel launches
   int dev = 0, n_sm = 0, per_sm = 0;
   TAM_CUDA(cudaGetDevice(&dev));
   TAM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -785,8 +835,7 @@ static void coarse_inverse(tam_amg_s* H, const Level& L, cudaStream_t s) {
   int* bp = bad.p;
   int n_arg = N;
   void* args[] = {&dp, &n_arg, &cp, &bp};
-  TAM_CUDA(cudaLaunchCooperativeKernel((const void*)gj_coop_kernel, dim3(n_sm * std::min(per_sm, 2)), dim3(TPB), args,
-                                       0, s));
+  TAM_CUDA(cudaLaunchCooperativeKernel((const void*)gj_coop_kernel, dim3(n_sm), dim3(TPB), args, 0, s));
   TAM_LAUNCH_CHECK();
   dense_zero_inactive_kernel<<<ug, TPB, 0, s>>>(H->coarse_inv.p, N, inactive.p);
   TAM_LAUNCH_CHECK();
