@@ -516,15 +516,15 @@ __global__ void dense_inactive_kernel(double* __restrict__ D, int N, unsigned ch
 // pivots (D_kj /= p, D_ik = -D_ik / p, D_kk = 1 / p).  Per panel:
 //   1. block 0 inverts D_KK in shared memory by unblocked Gauss-Jordan (its
 //      pivots are the unblocked method's: positive for an SPD matrix);
-//   2. the row panel D_KJ becomes D_KK^-1 D_KJ, and the column panel D_IK is
-//      saved (cpan, row-major N x GJB);
-//   3. D_IJ -= cpan D_KJ(new) and D_IK = -cpan D_KK^-1.
+//   2. the new row panel D_KK^-1 D_KJ goes to rpan (GJB x N, a thread per
+//      element) and the column panel D_IK is saved (cpan, N x GJB);
+//   3. D_IJ -= cpan rpan, D_IK = -cpan D_KK^-1, and rpan is copied to D_KJ.
 // Three grid-wide barriers per panel instead of two per pivot (the barriers,
 // not the N^3 multiply-adds, dominated: 624 of them on a 312-DOF level).
 constexpr int GJB = 32;
 
 __global__ void __launch_bounds__(256) gj_coop_kernel(double* __restrict__ D, int N, double* __restrict__ cpan,
-                                                      int* __restrict__ bad) {
+                                                      double* __restrict__ rpan, int* __restrict__ bad) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double sd[GJB][GJB + 1];  // the diagonal block (step 1), then its inverse (steps 2-3)
   __shared__ double ck[GJB];
@@ -538,11 +538,11 @@ __global__ void __launch_bounds__(256) gj_coop_kernel(double* __restrict__ D, in
       for (int k = 0; k < b; ++k) {
         const double p = sd[k][k];
         if (threadIdx.x == 0 && !(p > 0.0)) *bad = 1;
+        const double inv = 1.0 / p;
         if (threadIdx.x < b) ck[threadIdx.x] = sd[threadIdx.x][k];
         __syncthreads();
-        if (threadIdx.x < b && threadIdx.x != k) sd[k][threadIdx.x] /= p;
+        if (threadIdx.x < b && threadIdx.x != k) sd[k][threadIdx.x] *= inv;
         __syncthreads();
-        const double inv = 1.0 / p;
         for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
           const int i = e / b, j = e % b;
           if (i == k) {
@@ -559,18 +559,13 @@ __global__ void __launch_bounds__(256) gj_coop_kernel(double* __restrict__ D, in
     grid.sync();
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) sd[e / b][e % b] = D[(size_t)(k0 + e / b) * N + k0 + e % b];
     __syncthreads();
-    // 2. row panel (a thread per column outside K) and the saved column panel
-    for (int jj = tid; jj < N - b; jj += nth) {
-      const int j = jj < k0 ? jj : jj + b;
-      double old[GJB];
-#pragma unroll
-      for (int t = 0; t < GJB; ++t) old[t] = t < b ? D[(size_t)(k0 + t) * N + j] : 0.0;
-      for (int r = 0; r < b; ++r) {
-        double v = 0.0;
-#pragma unroll
-        for (int t = 0; t < GJB; ++t) v = fma(sd[r][t < b ? t : 0], t < b ? old[t] : 0.0, v);
-        D[(size_t)(k0 + r) * N + j] = v;
-      }
+    // 2. new row panel (a thread per element, columns outside K) and the
+    // saved column panel
+    for (int e = tid; e < b * (N - b); e += nth) {
+      const int r = e / (N - b), jj = e % (N - b), j = jj < k0 ? jj : jj + b;
+      double v = 0.0;
+      for (int t = 0; t < b; ++t) v = fma(sd[r][t], D[(size_t)(k0 + t) * N + j], v);
+      rpan[(size_t)r * N + j] = v;
     }
     for (int e = tid; e < (N - b) * b; e += nth) {
       const int ii = e / b, c = e % b, i = ii < k0 ? ii : ii + b;
@@ -586,9 +581,13 @@ __global__ void __launch_bounds__(256) gj_coop_kernel(double* __restrict__ D, in
         for (int t = 0; t < b; ++t) v = fma(ci[t], sd[t][j - k0], v);
         D[(size_t)i * N + j] = -v;
       } else {
-        for (int t = 0; t < b; ++t) v = fma(ci[t], D[(size_t)(k0 + t) * N + j], v);
+        for (int t = 0; t < b; ++t) v = fma(ci[t], rpan[(size_t)t * N + j], v);
         D[(size_t)i * N + j] -= v;
       }
+    }
+    for (int e = tid; e < b * (N - b); e += nth) {
+      const int r = e / (N - b), jj = e % (N - b), j = jj < k0 ? jj : jj + b;
+      D[(size_t)(k0 + r) * N + j] = rpan[(size_t)r * N + j];
     }
     grid.sync();
   }
@@ -819,7 +818,7 @@ static void coarse_inverse(tam_amg_s* H, const Level& L, cudaStream_t s) {
   DBuf<unsigned char> inactive(N, s);
   dense_inactive_kernel<<<N, 128, 0, s>>>(H->coarse_inv.p, N, inactive.p);
   TAM_LAUNCH_CHECK();
-  DBuf<double> colk((size_t)N * GJB, s);
+  DBuf<double> colk((size_t)N * GJB, s), rowk((size_t)N * GJB, s);
   DBuf<int> bad(1, s);
   bad.zero();
   dim3 ug(grid_for(N, TPB), N);
@@ -832,9 +831,10 @@ static void coarse_inverse(tam_amg_s* H, const Level& L, cudaStream_t s) {
   TAM_CHECK(per_sm >= 1, TAM_ERR_INTERNAL, "amg_setup: Gauss-Jordan kernel cannot be resident");
   double* dp = H->coarse_inv.p;
   double* cp = colk.p;
+  double* rp = rowk.p;
   int* bp = bad.p;
   int n_arg = N;
-  void* args[] = {&dp, &n_arg, &cp, &bp};
+  void* args[] = {&dp, &n_arg, &cp, &rp, &bp};
   TAM_CUDA(cudaLaunchCooperativeKernel((const void*)gj_coop_kernel, dim3(n_sm), dim3(TPB), args, 0, s));
   TAM_LAUNCH_CHECK();
   dense_zero_inactive_kernel<<<ug, TPB, 0, s>>>(H->coarse_inv.p, N, inactive.p);
