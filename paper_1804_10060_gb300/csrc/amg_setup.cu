@@ -459,25 +459,25 @@ __global__ void ptent_qr_kernel(const int* __restrict__ ap, const int* __restric
 }
 
 // P = (I - omega D^-1 A) P_tent, in place on the values of A*P_tent
+// One warp per row: a row's blocks are contiguous, so the lanes stride its
+// bs * k values (coalesced) instead of one thread walking them.
 __global__ void smooth_prolongator_kernel(const int* __restrict__ rp, const int* __restrict__ ci, double* __restrict__ v,
                                           int n, int bs, int k, const double* __restrict__ dinv,
                                           const double* __restrict__ consts, const int* __restrict__ agg,
                                           const int* __restrict__ ptrp, const double* __restrict__ ptv) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= n) return;
   const double omega = consts[1];
-  const int a = agg[i];
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    const bool diag = ci[p] == a;
-    for (int r = 0; r < bs; ++r) {
-      const double sc = -omega * dinv[(size_t)i * bs + r];
-      for (int q = 0; q < k; ++q) {
-        size_t o = (size_t)p * bs * k + r * k + q;
-        double val = sc * v[o];
-        if (diag) val += ptv[(size_t)ptrp[i] * bs * k + r * k + q];
-        v[o] = val;
-      }
-    }
+  const int a = agg[i], bk = bs * k, p0 = rp[i];
+  const int len = (rp[i + 1] - p0) * bk;
+  const double* __restrict__ pt = a >= 0 ? ptv + (size_t)ptrp[i] * bk : nullptr;  // P_tent's block of row i
+  double* __restrict__ vr = v + (size_t)p0 * bk;
+  for (int rel = lane; rel < len; rel += 32) {
+    const int p = p0 + rel / bk, e = rel % bk, r = e / k;
+    const double sc = -omega * dinv[(size_t)i * bs + r];
+    double val = sc * vr[rel];
+    if (ci[p] == a) val += pt[e];
+    vr[rel] = val;
   }
 }
 
@@ -981,9 +981,9 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       T.mark(0, s);  // waiting for lambda_max counts as its phase
       side.join(s);
       T.mark(3, s);
-      smooth_prolongator_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p,
-                                                                        L.n_rows, L.bs, k, L.dinv.p, L.consts.p,
-                                                                        L.agg.p, L.Pt.row_ptr.p, L.Pt.vals.p);
+      smooth_prolongator_kernel<<<grid_for((long long)L.n_rows * 32, TPB), TPB, 0, s>>>(
+          L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p, L.n_rows, L.bs, k, L.dinv.p, L.consts.p, L.agg.p, L.Pt.row_ptr.p,
+          L.Pt.vals.p);
       TAM_LAUNCH_CHECK();
       T.mark(4, s);
       bsr_transpose(L.P, L.R, s);
