@@ -616,8 +616,7 @@ static void plan_spop(SpOp& op, Bsr& A, Sell& S, LprStore& store, int spmv_fp64,
   bool df = use_df(A, spmv_fp64);
   op = SpOp{&A, &S, choose_lpr(A), df};
   if (op.lpr == 0) {
-    bsr_to_sell(A, S, s);
-    if (df) build_df_values(S, s);
+    bsr_to_sell(A, S, s, df);
     return;
   }
   op.tpr = rows_tpr(A.n_rows, A.nnzb, op.lpr);

@@ -528,10 +528,10 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
               "fem_assemble: a cell has non-positive or non-finite volume");
     M->dmask = DBuf<unsigned char>((size_t)n_nodes, s);
     TAM_CUDA(cudaMemcpyAsync(M->dmask.p, dmask, n_nodes, cudaMemcpyDeviceToDevice, s));
-    bsr_to_sell(A, M->S, s);
     // split copies for the double-float SpMV: SELL always (the CG's own SpMVs
-    // with K use it), the block-CSR only where K's operator runs on it
-    build_df_values(M->S, s);
+    // with K use it; written by the SELL fill), the block-CSR only where K's
+    // operator runs on it
+    bsr_to_sell(A, M->S, s, true);
     if (choose_lpr(A) != 0) build_df_values(A, s);
     TAM_CUDA(cudaStreamSynchronize(s));
   } catch (...) {

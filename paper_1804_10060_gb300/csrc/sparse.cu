@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(256) sell_sort_window_kernel(const int* __rest
 __global__ void sell_fill_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
                                  const double* __restrict__ vals, int n_rows, int n_slices, int bb,
                                  const int* __restrict__ slice_ptr, const int* __restrict__ perm,
-                                 int* __restrict__ scols, double* __restrict__ svals, bool with_pattern) {
+                                 int* __restrict__ scols, double* __restrict__ svals, float2* __restrict__ svals_df,
+                                 bool with_pattern) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int s = t >> 5, lane = t & 31;
   if (s >= n_slices) return;
@@ -65,14 +66,17 @@ __global__ void sell_fill_kernel(const int* __restrict__ row_ptr, const int* __r
   for (int k = 0; k < K; ++k) {
     size_t slot = (size_t)(k0 + k);
     if (with_pattern) scols[slot * 32 + lane] = k < len ? col_idx[rp + k] : lastc;
-    for (int e = 0; e < bb; ++e)
-      svals[(slot * bb + e) * 32 + lane] = k < len ? vals[((size_t)rp + k) * bb + e] : 0.0;
+    for (int e = 0; e < bb; ++e) {
+      const double x = k < len ? vals[((size_t)rp + k) * bb + e] : 0.0;
+      svals[(slot * bb + e) * 32 + lane] = x;
+      if (svals_df) svals_df[(slot * bb + e) * 32 + lane] = split_bits(x);  // the split copy in the same pass
+    }
   }
 }
 
 }  // namespace
 
-void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s) {
+void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s, bool df) {
   TAM_CHECK(A.n_cols > 0, TAM_ERR_INTERNAL, "SELL of a matrix without columns");
   S.n_rows = A.n_rows;
   S.br = A.br;
@@ -97,18 +101,18 @@ void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s) {
   }
   S.cols = DBuf<int>((size_t)S.n_slots * 32, s);
   S.vals = DBuf<double>((size_t)S.n_slots * 32 * A.block_elems(), s);
+  if (df) S.vals_df = DBuf<float2>((size_t)std::max(1LL, S.n_slots * 32 * (long long)A.block_elems()), s);
   sell_fill_kernel<<<grid_for((long long)S.n_slices * 32, 256), 256, 0, s>>>(
       A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, S.n_slices, (int)A.block_elems(),
-      S.slice_ptr.p, S.perm.p, S.cols.p, S.vals.p, true);
+      S.slice_ptr.p, S.perm.p, S.cols.p, S.vals.p, df ? S.vals_df.p : nullptr, true);
   TAM_LAUNCH_CHECK();
 }
 
 void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s) {
   sell_fill_kernel<<<grid_for((long long)S.n_slices * 32, 256), 256, 0, s>>>(
       A.row_ptr.p, A.col_idx.p, A.vals.p, A.n_rows, S.n_slices, (int)A.block_elems(),
-      S.slice_ptr.p, S.perm.p, S.cols.p, S.vals.p, false);
+      S.slice_ptr.p, S.perm.p, S.cols.p, S.vals.p, S.vals_df.p, false);
   TAM_LAUNCH_CHECK();
-  if (S.vals_df.p) build_df_values(S, s);
 }
 
 namespace {

@@ -135,7 +135,7 @@ void build_df_values(Sell& S, cudaStream_t s);
 void build_df_values(Bsr& B, cudaStream_t s);
 
 // Builds the SELL-32 copy of a Bsr (pattern + values).
-void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s);
+void bsr_to_sell(const Bsr& A, Sell& S, cudaStream_t s, bool df = false);  // df: the split copy too
 // Refreshes only the values of an existing SELL copy built from A (and its
 // split copy, when it has one).
 void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s);
