@@ -177,9 +177,10 @@ typedef struct amg_params {
   int spmv_fp64;           /* products of the solve's SpMVs (outer CG, V-cycle operators): 0 (default)
                               double-float, on split copies of the matrix values (same 8 bytes per
                               value, about 2^-47 relative, bound by memory instead of GB300's FP64
-                              pipe), for operators of at least 2^20 blocks and plain FP64 below;
-                              1 plain FP64 everywhere; 2 double-float everywhere.  Vectors and all
-                              other arithmetic stay FP64                                            */
+                              pipe), for operators of at least 2^20 blocks and for the coarse
+                              operators of a few long rows run with whole warps per row, plain FP64
+                              on the others; 1 plain FP64 everywhere; 2 double-float everywhere.
+                              Vectors and all other arithmetic stay FP64                            */
 } amg_params;
 
 /* Fills *p with the defaults above. */
