@@ -36,11 +36,10 @@ WORKLOAD = ("two-material box [0,4]x[0,1]^2, 256x64x64 hexes -> 6,291,456 P1 tet
 DIMS = (256, 64, 64)
 SAMPLE_DIMS = (96, 24, 24)      # bounded oracle sample (same structure, 181,875 DOF)
 FALLBACK_HBM_GBS = 6800.0       # recipe fallback when MEASURED_PEAKS.json is absent
-NOMINAL_FP64_TFLOPS = 1.25      # GB300 FP64 (nominal table)
-# DRAM bytes (read + write) of one double-float level-0 SpMV launch on the
-# 256x64x64 box: ncu capture of the same kernel on the 160x40x40 box (315.3 MB,
-# profiles/sell_spmv_box160x40x40.md) scaled by the block count (x 4.065).
-SPMV_DRAM_BYTES_FULL = 1.2815e9
+# DRAM bytes (read + write) of one launch of the dominant kernel (the level-0
+# Chebyshev step) on the 256x64x64 box, from an ncu capture of that launch at
+# full size (profiles/cheb_step_box256.md): 1,305,854,464 read + 47,776,256 written.
+CHEB_DRAM_BYTES_FULL = 1353630720
 
 
 def parse():
@@ -63,6 +62,9 @@ def parse():
                     help="run exactly one assemble+setup+solve (profiling target) and exit")
     ap.add_argument("--spmv-only", type=int, default=0, metavar="LAUNCHES",
                     help="assemble K and launch only the level-0 SpMV this many times (profiling target)")
+    ap.add_argument("--smooth-only", type=int, default=0, metavar="STEPS",
+                    help="assemble K, build the AMG and run only this many level-0 Chebyshev steps (profiling target)")
+    ap.add_argument("--fma", action="store_true", help="print the device's measured FP64/FP32 FMA throughput and exit")
     ap.add_argument("--summarize-ncu", default=None, metavar="CSV",
                     help="print a per-kernel summary (launches, time, share) of an ncu --csv launch list and exit")
     return ap.parse_args()
@@ -174,21 +176,22 @@ from paper_1804_10060_gb300 import meshgen
 from oracle import fem, amg
 pb = meshgen.slab_box_problem(*{dims!r})
 out = []
-for _ in range({reps}):
+for k in range({warm} + {reps}):
     t0 = time.perf_counter()
     K, f = fem.assemble_system(pb)
     H = amg.setup(K, fem.rigid_body_modes(pb.coords, pb.dirichlet_mask), 3)
     x, it, rel = amg.pcg(K, f, H, rtol=1e-8)
-    out.append(dict(t=time.perf_counter() - t0, it=it, rel=rel))
-print(json.dumps(dict(n_dof=pb.n_dof, runs=out)))
+    if k >= {warm}:
+        out.append(dict(t=time.perf_counter() - t0, it=it, rel=rel))
+print(json.dumps(dict(n_dof=pb.n_dof, warmup={warm}, runs=out)))
 """
 
 
-def run_oracle(reps, dims=SAMPLE_DIMS):
+def run_oracle(reps, dims=SAMPLE_DIMS, warm=0):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, dims=tuple(dims), reps=reps)
+    code = ORACLE_SNIPPET.format(root=ROOT, dims=tuple(dims), reps=reps, warm=warm)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed:\n" + r.stderr[-2000:])
@@ -249,9 +252,8 @@ def reference_arm(args):
     if rank != 0:
         return
     dims = SAMPLE_DIMS
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm state worth priming beyond one run below
-    res = run_oracle(max(args.steps, 1), dims)
+    # W untimed oracle runs, then K timed ones, in one fresh single-threaded process
+    res = run_oracle(max(args.steps, 1), dims, warm=max(args.warmup, 0))
     cb = cpu_baseline_obj(res, dims)
     ts = [x["t"] for x in res["runs"]]
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "DOF/s", "n_gpus": args.gpus,
@@ -329,39 +331,67 @@ def native_arm(args):
         phases = {"assemble_ms": ev[0].elapsed_time(ev[1]), "setup_ms": ev[1].elapsed_time(ev[2]),
                   "solve_ms": ev[2].elapsed_time(ev[3]), "solve_iterations": it,
                   "setup_phases_ms": {k: round(v, 3) for k, v in tam.amg_setup_stats(H).items()}}
-        # dominant kernel: level-0 SELL-32 FP64 block SpMV, timed alone with L2 flushed before each launch
         n, nnzb, _ = K.info()
+        solve_bytes = tam.amg_solve_bytes(H)
+        # dominant kernel: the level-0 Chebyshev step (one fused SpMV + smoother
+        # update; three of the five level-0 SpMVs of every PCG iteration), timed
+        # as 20 consecutive steps (each reads 1.37 GB, far more than L2)
         xs = torch.randn(n, 3, dtype=torch.float64, device="cuda")
         ys = torch.empty_like(xs)
-        reps = 20
-        tsum = 0.0
+        steps = 20
+        tam.amg_smooth(H, rhs, xs, steps, stream=stream)
+        cheb = []
+        for _ in range(5):
+            flush.fill_(2.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tam.amg_smooth(H, rhs, xs, steps, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            cheb.append(a.elapsed_time(b) / steps)
+        cheb_ms = statistics.median(cheb)
+        # the outer CG's SpMV with K (accurate double-float accumulation), timed alone with L2 flushed
         for _ in range(3):
             tam.tam_matrix_spmv(K, xs, ys, stream=stream)
-        for _ in range(reps):
+        outer = []
+        for _ in range(20):
             flush.fill_(2.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             tam.tam_matrix_spmv(K, xs, ys, stream=stream)
             b.record(stream)
             b.synchronize()
-            tsum += a.elapsed_time(b)
-        spmv_ms = tsum / reps
+            outer.append(a.elapsed_time(b))
+        spmv_ms = statistics.median(outer)
+        fma = tam.fma_throughput(stream=stream)
         H.destroy()
         K.destroy()
-    alg_bytes = nnzb * 76 + n * 48          # 72 B values + 4 B column per block; x read, y written
-    alg_flops = nnzb * 18                   # 9 multiply-adds per 3x3 block
     hbm_peak, hbm_src = peaks()
-    achieved_tf = alg_flops / (spmv_ms * 1e-3) / 1e12
-    achieved_gbs = alg_bytes / (spmv_ms * 1e-3) / 1e9
-    traffic = SPMV_DRAM_BYTES_FULL if dims == DIMS else None
-    # the SpMV multiplies in double-float on the FP32 pipe, so it is bound by
-    # memory; the FP64-equivalent rate is given against GB300's FP64 peak
-    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_source": hbm_src,
-                "kernel": "sell_spmv_kernel<3,3,EpiStore<3>,DF> (level-0 block SpMV, double-float products)",
-                "spmv_ms": spmv_ms, "alg_bytes": alg_bytes, "alg_flops": alg_flops,
-                "fp64_equivalent": {"achieved": achieved_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                                    "frac": achieved_tf / NOMINAL_FP64_TFLOPS}}
+    # algorithmic bytes: 72 B values + 4 B column per 3x3 block; per block row the
+    # Chebyshev step reads x, b, D^-1, d and writes d, x' (6 x 24 B), the plain
+    # SpMV reads x and writes y (2 x 24 B)
+    cheb_bytes = nnzb * 76 + n * 144
+    spmv_bytes = nnzb * 76 + n * 48
+    cheb_gbs = cheb_bytes / (cheb_ms * 1e-3) / 1e9
+    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    it = phases["solve_iterations"]
+    # the solve moves (iterations + 1) x the per-iteration bytes: the start does
+    # one residual SpMV and one V-cycle more
+    solve_gbs = solve_bytes["iteration"] * (it + 1) / (phases["solve_ms"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": cheb_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": cheb_gbs / hbm_peak, "traffic": CHEB_DRAM_BYTES_FULL if dims == DIMS else None,
+                "peak_source": hbm_src,
+                "kernel": "sell_spmv_kernel<3,3,EpiCheb<3>,DF> (level-0 Chebyshev step: fused block SpMV + "
+                          "smoother update, double-float products)",
+                "kernel_ms": cheb_ms, "alg_bytes": cheb_bytes,
+                "outer_spmv": {"kernel": "sell_spmv_kernel<3,3,EpiStore<3>,DF,ACC> (y = K x, accurate double-float "
+                                         "accumulation: the outer CG's product)",
+                               "ms": spmv_ms, "alg_bytes": spmv_bytes, "achieved": spmv_gbs,
+                               "frac": spmv_gbs / hbm_peak},
+                "solve_phase": {"bytes_per_iteration": solve_bytes["iteration"],
+                                "bytes_per_vcycle": solve_bytes["vcycle"], "iterations": it,
+                                "solve_ms": phases["solve_ms"], "achieved": solve_gbs, "frac": solve_gbs / hbm_peak},
+                "fma_tflops_measured": fma}
 
     # end to end through the host-buffer entry point (pinned host arrays)
     pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
@@ -755,6 +785,24 @@ def spmv_only(args):
     print(json.dumps({"spmv_only": args.spmv_only, "n": n, "nnzb": nnzb, "dims": dims}))
 
 
+def smooth_only(args):
+    """Assemble the box, build the AMG and run only level-0 Chebyshev steps (profiling target)."""
+    import torch
+
+    from paper_1804_10060_gb300 import meshgen
+    from paper_1804_10060_gb300 import thermoamg as tam
+    dims = tuple(int(x) for x in args.dims.split("x")) if args.dims else DIMS
+    pb = meshgen.slab_box_problem(*dims)
+    d = tam.problem_to_device(pb)
+    K, rhs = tam.fem_assemble_elasticity(**d)
+    H = tam.amg_setup(K, d["coords"])
+    x = torch.zeros_like(rhs)
+    tam.amg_smooth(H, rhs, x, args.smooth_only)
+    torch.cuda.synchronize()
+    n, nnzb, _ = K.info()
+    print(json.dumps({"smooth_only": args.smooth_only, "n": n, "nnzb": nnzb, "dims": dims}))
+
+
 def one_step(args):
     """Exactly one assemble + setup + solve of the workload (launch-list profiling target)."""
     import torch
@@ -780,6 +828,13 @@ def main():
         return
     if args.spmv_only:
         spmv_only(args)
+        return
+    if args.smooth_only:
+        smooth_only(args)
+        return
+    if args.fma:
+        from paper_1804_10060_gb300 import thermoamg as tam
+        print(json.dumps({"fma_tflops_measured": tam.fma_throughput()}))
         return
     if args.one_step:
         one_step(args)

@@ -58,6 +58,14 @@ const char* tam_last_error(void);
  * benchmarks; never fails. */
 long long tam_kernel_launches(void);
 
+/* Measured FMA throughput of the current device's FP64 and FP32 pipes in
+ * TFLOP/s (2 flops per FMA; best of 5 launches of 8 independent FMA chains
+ * per thread, 8 blocks of 256 threads per SM), into host doubles (either may
+ * be NULL).  Instrumentation: the rate that decides whether a matrix product
+ * is bound by memory or by the FP64 pipe; the paper has no counterpart.
+ * Synchronising.  Errors: INVALID_ARG, CUDA. */
+int tam_fma_throughput(double* fp64_tflops_host, double* fp32_tflops_host, void* stream);
+
 /* ------------------------------------------------------------------------
  * Assembly (Sec. 3, Eq. wf_elastic, steady, traction free; Eq. u-dbc).
  *
@@ -113,14 +121,17 @@ int tam_matrix_info(tam_matrix K, int* n_block_rows, long long* nnzb, int* block
  * vals[nnzb*9] (row-major 3x3 blocks).  Device pointers; synchronising. */
 int tam_matrix_export_bsr(tam_matrix K, int* row_ptr, int* col_idx, double* vals, void* stream);
 
-/* y = K x (x, y: [3n] float64 device vectors, must not overlap). */
+/* y = K x (x, y: [3n] float64 device vectors, must not overlap).  The
+ * product is the solve's own: double-float products on K's split values
+ * (see amg_params.spmv_fp64), FP64 vectors in and out. */
 int tam_matrix_spmv(tam_matrix K, const double* x, double* y, void* stream);
 
 /* ||b - K x||_2 into *norm_host (host double): the true residual of a
  * candidate displacement, the quantity the CG stopping test of Sec. 2.1 is
  * measured by.  b, x: [3n] float64 device vectors.  One fused SpMV + grid
- * reduction; its per-block partial sums live in scratch memory the call
- * allocates stream-ordered and frees again.  Synchronising.
+ * reduction in plain FP64 arithmetic; its per-block partial sums live in
+ * scratch memory the call allocates stream-ordered and frees again.
+ * Synchronising.
  * Errors: INVALID_ARG, OOM, CUDA. */
 int tam_matrix_residual_norm(tam_matrix K, const double* b, const double* x, double* norm_host,
                              void* stream);
@@ -136,7 +147,8 @@ int tam_matrix_residual_norm(tam_matrix K, const double* b, const double* x, dou
  *    larger K returns INVALID_ARG without launching anything.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) and caches it; make that call before any stream
- *    capture begins.
+ *    capture begins.  The cache does not survive cudaDeviceReset: do not call
+ *    this entry point on a device after resetting it.
  *  - All calls share the array: calls whose work overlaps on the GPU race.
  * b, x: [3n] float64 device vectors; *norm_host receives ||b - K x||_2.
  * Synchronising.  Errors: INVALID_ARG, CUDA. */
@@ -172,15 +184,21 @@ typedef struct amg_params {
   double strength_theta_scale; /* level l uses strength_theta * strength_theta_scale^l; default 0.5    */
   int setup_fp64;          /* products of the setup (A P_tent, A P, R (A P)) in plain FP64 arithmetic (1)
                               or in double-float, two FP32 values per operand with error-free transforms,
-                              about 2^-47 relative, faster on GB300 (0, default); double-float loses
-                              accuracy on operand entries below about 2^-100 in magnitude            */
+                              about 2^-47 relative, faster on GB300 (0, default)                     */
   int spmv_fp64;           /* products of the solve's SpMVs (outer CG, V-cycle operators): 0 (default)
                               double-float, on split copies of the matrix values (same 8 bytes per
-                              value, about 2^-47 relative, bound by memory instead of GB300's FP64
-                              pipe), for operators of at least 2^20 blocks and for the coarse
+                              value, each split to within 2^-49, bound by memory instead of GB300's
+                              FP64 pipe), for operators of at least 2^20 blocks and for the coarse
                               operators of a few long rows run with whole warps per row, plain FP64
                               on the others; 1 plain FP64 everywhere; 2 double-float everywhere.
-                              Vectors and all other arithmetic stay FP64                            */
+                              The outer CG's product with K accumulates accurately (within about
+                              1e-14 of sum_j |K_ij x_j| per row), the V-cycle's more loosely (a few
+                              1e-14).  Vectors and all other arithmetic stay FP64.
+                              Exponent range: double-float and the FP32 V-cycle need K's largest
+                              entry (over rows with off-diagonal blocks) within 2^-90..2^90; outside
+                              it amg_setup runs every product in FP64 (spmv_fp64 0 and setup_fp64 0
+                              fall back) and refuses spmv_fp64 = 2 and level_precision 1/2 with
+                              INVALID_ARG.  The loads may have any scale (see amg_pcg_solve)      */
 } amg_params;
 
 /* Fills *p with the defaults above. */
@@ -221,6 +239,41 @@ int amg_level_aggregates(tam_amg amg, int level, int* agg, void* stream);
 int amg_level_export(tam_amg amg, int level, int which, int* n_rows, int* n_cols, int* br, int* bc,
                      long long* nnzb, int* row_ptr, int* col_idx, double* vals, void* stream);
 
+/* SpMV layout the setup chose for one operator of `level` (which = 0 A_level,
+ * 1 P, 2 R), host ints: *kind 0 = SELL-32, one thread per block row; 1 =
+ * lanes per row over the interleaved lanes-per-row store; 2 = lanes per row
+ * over the block-CSR arrays; 3 = whole warps per row over the 8-lane store.
+ * *lanes = lanes (kinds 1, 2) or threads (kind 3) per row, 1 for kind 0;
+ * *df = 1 when its products run in double-float on split values.  The
+ * layouts differ only in arithmetic order, not in the operator (Sec. 2.1
+ * V-cycle); exposed so that parity tests can name the kernel they cover.
+ * Level 0's A is K (the outer CG's SpMV).  Errors: INVALID_ARG. */
+int amg_level_spmv_plan(tam_amg amg, int level, int which, int* kind, int* lanes, int* df);
+
+/* Algorithmic bytes of one V-cycle and of one PCG iteration (Sec. 2.1: CG
+ * preconditioned by the V-cycle), host doubles, either may be NULL: every
+ * array each kernel of this implementation must touch, counted once per
+ * kernel, without SELL padding or cache re-reads -- matrix values (8 B FP64 /
+ * double-float, 4 B FP32, 2 B BF16) and 4 B column indices per block, plus
+ * the vectors of the fused epilogues.  Per smoothed level: a zero-start
+ * Chebyshev step (4 vectors), 2*degree - 1 fused SpMV Chebyshev steps (matrix +
+ * 6 vectors), the residual (matrix + 3), restriction (R + fine + coarse
+ * vector), prolongation (P + coarse + 2 fine); the coarsest level's dense
+ * inverse (N^2 * 8 B); the outer CG adds K (8 B values) and 13 vectors of 3n
+ * FP64.  Divided by the measured time this gives the solve phase's achieved
+ * bandwidth.  Errors: INVALID_ARG. */
+int amg_solve_bytes(tam_amg amg, double* vcycle_bytes, double* iteration_bytes);
+
+/* x <- `degree` (1..64) Chebyshev-Jacobi steps on K x = b from the given x,
+ * over [cheb_lo, cheb_hi] * lambda_max(D^-1 K) of the hierarchy's parameters:
+ * the finest level's smoother of the V-cycle (Sec. 5.1, "Solver
+ * configuration"; Chebyshev with an estimated lambda_max), each step one fused
+ * SpMV kernel (res = D^-1 (b - K x), d = c_d d + c_r res, x += d) in the
+ * V-cycle's arithmetic.  b, x: [3n] device vectors, must not overlap.  The
+ * first call with a new degree uploads its coefficients (synchronising);
+ * later calls are asynchronous.  Errors: INVALID_ARG. */
+int amg_smooth(tam_amg amg, const double* b, double* x, int degree, void* stream);
+
 /* z = M^-1 r: one V-cycle (the preconditioner), r and z [3n] device. */
 int amg_vcycle(tam_amg amg, const double* r, double* z, void* stream);
 
@@ -228,7 +281,12 @@ int amg_vcycle(tam_amg amg, const double* r, double* z, void* stream);
  * recursively updated residual satisfies ||r||_2 <= max(rtol ||b||_2, atol)
  * or after max_iter iterations.  iters_out and final_rel_resid_out (host,
  * may be NULL) receive the iteration count and ||b - K x||_2 / ||b||_2
- * (recomputed at the end).  Synchronising (once per check interval).
+ * (recomputed at the end in plain FP64).  Internally the solve runs on b and
+ * x divided by a power of two chosen from ||b|| and K's largest entry, so that
+ * the vectors the double-float and FP32 products see sit inside FP32's
+ * exponent range whatever the units of the problem; the scaling is exact (in
+ * range the iterates are the unscaled ones times that power of two) and x is
+ * scaled back before return.  Synchronising (once per check interval).
  * Errors: NOT_CONVERGED (x holds the last iterate), BREAKDOWN,
  * INDEFINITE_PRECOND, NAN, INVALID_ARG, CUDA. */
 int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double atol, int max_iter,
@@ -239,7 +297,7 @@ int amg_destroy(tam_amg amg);
 
 /* ------------------------------------------------------------------------
  * Many load cases at once (an extension of the paper's per-load-case solve;
- * the paper reuses the elastic preconditioner across time steps, Sec. 6).
+ * the paper reuses the elastic preconditioner across time steps, Sec. 5.3).
  * Each system i (hierarchy amg[i]) has n_rhs[i] (1..16) right-hand sides,
  * B[i] and X[i] device arrays [n_rhs[i] x 3n_i] (one displacement vector per
  * row; X holds the initial guesses in, the solutions out).  Every right-hand

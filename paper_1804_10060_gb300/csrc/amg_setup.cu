@@ -721,7 +721,7 @@ static int aggregate(Level& L, int level, double theta, int distance, cudaStream
   const int n = A.n_rows;
   DBuf<double> nrm((size_t)A.nnzb, s), dnrm(n, s);
   DBuf<unsigned char> strong((size_t)A.nnzb, s), isolated(n, s), state(n, s);
-  block_norms_kernel<<<std::min<unsigned>(grid_for(A.nnzb, TPB), 152u * 16u), TPB, 0, s>>>(A.vals.p, A.nnzb,
+  block_norms_kernel<<<stride_grid(A.nnzb, TPB, 16), TPB, 0, s>>>(A.vals.p, A.nnzb,
                                                                                           (int)A.block_elems(), nrm.p);
   TAM_LAUNCH_CHECK();
   diag_norms_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, nrm.p, n, dnrm.p);
@@ -873,7 +873,26 @@ struct PhaseTimer {
   }
 };
 
-tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& prm, cudaStream_t s) {
+// The parameters the setup runs with: the double-float products (SpMV and
+// setup) need K's entries within 2^-kDfExpLimit..2^kDfExpLimit (FP32's
+// exponent range, with room for the products), so outside it the automatic
+// choices fall back to FP64 and the requests that need FP32 arithmetic are
+// refused with the range in the message.
+static amg_params effective_params(const tam_matrix_s* K, const amg_params& in) {
+  amg_params p = in;
+  TAM_CHECK(K->finite, TAM_ERR_INVALID_ARG, "amg_setup: K has an inf or NaN entry");
+  if (K->df_ok) return p;
+  const std::string why = "largest |K| entry is 2^" + std::to_string(K->vmax_exp) + "; FP32 arithmetic needs 2^-" +
+                          std::to_string(kDfExpLimit) + "..2^" + std::to_string(kDfExpLimit);
+  TAM_CHECK(p.spmv_fp64 != 2, TAM_ERR_INVALID_ARG, "amg_setup: spmv_fp64 = 2 (double-float SpMVs): " + why);
+  TAM_CHECK(p.level_precision == 0, TAM_ERR_INVALID_ARG, "amg_setup: level_precision 1/2 (FP32 V-cycle): " + why);
+  if (p.spmv_fp64 == 0) p.spmv_fp64 = 1;
+  p.setup_fp64 = 1;
+  return p;
+}
+
+tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& prm_in, cudaStream_t s) {
+  const amg_params prm = effective_params(K, prm_in);
   TAM_CHECK(prm.level_precision >= 0 && prm.level_precision <= 2, TAM_ERR_INVALID_ARG,
             "amg_setup: level_precision must be 0 (FP64), 1 (FP32) or 2 (FP32, BF16 finest values)");
   TAM_CHECK(prm.smoother_degree >= 1 && prm.smoother_degree <= 8 && prm.eig_iters >= 1 && prm.eig_iters <= 64 &&

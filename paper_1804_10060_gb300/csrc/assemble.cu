@@ -13,6 +13,8 @@
 // pattern: an element block K_ab with a free row a and a Dirichlet column b
 // is lifted straight into the load (f_a -= K_ab u_b) and rows of Dirichlet
 // nodes become identity rows -- the symmetric elimination of Eq. u-dbc.
+#include <cstdlib>
+
 #include "handles.cuh"
 #include "tet.cuh"
 
@@ -526,13 +528,18 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
     TAM_LAUNCH_CHECK();
     TAM_CHECK(read_back_int(flag.p, s) == 0, TAM_ERR_DEGENERATE_CELL,
               "fem_assemble: a cell has non-positive or non-finite volume");
+    {
+      operator_exponent_range(A, &M->vmax_exp, &M->finite, s);
+      M->df_ok = M->finite && std::abs(M->vmax_exp) <= kDfExpLimit;
+    }
     M->dmask = DBuf<unsigned char>((size_t)n_nodes, s);
     TAM_CUDA(cudaMemcpyAsync(M->dmask.p, dmask, n_nodes, cudaMemcpyDeviceToDevice, s));
     // split copies for the double-float SpMV: SELL always (the CG's own SpMVs
     // with K use it; written by the SELL fill), the block-CSR only where K's
     // operator runs on it
-    bsr_to_sell(A, M->S, s, true);
-    if (choose_lpr(A) != 0) build_df_values(A, s);
+    // (none when K is outside the double-float range: every product is FP64)
+    bsr_to_sell(A, M->S, s, M->df_ok);
+    if (M->df_ok && choose_lpr(A) != 0) build_df_values(A, s);
     TAM_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     delete M;

@@ -1,6 +1,7 @@
 // C ABI of the thermoamg library (declared in include/thermoamg.h).  Every
 // entry point converts internal exceptions into a status code and a message
 // for tam_last_error(); none aborts the process.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -219,6 +220,90 @@ int amg_level_export(tam_amg amg, int level, int which, int* n_rows, int* n_cols
       TAM_CHECK(col_idx && vals, TAM_ERR_INVALID_ARG, "amg_level_export: NULL array");
       export_bsr(*M, row_ptr, col_idx, vals, as_stream(stream));
     }
+    return TAM_OK;
+  });
+}
+
+int amg_level_spmv_plan(tam_amg amg, int level, int which, int* kind, int* lanes, int* df) {
+  return guarded([&] {
+    TAM_CHECK(amg && level >= 0 && level < (int)amg->levels.size() && which >= 0 && which <= 2,
+              TAM_ERR_INVALID_ARG, "amg_level_spmv_plan: bad argument");
+    const Level& L = amg->levels[level];
+    TAM_CHECK(which == 0 || L.n_agg > 0, TAM_ERR_INVALID_ARG, "amg_level_spmv_plan: the coarsest level has no P/R");
+    const SpOp& op = which == 0 ? L.Aop : which == 1 ? L.Pop : L.Rop;
+    int k = 0, ln = 0;
+    if (op.lpr == 0) {
+      k = 0;
+      ln = 1;
+    } else if (op.L && op.tpr) {
+      k = 3;
+      ln = op.tpr;
+    } else if (op.L) {
+      k = 1;
+      ln = op.lpr;
+    } else {
+      k = 2;
+      ln = op.lpr;
+    }
+    bool split = false;
+    if (op.lpr == 0) split = op.df && op.S && op.S->vals_df.p;
+    else if (op.L) split = op.df && op.L->vals_df.p;
+    else split = op.df && op.B && op.B->vals_df.p;
+    if (kind) *kind = k;
+    if (lanes) *lanes = ln;
+    if (df) *df = split ? 1 : 0;
+    return TAM_OK;
+  });
+}
+
+// Algorithmic bytes (the data the method itself must move, each array once per
+// kernel, no padding or re-reads) of one V-cycle and of one PCG iteration of
+// this implementation, from the hierarchy's sizes and precision.
+int amg_solve_bytes(tam_amg amg, double* vcycle_bytes, double* iteration_bytes) {
+  return guarded([&] {
+    TAM_CHECK(amg, TAM_ERR_INVALID_ARG, "amg_solve_bytes: NULL handle");
+    const int prec = amg->prm.level_precision;
+    const int nl = (int)amg->levels.size();
+    auto mat = [](const Bsr& B, double vb) { return (double)B.nnzb * ((double)B.br * B.bc * vb + 4.0); };
+    double v = 0.0;
+    for (int l = 0; l < nl; ++l) {
+      const Level& L = amg->levels[l];
+      const double ws = prec > 0 ? 4.0 : 8.0;                    // V-cycle vector word
+      const double n = (double)L.n_rows * L.bs;                  // this level's vector length
+      if (l == nl - 1) {                                         // dense inverse, b in, y out
+        v += (double)amg->n_coarse * amg->n_coarse * 8.0 + 2.0 * amg->n_coarse * ws;
+        break;
+      }
+      const double va = prec == 0 ? 8.0 : (prec == 2 && l == 0 ? 2.0 : 4.0);
+      const double vp = prec == 0 ? 8.0 : 4.0;
+      const double A = mat(*L.A, va), P = mat(L.P, vp), R = mat(L.R, vp);
+      const double nc = (double)L.P.n_cols * L.P.bc;
+      const int deg = std::max(L.deg, 1);
+      // pre-smoothing: first step from zero (b, dinv in; d, x out), deg - 1 fused
+      // SpMV steps (x, b, dinv, d in; d, x' out); residual (x, b in; t out);
+      // restriction (t in; b_c out); prolongation (x_c in; x in/out);
+      // post-smoothing: deg fused SpMV steps
+      v += 4.0 * n * ws;
+      v += (double)(2 * deg - 1) * (A + 6.0 * n * ws);
+      v += A + 3.0 * n * ws;
+      v += R + n * ws + nc * ws;
+      v += P + nc * ws + 2.0 * n * ws;
+    }
+    if (prec > 0) v += 2.0 * (double)amg->K->n_nodes * 3 * 4.0;  // FP64 r in / z out at level 0
+    // outer CG: q = K p (p in, q out), x/r update (x, r in/out; p, q in),
+    // r.z (r, z in), p = z + beta p (z in, p in/out)
+    const double n0 = (double)amg->K->n_nodes * 3;
+    const double it = v + mat(amg->K->A, 8.0) + 13.0 * n0 * 8.0;
+    if (vcycle_bytes) *vcycle_bytes = v;
+    if (iteration_bytes) *iteration_bytes = it;
+    return TAM_OK;
+  });
+}
+
+int amg_smooth(tam_amg amg, const double* b, double* x, int degree, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(amg && b && x && b != x, TAM_ERR_INVALID_ARG, "amg_smooth: bad argument");
+    smooth_fine(amg, b, x, degree, amg->prm.cheb_lo, amg->prm.cheb_hi, as_stream(stream));
     return TAM_OK;
   });
 }

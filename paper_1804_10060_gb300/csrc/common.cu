@@ -21,6 +21,22 @@ long long launches_total() { return g_launches.load(); }
 long long captured_and_reset() { long long c = g_captured; g_captured = 0; return c; }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cached[kMaxDev] = {};
+  int dev = 0;
+  TAM_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < kMaxDev) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int n = 0;
+  TAM_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  n = n > 0 ? n : 1;
+  if (dev >= 0 && dev < kMaxDev) cached[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
 const char* last_error_cstr() { return g_last_error.c_str(); }
 
 static void configure_pool_once() {

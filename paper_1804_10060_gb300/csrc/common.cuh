@@ -110,6 +110,15 @@ inline unsigned grid_for(long long n, int block) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Streaming multiprocessors of the current device (cached per device id).
+int sm_count();
+// Grid of a grid-stride vector kernel: `per_sm` blocks per SM at most.
+inline unsigned stride_grid(long long n, int block, int per_sm) {
+  const unsigned cap = (unsigned)sm_count() * (unsigned)per_sm;
+  const unsigned g = grid_for(n, block);
+  return g < cap ? g : cap;
+}
+
 // ---------------------------------------------------------------------------
 // Prefix sums: out[0..n] = exclusive scan of in[0..n), out[n] = total.
 // `in` and `out` may alias.  Returns nothing; total stays on the device.

@@ -9,6 +9,12 @@
 
 struct tam_matrix_s {
   int n_nodes = 0;
+  // floor(log2 max |K_ij|) over the rows with off-diagonal blocks, and whether
+  // K is finite and within the double-float range (|exponent| <= kDfExpLimit):
+  // else every product with K is plain FP64
+  int vmax_exp = 0;
+  bool finite = true;
+  bool df_ok = true;
   tam::Bsr A;                          // 3x3 blocks, Dirichlet rows are identity rows
   tam::Sell S;                         // SELL-32 copy used by every SpMV with K
   tam::DBuf<unsigned char> dmask;      // Dirichlet mask [n_nodes]
@@ -27,6 +33,7 @@ struct PcgScalars {
   int max_iter;
   int stop;         // nonzero: every solver kernel returns at entry
   int status;       // TAM_OK or a TAM_ERR_* code
+  int scale_exp;    // the solve runs on b 2^-scale_exp and x 2^-scale_exp (exact)
 };
 
 struct Level {
@@ -93,6 +100,7 @@ struct tam_amg_s {
   tam::DBuf<double> coarse_inv;          // [n_coarse * n_coarse]
   // PCG workspace
   tam::DBuf<double> r, z, p, q;
+  tam::DBuf<double> bs;                  // b scaled by the solve's power of two
   tam::DBuf<tam::PcgScalars> sc;
   tam::DBuf<double> partials;            // grid-reduction partials
   tam::DBuf<unsigned int> ticket;
@@ -104,6 +112,10 @@ struct tam_amg_s {
   cudaStream_t graph_stream = nullptr;
   long long graph_kernels = 0;           // kernel nodes in iter_exec
   double setup_ms[8] = {};               // setup phase times, see amg_setup_stats
+  // Chebyshev coefficients of the last smooth_fine call (degree, interval)
+  tam::DBuf<double> smooth_coef;
+  int smooth_deg = 0;
+  double smooth_lo = 0.0, smooth_hi = 0.0;
   std::unique_ptr<tam::MultiState> multi;  // multi-RHS workspace (built on first use)
   ~tam_amg_s();
 };

@@ -141,13 +141,13 @@ extern "C" int tam_learned_guess(tam_mlp_s* M, tam_amg H, const float* features,
     guess_to_x_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, Y.p, K->dmask.p, rhs, x);
     TAM_LAUNCH_CHECK();
     if (smooth_degree > 0) smooth_fine(H, rhs, x, smooth_degree, 0.1, 1.1, s);
-    DBuf<double> r((size_t)N, s), z((size_t)N, s), part(1216, s), out(2, s);
+    const unsigned g = stride_grid(N, 256, 8);
+    DBuf<double> r((size_t)N, s), z((size_t)N, s), part(g, s), out(2, s);
     DBuf<unsigned int> ticket(1, s);
     ticket.zero();
     GridReduce gr{part.p, ticket.p};
-    sell_spmv<3, 3>(K->S, x, EpiResidual<3>{rhs, r.p, n, nullptr}, s);
+    sell_spmv<3, 3>(K->S, x, EpiResidual<3>{rhs, r.p, n, nullptr}, s, K->df_ok);
     vcycle_apply(H, r.p, z.p, nullptr, s);
-    const unsigned g = std::min<unsigned>(grid_for(N, 256), 1216u);
     dot_kernel<<<g, 256, 0, s>>>(r.p, z.p, N, gr, out.p);
     TAM_LAUNCH_CHECK();
     vcycle_apply(H, rhs, z.p, nullptr, s);

@@ -304,8 +304,8 @@ size_t dense_mma_smem(int N) {
   return sizeof(__nv_bfloat16) * ((size_t)((N + 7) & ~7) * MMA_LD + (size_t)MMA_ROWS * MMA_LD);
 }
 
-unsigned ew_grid(long long n) { return std::min<unsigned>(grid_for(n, 256), 152u * 8u); }
-unsigned row_grid(long long n) { return std::min<unsigned>((unsigned)((n + ROWS - 1) / ROWS), 152u * 2u); }
+unsigned ew_grid(long long n) { return stride_grid(n, 256, 8); }
+unsigned row_grid(long long n) { return std::min<unsigned>((unsigned)((n + ROWS - 1) / ROWS), (unsigned)sm_count() * 2u); }
 
 size_t dense_smem(int K, int N) { return sizeof(float) * ((size_t)K * N + (size_t)ROWS * K); }
 
@@ -318,7 +318,7 @@ void dense(const float* A, long long n, int K, int N, const TW* W, const float* 
       const size_t smem = dense_mma_smem(N);
       TAM_CUDA(cudaFuncSetAttribute(dense_mma_kernel<MODE, STD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-      const unsigned grid = std::min<unsigned>((unsigned)((n + MMA_ROWS - 1) / MMA_ROWS), 152u * 8u);
+      const unsigned grid = std::min<unsigned>((unsigned)((n + MMA_ROWS - 1) / MMA_ROWS), (unsigned)sm_count() * 8u);
       dense_mma_kernel<MODE, STD><<<std::max(1u, grid), MMA_THREADS, smem, s>>>(
           A, n, K, N, W, bias, M->shift.p, M->scale.p, M->out_scale.p, out);
       TAM_LAUNCH_CHECK();
@@ -498,7 +498,7 @@ int tam_mlp_create(int n_in, int width, int depth, int n_out, unsigned long long
     TAM_CUDA(cudaMemcpy(M->shift.p, zero.data(), 4 * n_in, cudaMemcpyHostToDevice));
     TAM_CUDA(cudaMemcpy(M->scale.p, one.data(), 4 * n_in, cudaMemcpyHostToDevice));
     TAM_CUDA(cudaMemcpy(M->out_scale.p, one.data(), 4 * n_out, cudaMemcpyHostToDevice));
-    M->red = DBuf<double>(152 * 8 * 2, s);
+    M->red = DBuf<double>((size_t)sm_count() * 8 * 2, s);
     M->ticket = DBuf<unsigned int>(1, s);
     M->ticket.zero();
     TAM_CUDA(cudaStreamSynchronize(s));

@@ -23,9 +23,12 @@ namespace {
 constexpr int TPB = 256;
 constexpr int TMAX = 8;    // RHS per thread, compile-time register tile
 constexpr int MPMAX = 16;  // RHS per system
-enum { S_RHO = 0, S_ALPHA, S_BETA, S_RR, S_TOL2, S_BB, S_DONE, S_ITER };
+enum { S_RHO = 0, S_ALPHA, S_BETA, S_RR, S_TOL2, S_BB, S_DONE, S_ITER, S_SCALE, S_COUNT };
 
-unsigned vgrid(long long n) { return std::min<unsigned>(grid_for(n, TPB), 152u * 8u); }
+// 2^e for |e| <= 1000, built from its bits (exact)
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+unsigned vgrid(long long n) { return stride_grid(n, TPB, 8); }
 
 // -------------------------------------------------------------------------
 // layout conversion
@@ -38,12 +41,23 @@ __global__ void interleave_kernel(const double* __restrict__ src, double* __rest
   }
 }
 
+// back to one vector per RHS, undoing each RHS's power-of-two scaling
 __global__ void deinterleave_kernel(const double* __restrict__ src, double* __restrict__ dst, int m, int mp,
-                                    long long n3) {
+                                    long long n3, const double* __restrict__ sc) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n3 * m; e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e / n3);
     const long long i = e % n3;
-    dst[e] = src[i * mp + j];
+    dst[e] = src[i * mp + j] * pow2((int)sc[S_SCALE * mp + j]);
+  }
+}
+
+// b and x of every RHS into the solve's scaling (b 2^-e_j, x 2^-e_j; see mstart_kernel)
+__global__ void mscale_in_kernel(double* __restrict__ b, double* __restrict__ x, long long n3, int mp,
+                                 const double* __restrict__ sc) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n3 * mp; e += (long long)gridDim.x * blockDim.x) {
+    const double f = pow2(-(int)sc[S_SCALE * mp + (int)(e % mp)]);
+    b[e] *= f;
+    x[e] *= f;
   }
 }
 
@@ -54,8 +68,13 @@ __device__ bool reduce_rhs(GridReduce gr, double (&v)[MPMAX], double (&tot)[MPMA
   return grid_reduce<MPMAX>(gr, v, tot, sh);
 }
 
+// Per RHS: ||b||^2, and the power of two e_j the solve divides b_j and x_j by
+// (b_j's RMS entry moved to about 2^half_exp, half K's largest entry exponent,
+// so that every vector the double-float and FP32 products see stays far inside
+// FP32's exponent range; exact, see pcg_solve); tolerances in scaled units.
 __global__ void mstart_kernel(const double* __restrict__ b, long long n3, int m, int mp, double rtol, double atol,
-                              int max_iter, GridReduce gr, double* __restrict__ sc, int* __restrict__ flags) {
+                              int max_iter, int half_exp, GridReduce gr, double* __restrict__ sc,
+                              int* __restrict__ flags) {
   __shared__ double sh[32];
   double acc[MPMAX];
 #pragma unroll
@@ -70,8 +89,15 @@ __global__ void mstart_kernel(const double* __restrict__ b, long long n3, int m,
   double tot[MPMAX];
   if (reduce_rhs(gr, acc, tot, sh) && threadIdx.x == 0) {
     for (int j = 0; j < mp; ++j) {
-      sc[S_BB * mp + j] = tot[j];
-      const double t = fmax(rtol * sqrt(tot[j]), atol);
+      int e = 0;
+      if (tot[j] > 0.0 && isfinite(tot[j])) {
+        e = ilogb(sqrt(tot[j] / (double)n3)) - half_exp;
+        e = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+      }
+      const double inv = pow2(-e);
+      sc[S_SCALE * mp + j] = (double)e;
+      sc[S_BB * mp + j] = tot[j] * inv * inv;
+      const double t = fmax(rtol * sqrt(tot[j]), atol) * inv;
       sc[S_TOL2 * mp + j] = t * t;
       sc[S_DONE * mp + j] = j < m ? 0.0 : 1.0;
       sc[S_ITER * mp + j] = 0.0;
@@ -335,10 +361,12 @@ struct EpiStoreKM {
   }
 };
 
+// df: the double-float kernel on K's split values (the hierarchy's level-0
+// choice, amg_params.spmv_fp64); false: plain FP64.
 template <class Epi>
-void kspmm(const Sell& S, const double* x, int mp, int tm, Epi epi, cudaStream_t s) {
+void kspmm(const Sell& S, const double* x, int mp, int tm, Epi epi, cudaStream_t s, bool df) {
   dim3 g(sell_grid(S), mp / tm);
-  if (S.vals_df.p)
+  if (df && S.vals_df.p)
     kspmm_kernel<Epi, true><<<g, SPMV_THREADS, 0, s>>>(view(S), x, mp, tm, epi);
   else
     kspmm_kernel<Epi, false><<<g, SPMV_THREADS, 0, s>>>(view(S), x, mp, tm, epi);
@@ -659,7 +687,7 @@ void autotune(tam_amg_s* H, cudaStream_t s) {
   const int mp = MS.mp;
   auto t0 = std::chrono::steady_clock::now();
   MS.tmK = pick_tm(mp, [&](int tm) {
-    kspmm(H->K->S, MS.p.p, mp, tm, EpiStoreKM{MS.q.p, H->K->n_nodes, mp}, s);
+    kspmm(H->K->S, MS.p.p, mp, tm, EpiStoreKM{MS.q.p, H->K->n_nodes, mp}, s, H->levels[0].Aop.df);
   }, s);
   for (size_t l = 0; l + 1 < H->levels.size(); ++l) {
     Level& L = H->levels[l];
@@ -698,10 +726,10 @@ void ensure_multi(tam_amg_s* H, int mp, cudaStream_t s) {
     *v = DBuf<double>(n3 * mp, s);
     v->zero();
   }
-  MS.sc = DBuf<double>(8 * (size_t)mp, s);
+  MS.sc = DBuf<double>(S_COUNT * (size_t)mp, s);
   MS.flags = DBuf<int>(4, s);
   MS.flags.zero();
-  const unsigned g = std::max<unsigned>(sell_grid(H->K->S), 152u * 8u);
+  const unsigned g = std::max<unsigned>(sell_grid(H->K->S), (unsigned)sm_count() * 8u);
   MS.partials = DBuf<double>((size_t)g * std::max(TMAX, MPMAX) * (MPMAX / 1 + 1), s);
   MS.tickets = DBuf<unsigned int>(MPMAX + 1, s);
   MS.tickets.zero();
@@ -723,7 +751,7 @@ void enqueue_multi_iteration(tam_amg_s* H, cudaStream_t s) {
   const long long n3 = (long long)H->K->n_nodes * 3;
   int* flags = MS.flags.p;
   GridReduce gk{MS.partials.p, MS.tickets.p};
-  kspmm(H->K->S, MS.p.p, mp, MS.tmK, EpiPqM{MS.p.p, MS.q.p, H->K->n_nodes, mp, gk, MS.sc.p, flags}, s);
+  kspmm(H->K->S, MS.p.p, mp, MS.tmK, EpiPqM{MS.p.p, MS.q.p, H->K->n_nodes, mp, gk, MS.sc.p, flags}, s, H->levels[0].Aop.df);
   GridReduce ge{MS.partials.p, MS.tickets.p + MPMAX};
   mupdate_kernel<<<vgrid(n3), TPB, 0, s>>>(MS.x.p, MS.r.p, MS.p.p, MS.q.p, n3, mp, ge, MS.sc.p, flags);
   TAM_LAUNCH_CHECK();
@@ -745,11 +773,14 @@ void start_multi(tam_amg_s* H, int m, const double* B, const double* X, double r
   interleave_kernel<<<vgrid(n3 * mp), TPB, 0, s>>>(X, MS.x.p, m, mp, n3);
   TAM_LAUNCH_CHECK();
   GridReduce ge{MS.partials.p, MS.tickets.p + MPMAX};
-  mstart_kernel<<<vgrid(n3), TPB, 0, s>>>(MS.b.p, n3, m, mp, rtol, atol, max_iter, ge, MS.sc.p, MS.flags.p);
+  mstart_kernel<<<vgrid(n3), TPB, 0, s>>>(MS.b.p, n3, m, mp, rtol, atol, max_iter, H->K->vmax_exp / 2, ge, MS.sc.p,
+                                          MS.flags.p);
+  TAM_LAUNCH_CHECK();
+  mscale_in_kernel<<<vgrid(n3 * mp), TPB, 0, s>>>(MS.b.p, MS.x.p, n3, mp, MS.sc.p);
   TAM_LAUNCH_CHECK();
   GridReduce gk{MS.partials.p, MS.tickets.p};
   kspmm(H->K->S, MS.x.p, mp, MS.tmK,
-        EpiResInitM{MS.b.p, MS.r.p, H->K->n_nodes, mp, gk, MS.sc.p, nullptr, MS.flags.p}, s);
+        EpiResInitM{MS.b.p, MS.r.p, H->K->n_nodes, mp, gk, MS.sc.p, nullptr, MS.flags.p}, s, H->levels[0].Aop.df);
   mcheck_kernel<<<1, 32, 0, s>>>(MS.sc.p, mp, MS.flags.p);
   TAM_LAUNCH_CHECK();
   mvcycle<double, double>(H, 0, MS.r.p, MS.z.p, MS.flags.p, s);
@@ -763,11 +794,12 @@ int finish_multi(tam_amg_s* H, int m, const double* B, double* X, int* iters, do
   const long long n3 = (long long)H->K->n_nodes * 3;
   DBuf<double> rn(mp, s);
   GridReduce gk{MS.partials.p, MS.tickets.p};
+  // the reported true residual is always a plain FP64 product
   kspmm(H->K->S, MS.x.p, mp, MS.tmK, EpiResInitM{MS.b.p, nullptr, H->K->n_nodes, mp, gk, MS.sc.p, rn.p, MS.flags.p},
-        s);
-  deinterleave_kernel<<<vgrid(n3 * m), TPB, 0, s>>>(MS.x.p, X, m, mp, n3);
+        s, false);
+  deinterleave_kernel<<<vgrid(n3 * m), TPB, 0, s>>>(MS.x.p, X, m, mp, n3, MS.sc.p);
   TAM_LAUNCH_CHECK();
-  std::vector<double> sc(8 * (size_t)mp), r2(mp);
+  std::vector<double> sc(S_COUNT * (size_t)mp), r2(mp);
   int flags[4];
   TAM_CUDA(cudaMemcpyAsync(sc.data(), MS.sc.p, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, s));
   TAM_CUDA(cudaMemcpyAsync(r2.data(), rn.p, sizeof(double) * mp, cudaMemcpyDeviceToHost, s));
@@ -802,6 +834,10 @@ int pcg_solve_batch(int n_sys, tam_amg_s* const* H, const int* m, const double* 
               "batch solve: each system needs a hierarchy and 1..16 right-hand sides");
   for (int i = 0; i < n_sys; ++i)
     for (int k = 0; k < i; ++k) TAM_CHECK(H[i] != H[k], TAM_ERR_INVALID_ARG, "batch solve: a hierarchy appears twice");
+  for (int i = 0; i < n_sys; ++i)
+    TAM_CHECK(H[i]->K->df_ok, TAM_ERR_INVALID_ARG,
+              "batch solve: the FP32 V-cycle needs K's largest entry within 2^-" + std::to_string(kDfExpLimit) +
+                  "..2^" + std::to_string(kDfExpLimit) + " (it is 2^" + std::to_string(H[i]->K->vmax_exp) + ")");
   for (int i = 0; i < n_sys; ++i) start_multi(H[i], m[i], B[i], X[i], rtol, atol, max_iter, s);
   // one graph: every system's iteration on its own branch, joined, then a
   // flag telling whether all systems have stopped

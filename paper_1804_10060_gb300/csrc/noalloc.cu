@@ -12,7 +12,13 @@
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress (with that device current) and caches it; make
-// that first call before any stream capture begins.
+// that first call before any stream capture begins.  The cached address
+// belongs to the device's primary context: after cudaDeviceReset the array
+// lives at an address the cache does not know, so a process that resets a
+// device must not call this entry point on it again.
+//
+// The product is plain FP64 (the split copy of K is not used), like
+// tam_matrix_residual_norm's.
 //
 // The array is TAM_NOALLOC_MAX_BLOCKS + 2 doubles (128 KiB) and stays
 // resident on every device that loads the library until the process exits.
@@ -94,7 +100,7 @@ extern "C" int tam_matrix_residual_norm_noalloc(tam_matrix K, const double* b, c
     // the ticket must start at zero (a previous call may have been cut short)
     TAM_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s));
     GridReduce gr{scratch, ticket};
-    sell_spmv<3, 3>(K->S, x, EpiResNormStatic<3>{b, K->n_nodes, gr, out}, s);
+    sell_spmv<3, 3>(K->S, x, EpiResNormStatic<3>{b, K->n_nodes, gr, out}, s, /*df=*/false);
     double r2 = 0.0;
     TAM_CUDA(cudaMemcpyAsync(&r2, out, sizeof(double), cudaMemcpyDeviceToHost, s));
     TAM_CUDA(cudaStreamSynchronize(s));

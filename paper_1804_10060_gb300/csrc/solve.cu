@@ -79,16 +79,34 @@ __global__ void dense_gemv_kernel(const double* __restrict__ A, const double* __
 // ---------------------------------------------------------------------------
 // PCG kernels
 // ---------------------------------------------------------------------------
+// 2^e for |e| <= 1000, built from its bits (exact)
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// The power of two the solve divides b and x by: b's RMS entry moves to about
+// 2^half_exp, half K's largest entry exponent, so that the solution-like
+// vectors (about b / |K|) sit near 2^-half_exp and every vector the
+// double-float SpMVs split stays far inside FP32's exponent range.  Scaling by
+// a power of two is exact, so in range the iterates are the unscaled ones
+// times 2^-e bit for bit.
+__device__ __forceinline__ int centering_exp(double bb, long long N, int half_exp) {
+  if (!(bb > 0.0) || !isfinite(bb) || N <= 0) return 0;
+  const int e = ilogb(sqrt(bb / (double)N)) - half_exp;
+  return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+}
+
 __global__ void pcg_start_kernel(const double* __restrict__ b, long long N, GridReduce gr, PcgScalars* sc,
-                                 double rtol, double atol, int max_iter) {
+                                 double rtol, double atol, int max_iter, int half_exp) {
   __shared__ double sh[32];
   double acc[1] = {0.0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     acc[0] += b[i] * b[i];
   double tot[1];
   if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) {
-    sc->bb = tot[0];
-    double t = fmax(rtol * sqrt(tot[0]), atol);
+    const int e = centering_exp(tot[0], N, half_exp);
+    const double inv = pow2(-e);
+    sc->scale_exp = e;
+    sc->bb = tot[0] * inv * inv;
+    double t = fmax(rtol * sqrt(tot[0]), atol) * inv;
     sc->tol2 = t * t;
     sc->iter = 0;
     sc->max_iter = max_iter;
@@ -97,6 +115,16 @@ __global__ void pcg_start_kernel(const double* __restrict__ b, long long N, Grid
     sc->rho = sc->alpha = sc->beta = 0.0;
     sc->rr = 0.0;
   }
+}
+
+// dst = src 2^(dir * scale_exp) (dst may be src): into and out of the solve's scaling
+__global__ void pcg_scale_kernel(const double* __restrict__ src, double* __restrict__ dst, long long N,
+                                 const PcgScalars* __restrict__ sc, int dir) {
+  const int e = sc->scale_exp;
+  if (e == 0 && src == dst) return;
+  const double f = pow2(dir * e);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i] * f;
 }
 
 // r = b - K x and ||r||^2 -> stop if already converged
@@ -228,7 +256,7 @@ struct EpiResNorm {
   }
 };
 
-unsigned vec_grid(long long N) { return std::min<unsigned>(grid_for(N, TPB), 152u * 8u); }
+unsigned vec_grid(long long N) { return stride_grid(N, TPB, 8); }
 
 // ---------------------------------------------------------------------------
 // Dispatch on block shapes (3x3, 6x6 for A; 3x6, 6x3, 6x6, 3x3 for P and R)
@@ -324,7 +352,8 @@ void precondition(tam_amg_s* H, const double* r, double* z, const int* stop, cud
 
 void spmv_outer_pq(tam_amg_s* H, cudaStream_t s) {
   GridReduce gr{H->partials.p, H->ticket.p};
-  sell_spmv<3, 3>(H->K->S, H->p.p, EpiPq<3>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s, H->levels[0].Aop.df);
+  sell_spmv<3, 3>(H->K->S, H->p.p, EpiPq<3>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s, H->levels[0].Aop.df,
+                  /*acc=*/true);
 }
 
 void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
@@ -344,7 +373,7 @@ void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
 }  // namespace
 
 void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s) {
-  sell_spmv<3, 3>(K->S, x, EpiStore<3>{y, K->n_nodes, nullptr}, s);
+  sell_spmv<3, 3>(K->S, x, EpiStore<3>{y, K->n_nodes, nullptr}, s, K->df_ok, /*acc=*/true);
 }
 
 double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaStream_t s) {
@@ -353,7 +382,7 @@ double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaSt
   DBuf<unsigned int> ticket(1, s);
   ticket.zero();
   GridReduce gr{partials.p, ticket.p};
-  sell_spmv<3, 3>(K->S, x, EpiResNorm<3>{b, K->n_nodes, gr, out.p}, s);
+  sell_spmv<3, 3>(K->S, x, EpiResNorm<3>{b, K->n_nodes, gr, out.p}, s, /*df=*/false);
   return std::sqrt(read_back_double(out.p, s));
 }
 
@@ -367,9 +396,17 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   const long long N = (long long)H->K->n_nodes * 3;
   GridReduce gr{H->partials.p, H->ticket.p};
   PcgScalars* sc = H->sc.p;
-  pcg_start_kernel<<<vec_grid(N), TPB, 0, s>>>(b, N, gr, sc, rtol, atol, max_iter);
+  if (!H->bs.p) H->bs = DBuf<double>((size_t)N, s);
+  // the solve runs on b 2^-e and x 2^-e (e from ||b|| and K's range, see centering_exp)
+  pcg_start_kernel<<<vec_grid(N), TPB, 0, s>>>(b, N, gr, sc, rtol, atol, max_iter, H->K->vmax_exp / 2);
   TAM_LAUNCH_CHECK();
-  sell_spmv<3, 3>(H->K->S, x, EpiInitResidual<3>{b, H->r.p, H->K->n_nodes, gr, sc}, s, H->levels[0].Aop.df);
+  pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(b, H->bs.p, N, sc, -1);
+  TAM_LAUNCH_CHECK();
+  pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(x, x, N, sc, -1);
+  TAM_LAUNCH_CHECK();
+  b = H->bs.p;
+  sell_spmv<3, 3>(H->K->S, x, EpiInitResidual<3>{b, H->r.p, H->K->n_nodes, gr, sc}, s, H->levels[0].Aop.df,
+                  /*acc=*/true);
   precondition(H, H->r.p, H->z.p, &sc->stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, sc, 1);
   TAM_LAUNCH_CHECK();
@@ -419,9 +456,11 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
     TAM_CUDA(cudaStreamSynchronize(s));
     if (*reinterpret_cast<int*>(hs.ll)) break;
   }
-  // final true residual
+  // final true residual, always a plain FP64 product; then x back to the caller's scale
   DBuf<double> rn(1, s);
-  sell_spmv<3, 3>(H->K->S, x, EpiResNorm<3>{b, H->K->n_nodes, gr, rn.p}, s, H->levels[0].Aop.df);
+  sell_spmv<3, 3>(H->K->S, x, EpiResNorm<3>{b, H->K->n_nodes, gr, rn.p}, s, /*df=*/false);
+  pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(x, x, N, sc, +1);
+  TAM_LAUNCH_CHECK();
   PcgScalars host;
   TAM_CUDA(cudaMemcpyAsync(&host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   double rr = read_back_double(rn.p, s);  // synchronises the stream
@@ -441,14 +480,21 @@ void smooth_fine(tam_amg_s* H, const double* b, double* x, int degree, double lo
   TAM_CHECK(degree >= 1 && degree <= 64 && hi > lo && lo > 0, TAM_ERR_INVALID_ARG, "smooth_fine: bad degree or interval");
   Level& L = H->levels[0];
   const long long N = (long long)L.n_rows * L.bs;
-  const std::vector<double> c = cheb_coefficients(lo * L.lambda_host, hi * L.lambda_host, degree);
-  DBuf<double> coef(c.size(), s);
-  TAM_CUDA(cudaMemcpyAsync(coef.p, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice, s));
-  TAM_CUDA(cudaStreamSynchronize(s));  // c is a host temporary
+  if (H->smooth_deg != degree || H->smooth_lo != lo || H->smooth_hi != hi) {
+    // coefficients kept on the device for repeated calls with the same polynomial
+    const std::vector<double> c = cheb_coefficients(lo * L.lambda_host, hi * L.lambda_host, degree);
+    H->smooth_coef = DBuf<double>(c.size(), s);
+    TAM_CUDA(cudaMemcpyAsync(H->smooth_coef.p, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice, s));
+    TAM_CUDA(cudaStreamSynchronize(s));  // c is a host temporary
+    H->smooth_deg = degree;
+    H->smooth_lo = lo;
+    H->smooth_hi = hi;
+  }
+  const double* coef = H->smooth_coef.p;
   double* cur = x;
   double* nxt = L.xb.p;
   for (int k = 0; k < degree; ++k) {
-    spop_apply<3, 3>(L.Aop, cur, EpiCheb<3>{b, cur, L.dinv.p, coef.p + 2 + 2 * k, L.d.p, nxt, L.n_rows, nullptr}, s);
+    spop_apply<3, 3>(L.Aop, cur, EpiCheb<3>{b, cur, L.dinv.p, coef + 2 + 2 * k, L.d.p, nxt, L.n_rows, nullptr}, s);
     std::swap(cur, nxt);
   }
   if (cur != x) TAM_CUDA(cudaMemcpyAsync(x, cur, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, s));

@@ -116,6 +116,48 @@ void sell_refresh_values(const Bsr& A, Sell& S, cudaStream_t s) {
 }
 
 namespace {
+// Largest biased FP64 exponent (out[0]; 0: none) of the entries of a
+// block-CSR matrix and an inf/NaN flag (out[1]), leaving out rows that hold only their diagonal block (Dirichlet and cell-less nodes:
+// identity rows whose 1.0 says nothing about the operator's scale); inf/NaN
+// are flagged in every row.
+__global__ void row_exponent_range_kernel(const int* __restrict__ rp, const double* __restrict__ v, int n_rows,
+                                          int bb, int* __restrict__ out) {
+  int emax = 0, bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_rows; i += gridDim.x * blockDim.x) {
+    const int p0 = rp[i], p1 = rp[i + 1];
+    const bool scale_row = p1 - p0 > 1;
+    for (long long k = (long long)p0 * bb; k < (long long)p1 * bb; ++k) {
+      const int e = (int)(((unsigned long long)__double_as_longlong(v[k]) >> 52) & 0x7ff);
+      if (e == 0x7ff) bad = 1;
+      else if (scale_row) emax = max(emax, e);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (emax) atomicMax(out, emax);
+    if (bad) atomicOr(out + 1, 1);
+  }
+}
+}  // namespace
+
+void operator_exponent_range(const Bsr& A, int* max_exp, bool* finite, cudaStream_t s) {
+  DBuf<int> out(2, s);
+  out.zero();
+  if (A.n_rows > 0) {
+    row_exponent_range_kernel<<<stride_grid(A.n_rows, 256, 8), 256, 0, s>>>(A.row_ptr.p, A.vals.p, A.n_rows,
+                                                                           (int)A.block_elems(), out.p);
+    TAM_LAUNCH_CHECK();
+  }
+  int e = 0, bad = 0;
+  read_back_int2(out.p, out.p + 1, &e, &bad, s);
+  *max_exp = e ? e - 1023 : 0;
+  *finite = bad == 0;
+}
+
+namespace {
 __global__ void split_values_kernel(const double* __restrict__ in, float2* __restrict__ out, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = split_bits(in[i]);
@@ -124,7 +166,7 @@ __global__ void split_values_kernel(const double* __restrict__ in, float2* __res
 void split_into(const double* in, long long n, DBuf<float2>& out, cudaStream_t s) {
   if (out.n != (size_t)std::max(1LL, n)) out = DBuf<float2>((size_t)std::max(1LL, n), s);
   if (n > 0) {
-    split_values_kernel<<<std::min<unsigned>(grid_for(n, 256), 152u * 16u), 256, 0, s>>>(in, out.p, n);
+    split_values_kernel<<<stride_grid(n, 256, 16), 256, 0, s>>>(in, out.p, n);
     TAM_LAUNCH_CHECK();
   }
 }
@@ -964,7 +1006,7 @@ void convert_values(const SpOp& op, DBuf<T>& out, cudaStream_t s) {
   }
   out = DBuf<T>((size_t)std::max(1LL, n), s);
   if (n > 0) {
-    convert_kernel<T><<<std::min<unsigned>(grid_for(n, 256), 152u * 16u), 256, 0, s>>>(src, out.p, n);
+    convert_kernel<T><<<stride_grid(n, 256, 16), 256, 0, s>>>(src, out.p, n);
     TAM_LAUNCH_CHECK();
   }
 }

@@ -28,12 +28,16 @@ namespace tam {
 // IEEE-754 bit manipulations (integer pipe only: GB300's FP64 pipe, which also
 // executes FP64<->FP32 conversions, is the scarce resource here).
 //
-// split_bits: v = hi + lo exactly up to the last 5 bits of the 29 mantissa
-// bits below hi's 24 (relative error <= 2^-47): hi keeps the sign, the
-// exponent and the top 23 stored mantissa bits of v (truncation); lo is the
-// remaining 29-bit tail, normalised and truncated to 24 bits.  |v| < 2^-126
-// (zero, FP64 values below FP32's normal range) gives (0, 0); a tail below
-// FP32's normal range gives lo = 0.
+// split_bits: v = hi + lo with hi = v rounded to FP32's 24-bit significand
+// (to nearest on the first discarded bit) and lo = v - hi (at most 29 bits,
+// |lo| <= 2^-24 |v|) rounded to 24 bits the same way: |v - hi - lo| <=
+// 2^-49 |v| for 2^-78 <= |v| < 2^126, with no sign bias.  Below 2^-78 the
+// remainder may fall under FP32's normal range and is dropped (absolute error
+// < 2^-126); |v| < 2^-126 (zero, FP64 values below FP32's normal range)
+// gives (0, 0) and values that round to 2^128 give (+-inf, 0).  The library
+// splits only matrices whose largest entry lies within 2^-90..2^90
+// (kDfExpLimit), with the CG vectors scaled by a power of two to match (see
+// pcg_solve), so that products and sums stay far from both ends.
 __device__ __forceinline__ float2 split_bits(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned sign = (unsigned)(b >> 63) << 31;
@@ -41,14 +45,27 @@ __device__ __forceinline__ float2 split_bits(double v) {
   if (ef <= 0) return make_float2(0.f, 0.f);
   if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
   const unsigned long long m = b & 0xfffffffffffffull;
-  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(m >> 29));
-  const unsigned low = (unsigned)(m & 0x1fffffffull);  // weight 2^(E - 52) per unit
-  if (low == 0) return make_float2(hi, 0.f);
-  const int lz = __clz(low);                            // 3..31
-  const int el = ef - 52 + (31 - lz);                   // FP32 biased exponent of lo
+  const unsigned up = (unsigned)(m >> 28) & 1u;            // first bit below hi's 24
+  // a carry out of the significand moves into the exponent field (2^128 -> inf)
+  const unsigned hb = (((unsigned)ef << 23) | (unsigned)(m >> 29)) + up;
+  const float hi = __uint_as_float(sign | (hb < 0x7f800000u ? hb : 0x7f800000u));
+  // v - hi in units of 2^(E - 52): the 29-bit tail, less 2^29 when hi was rounded up
+  const int t = (int)(m & 0x1fffffffull) - (int)(up << 29);
+  if (t == 0) return make_float2(hi, 0.f);
+  const unsigned at = (unsigned)(t < 0 ? -t : t);           // 1 .. 2^28
+  const unsigned lsign = t < 0 ? (sign ^ 0x80000000u) : sign;
+  const int nb = 32 - __clz(at);                            // significant bits of the tail, 1..29
+  int el = ef - 53 + nb;                                    // FP32 biased exponent of lo
+  unsigned mant;
+  if (nb <= 24) {
+    mant = at << (24 - nb);
+  } else {
+    const int sh = nb - 24;                                  // 1..5 bits dropped, rounded to nearest
+    mant = (at + (1u << (sh - 1))) >> sh;
+    if (mant >> 24) { mant >>= 1; ++el; }
+  }
   if (el <= 0) return make_float2(hi, 0.f);
-  const unsigned frac = (unsigned)(((unsigned long long)low << (lz + 1)) & 0xffffffffull) >> 9;
-  return make_float2(hi, __uint_as_float(sign | ((unsigned)el << 23) | frac));
+  return make_float2(hi, __uint_as_float(lsign | ((unsigned)el << 23) | (mant & 0x7fffffu)));
 }
 
 // Exact FP32 -> FP64 (zero and FP32 subnormals give 0; inf/nan keep their class).
@@ -77,6 +94,23 @@ __device__ __forceinline__ void df_fma(float2& a, float2 x, float2 y) {
   a.y = __fadd_rn(a.y, __fadd_rn(err, e));
 }
 
+// a += b for two unevaluated sums, accurately: TwoSum of the high parts and
+// of the low parts, renormalised twice (the result keeps about 2^-48 of |a + b|)
+__device__ __forceinline__ void df_add_acc(float2& a, float2 b) {
+  float sh = __fadd_rn(a.x, b.x);
+  float bp = __fadd_rn(sh, -a.x);
+  float sl = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(sh, -bp)), __fadd_rn(b.x, -bp));
+  const float th = __fadd_rn(a.y, b.y);
+  bp = __fadd_rn(th, -a.y);
+  const float tl = __fadd_rn(__fadd_rn(a.y, -__fadd_rn(th, -bp)), __fadd_rn(b.y, -bp));
+  sl = __fadd_rn(sl, th);
+  float h = __fadd_rn(sh, sl);
+  sl = __fadd_rn(sl, -__fadd_rn(h, -sh));
+  sl = __fadd_rn(sl, tl);
+  a.x = __fadd_rn(h, sl);
+  a.y = __fadd_rn(sl, -__fadd_rn(a.x, -h));
+}
+
 // a += b for two unevaluated sums hi + lo: TwoSum of the high parts, the
 // low parts and the rounding error added to the low part.
 __device__ __forceinline__ void df_add(float2& a, float2 b) {
@@ -88,6 +122,18 @@ __device__ __forceinline__ void df_add(float2& a, float2 b) {
 }
 
 __device__ __forceinline__ double df_to_double(float2 a) { return f2d_bits(a.x) + f2d_bits(a.y); }
+
+// Largest |binary exponent| of a matrix's largest entry for which the
+// double-float products are used (amg_params.spmv_fp64 / setup_fp64 fall back
+// to FP64 outside it).
+constexpr int kDfExpLimit = 90;
+
+struct Bsr;
+// Binary exponent of A's largest |entry| (floor(log2 max |A_ij|); 0 when there
+// is none) into *max_exp, over the block rows that hold more than their
+// diagonal block (identity rows of Dirichlet and cell-less nodes do not set
+// the scale), and whether every entry is finite.  Synchronising.
+void operator_exponent_range(const Bsr& A, int* max_exp, bool* finite, cudaStream_t s);
 
 struct Bsr {
   int n_rows = 0, n_cols = 0, br = 0, bc = 0;
@@ -175,7 +221,8 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
 // ---------------------------------------------------------------------------
 constexpr int SPMV_THREADS = 128;
 
-template <int BR, int BC, class Epi, bool DF>
+
+template <int BR, int BC, class Epi, bool DF, bool ACC = false>
 __global__ void __launch_bounds__(SPMV_THREADS)
 sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
   __shared__ double sh[32];
@@ -190,9 +237,9 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
     const int* __restrict__ cp = A.cols + (size_t)k0 * 32 + lane;
     if constexpr (DF) {
       const float2* __restrict__ vp = A.vals_df + (size_t)k0 * 32 * BR * BC + lane;
-      float2 ad[BR];
+      float2 ad[BR], od[BR];
 #pragma unroll
-      for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
+      for (int r = 0; r < BR; ++r) ad[r] = od[r] = make_float2(0.f, 0.f);
 #pragma unroll 2
       for (int k = k0; k < k1; ++k) {
         float2 vv[BR * BC];  // the slot's values first, then the gather
@@ -206,11 +253,28 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
         for (int r = 0; r < BR; ++r)
 #pragma unroll
           for (int j = 0; j < BC; ++j) df_fma(ad[r], vv[r * BC + j], xv[j]);
+        if constexpr (ACC) {
+          // ACC: the running double-float sum restarts every 4 slots and is
+          // added into an outer one accurately, so that the low part never
+          // carries more than 4 slots' rounding: about 2^-47 of
+          // sum_j |A_ij x_j| per row whatever the row's length (the sloppy
+          // running sum drifts to ~2^-45 on long P2 rows)
+          if (((k - k0) & 3) == 3) {  // uniform over the warp (one slice)
+#pragma unroll
+            for (int r = 0; r < BR; ++r) {
+              df_add_acc(od[r], ad[r]);
+              ad[r] = make_float2(0.f, 0.f);
+            }
+          }
+        }
         cp += 32;
         vp += 32 * BR * BC;
       }
 #pragma unroll
-      for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
+      for (int r = 0; r < BR; ++r) {
+        if constexpr (ACC) df_add_acc(ad[r], od[r]);
+        acc[r] = df_to_double(ad[r]);
+      }
     } else {
       const double* __restrict__ vp = A.vals + (size_t)k0 * 32 * BR * BC + lane;
 #pragma unroll 2
@@ -232,10 +296,14 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
 }
 
 // df: use the split copy when the matrix has one (false: plain FP64).
+// acc: the accurate double-float accumulation (outer CG products with K and
+// tam_matrix_spmv; the V-cycle's smoothing SpMVs keep the faster running sum).
 template <int BR, int BC, class Epi>
-void sell_spmv(const Sell& A, const double* x, Epi epi, cudaStream_t s, bool df = true) {
+void sell_spmv(const Sell& A, const double* x, Epi epi, cudaStream_t s, bool df = true, bool acc = false) {
   unsigned grid = grid_for((long long)A.n_slices * 32, SPMV_THREADS);
-  if (df && A.vals_df.p)
+  if (df && A.vals_df.p && acc)
+    sell_spmv_kernel<BR, BC, Epi, true, true><<<grid, SPMV_THREADS, 0, s>>>(view(A), x, epi);
+  else if (df && A.vals_df.p)
     sell_spmv_kernel<BR, BC, Epi, true><<<grid, SPMV_THREADS, 0, s>>>(view(A), x, epi);
   else
     sell_spmv_kernel<BR, BC, Epi, false><<<grid, SPMV_THREADS, 0, s>>>(view(A), x, epi);

@@ -125,7 +125,7 @@ __global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__
     out[i] = (float)in[i];
 }
 
-unsigned vgrid(long long N) { return std::min<unsigned>(grid_for(N, TPB), 152u * 8u); }
+unsigned vgrid(long long N) { return stride_grid(N, TPB, 8); }
 
 // A x with the level's reduced-precision values: BF16 on the finest level in
 // mode 2, FP32 otherwise.

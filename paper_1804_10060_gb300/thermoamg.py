@@ -57,6 +57,7 @@ _pi, _pd, _pll = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), 
 _SIGNATURES = {
     "tam_last_error": ([], ctypes.c_char_p),
     "tam_kernel_launches": ([], ctypes.c_longlong),
+    "tam_fma_throughput": ([_pd, _pd, _vp], _i),
     "fem_assemble_elasticity": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp,
                                  ctypes.POINTER(_vp), _vp, _vp], _i),
     "tam_matrix_info": ([_vp, _pi, _pll, _pi], _i),
@@ -71,6 +72,9 @@ _SIGNATURES = {
     "amg_setup_stats": ([_vp, _pd], _i),
     "amg_level_aggregates": ([_vp, _i, _vp, _vp], _i),
     "amg_level_export": ([_vp, _i, _i, _pi, _pi, _pi, _pi, _pll, _vp, _vp, _vp, _vp], _i),
+    "amg_level_spmv_plan": ([_vp, _i, _i, _pi, _pi, _pi], _i),
+    "amg_smooth": ([_vp, _vp, _vp, _i, _vp], _i),
+    "amg_solve_bytes": ([_vp, _pd, _pd], _i),
     "amg_vcycle": ([_vp, _vp, _vp, _vp], _i),
     "amg_pcg_solve": ([_vp, _vp, _vp, _d, _d, _i, _pi, _pd, _vp], _i),
     "amg_destroy": ([_vp], _i),
@@ -114,6 +118,13 @@ def last_error() -> str:
 def kernel_launches() -> int:
     """Kernels launched by the library so far in this process (graph replays included)."""
     return int(lib.tam_kernel_launches())
+
+
+def fma_throughput(stream=None) -> dict:
+    """Measured FP64 / FP32 FMA throughput of the current device (TFLOP/s)."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    _check(lib.tam_fma_throughput(ctypes.byref(f64), ctypes.byref(f32), _stream(stream)))
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value}
 
 
 def _check(status, allow=()):
@@ -291,6 +302,29 @@ def amg_level_export(amg: Amg, level: int, which: int, stream=None) -> dict:
                                 _vp(v.data_ptr()), _stream(stream)))
     return {"n_rows": nr.value, "n_cols": nc.value, "br": br.value, "bc": bc.value, "nnzb": nnzb.value,
             "row_ptr": rp, "col_idx": ci[:nnzb.value], "vals": v[:nnzb.value]}
+
+
+def amg_level_spmv_plan(amg: Amg, level: int, which: int) -> dict:
+    """SpMV layout of one operator: kind (0 SELL, 1 lanes/row interleaved store,
+    2 lanes/row block-CSR, 3 whole warps/row), lanes per row, double-float flag."""
+    k, ln, df = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.amg_level_spmv_plan(amg.handle, int(level), int(which), ctypes.byref(k), ctypes.byref(ln),
+                                   ctypes.byref(df)))
+    return {"kind": k.value, "lanes": ln.value, "df": bool(df.value)}
+
+
+def amg_solve_bytes(amg: Amg) -> dict:
+    """Algorithmic bytes of one V-cycle and of one PCG iteration of this hierarchy."""
+    v, it = ctypes.c_double(), ctypes.c_double()
+    _check(lib.amg_solve_bytes(amg.handle, ctypes.byref(v), ctypes.byref(it)))
+    return {"vcycle": v.value, "iteration": it.value}
+
+
+def amg_smooth(amg: Amg, b, x, degree, stream=None):
+    """x <- `degree` Chebyshev-Jacobi steps on K x = b (the finest level's smoother), in place."""
+    _check(lib.amg_smooth(amg.handle, _dev(b, torch.float64, "b"), _dev(x, torch.float64, "x"), int(degree),
+                          _stream(stream)))
+    return x
 
 
 def amg_vcycle(amg: Amg, r, z=None, stream=None):

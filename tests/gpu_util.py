@@ -35,3 +35,34 @@ def sparse_rel(A, B):
     D = (A - B).tocsr()
     m = abs(B).max()
     return (abs(D).max() if D.nnz else 0.0) / m
+
+
+def _veltkamp(a):
+    """a = hi + lo with 26-bit halves (Veltkamp's splitting; exact for |a| < 2^996)."""
+    c = 134217729.0 * a          # 2^27 + 1
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def exact_spmv(A, x):
+    """Correctly rounded y = A x and s = sum_j |A_ij x_j| per row (A scipy CSR, x float64).
+
+    Every product is made exact with Dekker's TwoProduct (p + e = a x exactly),
+    then each row's 2 nnz terms are summed exactly by math.fsum.
+    """
+    import math
+    A = A.tocsr()
+    a = A.data
+    xv = x[A.indices]
+    p = a * xv
+    ah, al = _veltkamp(a)
+    xh, xl = _veltkamp(xv)
+    e = ((ah * xh - p) + ah * xl + al * xh) + al * xl
+    y = np.empty(A.shape[0])
+    s = np.empty(A.shape[0])
+    ab = np.abs(p)
+    for i in range(A.shape[0]):
+        lo, hi = A.indptr[i], A.indptr[i + 1]
+        y[i] = math.fsum(np.concatenate([p[lo:hi], e[lo:hi]]))
+        s[i] = math.fsum(ab[lo:hi])
+    return y, s

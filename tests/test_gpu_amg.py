@@ -145,7 +145,7 @@ def test_max_iter_and_status_paths():
     x0 = torch.zeros_like(rhs)
     it, rel, st = tam.amg_pcg_solve(H, torch.zeros_like(rhs), x0, rtol=1e-8)
     assert st == 0 and it == 0 and float(x0.abs().max()) == 0.0
-    # reuse of the hierarchy for another right-hand side (setup reuse, Sec. 6)
+    # reuse of the hierarchy for another right-hand side (setup reuse, Sec. 5.3)
     x2 = torch.zeros_like(rhs)
     it2, rel2, st2 = tam.amg_pcg_solve(H, 2 * rhs, x2, rtol=1e-8)
     x1 = torch.zeros_like(rhs)

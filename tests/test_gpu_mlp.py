@@ -79,27 +79,29 @@ def test_node_features_match_oracle(degree):
     assert np.all(np.abs(F - ref) <= 1e-5 * scale + 1e-6)
 
 
-def _disc(seed, blades=24, n_r=10):
+def _disc(seed, blades=24, n_r=10, degree=1):
     return meshgen.bladed_disc_problem(n_r=n_r, n_theta_per_blade=4, n_z=3, n_blades=blades, n_r_blade=4,
-                                       degree=1, seed=seed)
+                                       degree=degree, seed=seed)
 
 
-def test_trained_guess_reduces_iterations_and_guard_catches_bad_guess():
+# P1 discs of 16,128 DOF; P2 discs (the element of the benchmark's disc) of 72,576 DOF
+@pytest.mark.parametrize("degree,n_r", [(1, 10), (2, 6)])
+def test_trained_guess_reduces_iterations_and_guard_catches_bad_guess(degree, n_r):
     tam = need_gpu()
     from paper_1804_10060_gb300 import learned
-    train = [_disc(s) for s in (1, 2, 3, 4)]
+    train = [_disc(s, n_r=n_r, degree=degree) for s in (1, 2, 3, 4)]
     X, Y = learned.training_set(train)
     net = tam.Mlp(8, 64, 3, 3, seed=7)
     net.set_normalization(*learned.normalization(X, Y))
     hist = learned.train(net, X, Y, steps=600, batch=16384, lr=3e-3)
     assert hist[-1] < 0.2 * hist[0]
-    res = learned.evaluate(net, _disc(11))
+    res = learned.evaluate(net, _disc(11, n_r=n_r, degree=degree))
     assert res["guess_used"], res
     assert res["rel_resid_guess"] <= 1e-8 and res["solution_diff"] <= 1e-6, res
     assert res["iters_guess"] < res["iters_zero"], res
     # a network that outputs garbage is refused by the residual guard
     bad = tam.Mlp(8, 16, 1, 3, seed=1)
     bad.set_normalization(np.zeros(8), np.ones(8), np.full(3, 1e6))
-    res_bad = learned.evaluate(bad, _disc(12))
+    res_bad = learned.evaluate(bad, _disc(12, n_r=n_r, degree=degree))
     assert not res_bad["guess_used"]
     assert res_bad["iters_guess"] == res_bad["iters_zero"] and res_bad["rel_resid_guess"] <= 1e-8

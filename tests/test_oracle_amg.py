@@ -43,6 +43,42 @@ def _cube_system(n=4, degree=1, twist=False):
     return pb, Kd, fd, mask
 
 
+def _three_node_matrix():
+    """Hand-built 3-node matrix of 3x3 blocks for the strength pin.
+
+    Diagonal blocks 4I, 9I, I have Frobenius norms 4 sqrt3, 9 sqrt3, sqrt3, so
+    sqrt(||A_ii|| ||A_jj||) is sqrt(108) = 10.392 for (0,1), sqrt(12) = 3.464
+    for (0,2) and sqrt(27) = 5.196 for (1,2).  The off-diagonal blocks are
+    constant blocks -0.1, 0.05 and 0.09 with Frobenius norms 0.3, 0.15 and
+    0.27 (their largest entries, 0.1, 0.05 and 0.09, and their traces give
+    other answers, as do the norms without the square root or squared).
+    """
+    A = np.zeros((9, 9))
+    for i, d in enumerate((4.0, 9.0, 1.0)):
+        A[3 * i:3 * i + 3, 3 * i:3 * i + 3] = d * np.eye(3)
+    for (i, j), v in {(0, 1): -0.1, (0, 2): 0.05, (1, 2): 0.09}.items():
+        A[3 * i:3 * i + 3, 3 * j:3 * j + 3] = v
+        A[3 * j:3 * j + 3, 3 * i:3 * i + 3] = v
+    return sp.csr_matrix(A)
+
+
+@pytest.mark.parametrize("theta,expected", [
+    # thresholds theta * sqrt(||A_ii|| ||A_jj||), hand-computed:
+    #   theta = 0.02: (0,1) 0.2078, (0,2) 0.0693, (1,2) 0.1039 -> all three couplings strong
+    #   theta = 0.05: (0,1) 0.5196 > 0.3, (0,2) 0.1732 > 0.15 weak; (1,2) 0.2598 < 0.27 strong
+    (0.0, [[1, 2], [0, 2], [0, 1]]),
+    (0.02, [[1, 2], [0, 2], [0, 1]]),
+    (0.05, [[], [2], [1]]),
+    (0.1, [[], [], []]),
+])
+def test_strength_graph_threshold_hand_computed(theta, expected):
+    """Sec. 5.1 leaves the coupling threshold to the user; the strength rule
+    ||A_ij||_F >= theta sqrt(||A_ii||_F ||A_jj||_F) on a 3-node matrix whose
+    block norms straddle the thresholds."""
+    nbrs = amg.strength_graph(_three_node_matrix(), 3, theta)
+    assert [sorted(int(j) for j in nb) for nb in nbrs] == expected
+
+
 def test_mis2_roots_independent_maximal_and_greedy():
     pb, K, f, mask = _cube_system(5)
     nbrs = amg.strength_graph(K, 3)
