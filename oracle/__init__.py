@@ -9,6 +9,9 @@ path never does, and it shares no code with the CUDA sources.
   integration), assembly, Dirichlet elimination, rigid-body modes.
 * ``oracle.linsolve`` -- dense Cholesky, sparse direct and Jacobi-PCG solves.
 * ``oracle.amg``      -- smoothed-aggregation AMG pieces and the AMG-PCG solve.
+* ``oracle.thermal``  -- the heat equation of the thermal half of the model:
+  theta-method residual and Newton Jacobian with Robin faces, Newton, and
+  the adaptive time step.
 
 Parity status per function is stated in each module header.
 """

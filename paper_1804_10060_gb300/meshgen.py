@@ -437,3 +437,93 @@ def mesh_quality(coords: np.ndarray, cells: np.ndarray):
             c = -np.einsum("ij,ij->i", normals[a], normals[b])
             ang.append(np.degrees(np.arccos(np.clip(c, -1, 1))))
     return float(vol.min()), float(np.min(ang))
+
+
+# ----------------------------------------------------------------------------
+# Boundary faces and thermal inputs
+# ----------------------------------------------------------------------------
+
+# Local vertices of the four faces of a tet (face k is opposite vertex k).
+TET_FACES = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))
+
+
+def boundary_faces(cells: np.ndarray) -> np.ndarray:
+    """Faces that belong to exactly one cell, as node ids.
+
+    P1 cells give [n_f, 3] (three vertices); P2 cells give [n_f, 6]: the three
+    vertices (v0, v1, v2) then the mid-edge nodes of edges v0v1, v1v2, v2v0.
+    Faces come out in the order of their sorted vertex triples (deterministic).
+    """
+    cells = np.asarray(cells)
+    p2 = cells.shape[1] == 10
+    edge_slot = {e: 4 + k for k, e in enumerate(P2_EDGES)}
+    tri, full = [], []
+    for f in TET_FACES:
+        v = cells[:, list(f)]
+        tri.append(v)
+        if p2:
+            def mid(a, b):
+                return cells[:, edge_slot[(min(a, b), max(a, b))]]
+            full.append(np.stack([v[:, 0], v[:, 1], v[:, 2], mid(f[0], f[1]), mid(f[1], f[2]),
+                                  mid(f[2], f[0])], axis=1))
+        else:
+            full.append(v)
+    tri = np.concatenate(tri)
+    full = np.concatenate(full)
+    key = np.sort(tri, axis=1)
+    _, first, counts = np.unique(key, axis=0, return_index=True, return_counts=True)
+    keep = first[counts == 1]
+    return full[np.sort(keep)].astype(np.int32)
+
+
+@dataclass
+class ThermalProblem:
+    """Thermal data on a mesh (host arrays): materials, Robin faces, fields.
+
+    thermal_props[n_mat, 5] = (rho, c0, c1, k0, k1): density, specific heat
+    c_v(T) = c0 + c1 T and conductivity kappa(T) = k0 + k1 T.  faces are the
+    Robin faces (boundary_faces layout) with beta[n_f] per face and the
+    exterior temperature T_bc[n] given at the nodes.  dirichlet_mask / T_dirichlet
+    optionally fix nodal temperatures.
+    """
+
+    coords: np.ndarray
+    cells: np.ndarray
+    cell_material: np.ndarray
+    thermal_props: np.ndarray
+    faces: np.ndarray
+    beta: np.ndarray
+    T_bc: np.ndarray
+    dirichlet_mask: np.ndarray | None = None
+    T_dirichlet: np.ndarray | None = None
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.coords.shape[0])
+
+
+def disc_thermal_problem(pb: Problem, t: float = 0.0, seed: int = 11) -> ThermalProblem:
+    """Heating of a bladed disc (inputs for the transient thermal solve).
+
+    One material (rho 1, c_v = 1 + 5e-4 T, kappa = 0.05 (1 + 1e-3 T)); Robin
+    faces: the blade and rim faces (r > 0.995) see hot gas, T_bc = 300 + 600
+    (1 - exp(-t / 0.5)) + 20 F(x) with a seeded smooth field F, coefficient
+    beta = -5; the bore faces (r < 0.2005) are cooled, T_bc = 300,
+    beta = -1; the other faces are adiabatic (not listed).  beta < 0 is the
+    sign of a cooling film in the paper's boundary condition
+    kappa grad T . n = beta (T - T_bc).
+    """
+    faces = boundary_faces(pb.cells)
+    xc = pb.coords[faces[:, :3]].mean(axis=1)
+    r = np.hypot(xc[:, 0], xc[:, 1])
+    hot = r > 0.995
+    bore = r < 0.2005
+    sel = hot | bore
+    beta = np.where(hot[sel], -5.0, -1.0)
+    rad = np.hypot(pb.coords[:, 0], pb.coords[:, 1])
+    ext = np.ptp(pb.coords, axis=0)
+    F = fourier_temperature(pb.coords, seed, scale=np.where(ext > 0, ext, 1.0))
+    T_bc = np.where(rad > 0.5, 300.0 + 600.0 * (1.0 - np.exp(-t / 0.5)) + 20.0 * F, 300.0)
+    props = np.array([[1.0, 1.0, 5e-4, 0.05, 5e-5]])
+    return ThermalProblem(pb.coords, pb.cells, np.zeros(pb.n_cells, np.int32), props, faces[sel],
+                          beta, T_bc)
