@@ -377,6 +377,80 @@ int tam_learned_guess(tam_mlp mlp, tam_amg amg, const float* features, const dou
                       void* stream);
 
 /* ------------------------------------------------------------------------
+ * The thermal half of the model (Sec. 3): the heat equation
+ *   rho c_v dT/dt - div(kappa grad T) = 0 in Omega,
+ *   kappa grad T . n = beta (T - T_bc)  on the Robin faces,
+ * discretised by the theta-method (Eq. wf_thermal) on the same P1/P2 meshes,
+ * solved by Newton's method on the full linearisation (Sec. 3, "Solution
+ * strategy": the Jacobian is non-symmetric when kappa depends on T; as in the
+ * paper each Newton step is solved by CG), each step preconditioned by the
+ * smoothed-aggregation AMG of this library on the scalar operator (constant
+ * near-nullspace; the paper uses classical AMG there), with the adaptive time
+ * step of Eq. dt_spec.  Materials: c_v(T) = c0 + c1 T, kappa(T) = k0 + k1 T.
+ * beta follows the paper's sign: beta <= 0 is a cooling film.  T fields are
+ * nodal [n_nodes] float64 device vectors (interpolants in the cells' space).
+ */
+typedef struct tam_thermal_s* tam_thermal;
+
+/* Thermal problem on a mesh.  coords, cells, cell_material, faces: device
+ * arrays that must outlive the handle (not copied).  thermal_props_host
+ * [n_mat*5] (host): rho, c0, c1, k0, k1 per material.  faces[n_faces*nf]:
+ * the Robin faces, nf = 3 (P1: vertices) or 6 (P2: vertices v0 v1 v2, then
+ * the mid-edge nodes of v0v1, v1v2, v2v0).  dirichlet_mask[n_nodes] (device,
+ * may be NULL): nodes whose temperature is prescribed.  params: AMG knobs for
+ * the Newton steps (NULL = defaults; level_precision must be 0).  Builds the
+ * scalar pattern; synchronising.  Errors: INVALID_ARG, OOM, CUDA,
+ * UNSUPPORTED. */
+int tam_thermal_create(int n_nodes, const double* coords, int n_cells, int nodes_per_cell, const int* cells,
+                       const int* cell_material, int n_mat, const double* thermal_props_host, int n_faces,
+                       const int* faces, const unsigned char* dirichlet_mask, const amg_params* params,
+                       tam_thermal* out, void* stream);
+
+/* Residual F(T)[n_nodes] of Eq. wf_thermal at the iterate T of T_{m+1}
+ * (T_old = T_m, NULL = the steady problem with theta = 1), with per-face
+ * beta[n_faces] and nodal T_bc[n_nodes] at the theta-weighted time; Dirichlet
+ * entries 0.  The Jacobian dF/dT is assembled alongside (see export).
+ * Synchronising.  Errors: INVALID_ARG, DEGENERATE_CELL, CUDA. */
+int tam_thermal_residual(tam_thermal th, const double* T, const double* T_old, double dt, double theta,
+                         const double* beta, const double* T_bc, double* F_out, void* stream);
+
+/* The last assembled Jacobian in CSR form: *nnz_host (host) always; with
+ * row_ptr != NULL also row_ptr[n+1], col_idx[nnz], vals[nnz] (device).
+ * Dirichlet rows are identity rows.  Synchronising. */
+int tam_thermal_export_jacobian(tam_thermal th, int* row_ptr, int* col_idx, double* vals, long long* nnz_host,
+                                void* stream);
+
+/* Newton's method on F(T) = 0 from the guess in T (overwritten with the
+ * solution): stops when ||F||_2 <= rtol ||F(T_0)||_2 (the paper's steady runs
+ * use 1e-9) or after max_newton steps.  Each step solves J delta = F by CG to
+ * lin_rtol (at most lin_max_iter iterations) preconditioned by an AMG
+ * hierarchy: with reuse = 0 a new one every step, with reuse = 1 the
+ * hierarchy of an earlier Jacobian (from an earlier step or call) with its
+ * finest level refreshed, rebuilt only when that solve fails -- the paper's
+ * transient runs rebuild the thermal preconditioner only at some steps
+ * (Sec. 5.3).  T_dirichlet (may be NULL) sets the masked nodes first.
+ * Outputs (host, may be NULL): Newton steps, CG iterations in all, hierarchies
+ * built, final ||F|| / ||F_0||.  Synchronising.  Errors: NOT_CONVERGED, NAN,
+ * BREAKDOWN, INDEFINITE_PRECOND, INVALID_ARG, CUDA. */
+int tam_thermal_newton(tam_thermal th, double* T, const double* T_old, double dt, double theta, const double* beta,
+                       const double* T_bc, const double* T_dirichlet, double rtol, int max_newton, double lin_rtol,
+                       int lin_max_iter, int reuse, int* newton_iters, int* linear_iters, int* setups,
+                       double* rel_resid, void* stream);
+
+/* max_i |a_i - b_i| into *max_host (a, b: device [n]).  Synchronising. */
+int tam_thermal_max_change(const double* a, const double* b, long long n, double* max_host, void* stream);
+
+/* Eq. dt_spec: the step with max |T_{m+1} - T_m| = max_change is accepted when
+ * max_change <= dT_max, and then dt_next = eps dT_max / max_change * dt (twice
+ * dt when nothing changed); otherwise it is rejected and dt_next = dt / 2 (the
+ * step is repeated).  Host arithmetic only. */
+int tam_thermal_next_dt(double dt, double max_change, double dT_max, double eps, double* dt_next_host,
+                        int* accepted_host);
+
+/* Releases the handle (and the hierarchy it holds). */
+int tam_thermal_destroy(tam_thermal th);
+
+/* ------------------------------------------------------------------------
  * One-call host-buffer path: copies the mesh and fields from host memory
  * (pinned memory gives the fastest copies), assembles, builds the AMG, solves
  * to rtol and copies the displacement back into u_host[n_nodes*3].  Same

@@ -67,6 +67,13 @@ __global__ void rigid_modes_kernel(const double* __restrict__ X, const unsigned 
     for (int q = 0; q < k; ++q) B[(3 * (size_t)i + r) * k + q] = m[r][q];
 }
 
+// The near-nullspace of a scalar diffusion operator: the constant (zero on
+// Dirichlet nodes).
+__global__ void constant_mode_kernel(const unsigned char* __restrict__ dmask, int n, double* __restrict__ B) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) B[i] = dmask[i] ? 0.0 : 1.0;
+}
+
 // ---------------------------------------------------------------------------
 // Lanczos estimate of lambda_max(D^-1 A) on S = D^-1/2 A D^-1/2
 // ---------------------------------------------------------------------------
@@ -652,9 +659,12 @@ static void lanczos_lambda(tam_amg_s* H, Level& L, int level, cudaStream_t s, Gr
     if (L.bs == 3) {
       EpiLanczos<3> epi{w.p, sv.p, v.p, L.n_rows, gr, ab.p + j, done};
       spop_apply<3, 3>(L.Aop, u.p, epi, s);
-    } else {
+    } else if (L.bs == 6) {
       EpiLanczos<6> epi{w.p, sv.p, v.p, L.n_rows, gr, ab.p + j, done};
       spop_apply<6, 6>(L.Aop, u.p, epi, s);
+    } else {
+      EpiLanczos<1> epi{w.p, sv.p, v.p, L.n_rows, gr, ab.p + j, done};
+      spop_apply<1, 1>(L.Aop, u.p, epi, s);
     }
     lanczos_orth_kernel<<<g, TPB, 0, s>>>(LW, j, gr, done);
     TAM_LAUNCH_CHECK();
@@ -881,6 +891,8 @@ struct PhaseTimer {
 static amg_params effective_params(const tam_matrix_s* K, const amg_params& in) {
   amg_params p = in;
   TAM_CHECK(K->finite, TAM_ERR_INVALID_ARG, "amg_setup: K has an inf or NaN entry");
+  TAM_CHECK(K->A.br == 3 || p.level_precision == 0, TAM_ERR_UNSUPPORTED,
+            "amg_setup: the FP32 V-cycle (level_precision 1/2) is built for 3x3-block (elastic) operators only");
   if (K->df_ok) return p;
   const std::string why = "largest |K| entry is 2^" + std::to_string(K->vmax_exp) + "; FP32 arithmetic needs 2^-" +
                           std::to_string(kDfExpLimit) + "..2^" + std::to_string(kDfExpLimit);
@@ -917,13 +929,19 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
     H->ticket = DBuf<unsigned int>(1, s);
     H->ticket.zero();
     GridReduce gr{H->partials.p, H->ticket.p};
-    const int k = prm.use_rotations ? 6 : 3;
+    // near-nullspace: the rigid-body modes of elasticity (3x3 blocks), the
+    // constant for a scalar operator (1x1 blocks: the heat equation)
+    const bool scalar = K->A.br == 1;
+    const int k = scalar ? 1 : (prm.use_rotations ? 6 : 3);
     // near-nullspace of the finest level
     DBuf<double> cen(3, s);
     centroid_kernel<<<std::min<unsigned>(grid_for(n0, TPB), 1024), TPB, 0, s>>>(coords, n0, gr, cen.p);
     TAM_LAUNCH_CHECK();
     DBuf<double> B((size_t)n0 * 3 * k, s);
-    rigid_modes_kernel<<<grid_for(n0, TPB), TPB, 0, s>>>(coords, K->dmask.p, n0, cen.p, k, B.p);
+    if (scalar)
+      constant_mode_kernel<<<grid_for(n0, TPB), TPB, 0, s>>>(K->dmask.p, n0, B.p);
+    else
+      rigid_modes_kernel<<<grid_for(n0, TPB), TPB, 0, s>>>(coords, K->dmask.p, n0, cen.p, k, B.p);
     TAM_LAUNCH_CHECK();
     H->levels.reserve(prm.max_levels);  // references into `levels` stay valid while it grows
     H->levels.emplace_back();
@@ -1051,6 +1069,28 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
     throw;
   }
   return H;
+}
+
+// After K's values changed in place (same pattern): the finest level's
+// diagonal, its lanes-per-row store or split copy, so that a hierarchy built
+// on earlier values can keep preconditioning the new K (its coarse levels and
+// the lambda_max estimate stay as they were).  The captured PCG iteration is
+// dropped, since the store's buffers are new.
+void amg_refresh_finest(tam_amg_s* H, cudaStream_t s) {
+  Level& L = H->levels[0];
+  const Bsr& A = H->K->A;
+  point_dinv_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, A.vals.p, L.n_rows, L.bs,
+                                                            L.dinv.p);
+  TAM_LAUNCH_CHECK();
+  if (L.Aop.L) {
+    build_lpr_store(A, L.Aop.L->lpr, L.Aop.df, L.AL, s);
+  } else if (L.Aop.lpr != 0 && L.Aop.df) {
+    build_df_values(H->K->A, s);
+  }
+  if (H->iter_exec) {
+    cudaGraphExecDestroy(H->iter_exec);
+    H->iter_exec = nullptr;
+  }
 }
 
 }  // namespace tam

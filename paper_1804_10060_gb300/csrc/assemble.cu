@@ -31,7 +31,7 @@ __global__ void validate_kernel(const int* __restrict__ cells, long long n_entri
     int v = cells[t];
     if (v < 0 || v >= n_nodes) atomicExch(bad, 1);
   }
-  if (t < n_cells) {
+  if (mat && t < n_cells) {
     int m = mat[t];
     if (m < 0 || m >= n_mat) atomicExch(bad, 2);
   }
@@ -432,6 +432,89 @@ __global__ void dirichlet_rows_kernel(int n, const unsigned char* __restrict__ d
 
 }  // namespace
 
+// Node and material ids of a mesh in range (INVALID_ARG otherwise).  Synchronising.
+void validate_mesh(int n_nodes, int n_cells, int npc, const int* cells, const int* mat, int n_mat, const char* who,
+                   cudaStream_t s) {
+  if (n_cells <= 0) return;
+  const long long n_entries = (long long)n_cells * npc;
+  DBuf<int> bad(1, s);
+  bad.zero();
+  validate_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, npc, n_nodes, mat, n_cells, n_mat,
+                                                            bad.p);
+  TAM_LAUNCH_CHECK();
+  const int b = read_back_int(bad.p, s);
+  TAM_CHECK(b == 0, TAM_ERR_INVALID_ARG,
+            std::string(who) + (b == 1 ? ": cell node id out of range" : ": material id out of range"));
+}
+
+// Node-adjacency pattern of a mesh: block row i holds i and every node that
+// shares a cell with it, sorted, without the Dirichlet nodes (dmask) -- whose
+// own rows keep only the diagonal.  Fills A.n_rows/n_cols, row_ptr, col_idx
+// and nnzb (block sizes are the caller's), and returns the cell-node
+// incidence (inc_ptr[n_nodes + 1], inc) that the pattern came from.  flag[1]
+// is set when a node has too many incident cells for the shared-memory
+// builder.  Synchronising.
+void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, const unsigned char* dmask, Bsr& A,
+                        DBuf<int>& inc_ptr, DBuf<int>& inc, int* flag, cudaStream_t s) {
+  const long long n_entries = (long long)n_cells * npc;
+  // cell-node incidence
+  inc_ptr = DBuf<int>((size_t)n_nodes + 1, s);
+  inc = DBuf<int>((size_t)std::max(1LL, n_entries), s);
+  DBuf<int> cursor((size_t)n_nodes, s);
+  inc_ptr.zero();
+  cursor.zero();
+  if (n_cells > 0) {
+    incidence_count_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, inc_ptr.p);
+    TAM_LAUNCH_CHECK();
+  }
+  exclusive_scan_i32(inc_ptr.p, inc_ptr.p, n_nodes, s);
+  if (n_cells > 0) {
+    incidence_fill_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, npc, inc_ptr.p, cursor.p,
+                                                                   inc.p);
+    TAM_LAUNCH_CHECK();
+  }
+  // pattern
+  A.n_rows = A.n_cols = n_nodes;
+  A.row_ptr = DBuf<int>((size_t)n_nodes + 1, s);
+  unsigned pg = grid_for(n_nodes, PAT_WARPS);
+  if ((long long)n_nodes + (long long)npc * npc * n_cells < (1LL << 31)) {
+    // one sort pass: each row's sorted unique columns go to its candidate-
+    // bound offset in a scratch array (the bounds' sum, at most
+    // n_nodes + npc^2 n_cells, fits the int32 scan), the counts give
+    // row_ptr, then pack
+    DBuf<int> bptr((size_t)n_nodes + 1, s);
+    pattern_bound_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, npc, inc_ptr.p, dmask, bptr.p);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(bptr.p, bptr.p, n_nodes, s);
+    const long long total = read_back_int(bptr.p + n_nodes, s);
+    DBuf<int> tmp((size_t)std::max(1LL, total), s);
+    pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
+                                                      bptr.p, tmp.p, flag + 1);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
+    A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
+    TAM_CHECK(read_back_int(flag + 1, s) == 0, TAM_ERR_UNSUPPORTED,
+              "fem_assemble: a node has too many incident cells for the pattern builder");
+    A.col_idx = DBuf<int>((size_t)std::max(1LL, A.nnzb), s);
+    pattern_pack_kernel<<<grid_for((long long)n_nodes * 32, 256), 256, 0, s>>>(n_nodes, bptr.p, tmp.p,
+                                                                               A.row_ptr.p, A.col_idx.p);
+    TAM_LAUNCH_CHECK();
+  } else {
+    // very large meshes: count pass, then fill pass (no scratch)
+    pattern_kernel<false><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
+                                                       nullptr, nullptr, flag + 1);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
+    A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
+    TAM_CHECK(read_back_int(flag + 1, s) == 0, TAM_ERR_UNSUPPORTED,
+              "fem_assemble: a node has too many incident cells for the pattern builder");
+    A.col_idx = DBuf<int>((size_t)A.nnzb, s);
+    pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, nullptr,
+                                                      A.row_ptr.p, A.col_idx.p, flag + 1);
+    TAM_LAUNCH_CHECK();
+  }
+}
+
 tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells, int npc, const int* cells,
                                   const int* mat, int n_mat, const double* props, const double* T,
                                   double T_ref, const double* body, const unsigned char* dmask,
@@ -454,62 +537,11 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
       TAM_CHECK(bad == 0, TAM_ERR_INVALID_ARG,
                 bad == 1 ? "fem_assemble: cell node id out of range" : "fem_assemble: material id out of range");
     }
-    // cell-node incidence
-    DBuf<int> inc_ptr((size_t)n_nodes + 1, s), cursor((size_t)n_nodes, s), inc((size_t)std::max(1LL, n_entries), s);
-    inc_ptr.zero();
-    cursor.zero();
-    if (n_cells > 0) {
-      incidence_count_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, inc_ptr.p);
-      TAM_LAUNCH_CHECK();
-    }
-    exclusive_scan_i32(inc_ptr.p, inc_ptr.p, n_nodes, s);
-    if (n_cells > 0) {
-      incidence_fill_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, npc, inc_ptr.p, cursor.p,
-                                                                     inc.p);
-      TAM_LAUNCH_CHECK();
-    }
-    // pattern
+    // cell-node incidence and block pattern
     Bsr& A = M->A;
-    A.n_rows = A.n_cols = n_nodes;
     A.br = A.bc = 3;
-    A.row_ptr = DBuf<int>((size_t)n_nodes + 1, s);
-    unsigned pg = grid_for(n_nodes, PAT_WARPS);
-    if ((long long)n_nodes + (long long)npc * npc * n_cells < (1LL << 31)) {
-      // one sort pass: each row's sorted unique columns go to its candidate-
-      // bound offset in a scratch array (the bounds' sum, at most
-      // n_nodes + npc^2 n_cells, fits the int32 scan), the counts give
-      // row_ptr, then pack
-      DBuf<int> bptr((size_t)n_nodes + 1, s);
-      pattern_bound_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, npc, inc_ptr.p, dmask, bptr.p);
-      TAM_LAUNCH_CHECK();
-      exclusive_scan_i32(bptr.p, bptr.p, n_nodes, s);
-      const long long total = read_back_int(bptr.p + n_nodes, s);
-      DBuf<int> tmp((size_t)std::max(1LL, total), s);
-      pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
-                                                        bptr.p, tmp.p, flag.p + 1);
-      TAM_LAUNCH_CHECK();
-      exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
-      A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
-      TAM_CHECK(read_back_int(flag.p + 1, s) == 0, TAM_ERR_UNSUPPORTED,
-                "fem_assemble: a node has too many incident cells for the pattern builder");
-      A.col_idx = DBuf<int>((size_t)std::max(1LL, A.nnzb), s);
-      pattern_pack_kernel<<<grid_for((long long)n_nodes * 32, 256), 256, 0, s>>>(n_nodes, bptr.p, tmp.p,
-                                                                                 A.row_ptr.p, A.col_idx.p);
-      TAM_LAUNCH_CHECK();
-    } else {
-      // very large meshes: count pass, then fill pass (no scratch)
-      pattern_kernel<false><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
-                                                         nullptr, nullptr, flag.p + 1);
-      TAM_LAUNCH_CHECK();
-      exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
-      A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
-      TAM_CHECK(read_back_int(flag.p + 1, s) == 0, TAM_ERR_UNSUPPORTED,
-                "fem_assemble: a node has too many incident cells for the pattern builder");
-      A.col_idx = DBuf<int>((size_t)A.nnzb, s);
-      pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, nullptr,
-                                                        A.row_ptr.p, A.col_idx.p, flag.p + 1);
-      TAM_LAUNCH_CHECK();
-    }
+    DBuf<int> inc_ptr, inc;
+    build_node_pattern(n_nodes, n_cells, npc, cells, dmask, A, inc_ptr, inc, flag.p, s);
     // numeric
     A.vals = DBuf<double>((size_t)A.nnzb * 9, s);
     A.vals.zero();

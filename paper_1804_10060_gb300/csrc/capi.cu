@@ -289,10 +289,10 @@ int amg_solve_bytes(tam_amg amg, double* vcycle_bytes, double* iteration_bytes) 
       v += R + n * ws + nc * ws;
       v += P + nc * ws + 2.0 * n * ws;
     }
-    if (prec > 0) v += 2.0 * (double)amg->K->n_nodes * 3 * 4.0;  // FP64 r in / z out at level 0
+    const double n0 = (double)amg->K->n_nodes * amg->K->A.br;
+    if (prec > 0) v += 2.0 * n0 * 4.0;  // FP64 r in / z out at level 0
     // outer CG: q = K p (p in, q out), x/r update (x, r in/out; p, q in),
     // r.z (r, z in), p = z + beta p (z in, p in/out)
-    const double n0 = (double)amg->K->n_nodes * 3;
     const double it = v + mat(amg->K->A, 8.0) + 13.0 * n0 * 8.0;
     if (vcycle_bytes) *vcycle_bytes = v;
     if (iteration_bytes) *iteration_bytes = it;

@@ -122,6 +122,12 @@ struct tam_amg_s {
 
 namespace tam {
 
+// Mesh topology shared by the elastic and the thermal assembly (assemble.cu).
+void validate_mesh(int n_nodes, int n_cells, int npc, const int* cells, const int* mat, int n_mat, const char* who,
+                   cudaStream_t s);
+void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, const unsigned char* dmask, Bsr& A,
+                        DBuf<int>& inc_ptr, DBuf<int>& inc, int* flag, cudaStream_t s);
+
 tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells, int npc, const int* cells,
                                   const int* mat, int n_mat, const double* props, const double* T,
                                   double T_ref, const double* body, const unsigned char* dmask,
@@ -132,6 +138,8 @@ void assemble_loads(tam_matrix_s* K, const double* coords, int n_cells, int npc,
                     const double* ud, double* rhs, cudaStream_t s);
 
 tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& prm, cudaStream_t s);
+// Finest-level data of H refreshed after K's values changed in place.
+void amg_refresh_finest(tam_amg_s* H, cudaStream_t s);
 
 // One V-cycle z = M^-1 r on level 0 (r, z device vectors of the fine size).
 void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cudaStream_t s);

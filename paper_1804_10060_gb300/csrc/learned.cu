@@ -134,6 +134,7 @@ extern "C" int tam_learned_guess(tam_mlp_s* M, tam_amg H, const float* features,
               "tam_learned_guess: smooth_degree must be 0..64");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     tam_matrix_s* K = H->K;
+    TAM_CHECK(K->A.br == 3, TAM_ERR_INVALID_ARG, "tam_learned_guess: needs an elastic (3x3-block) hierarchy");
     const int n = K->n_nodes;
     const long long N = 3LL * n;
     DBuf<float> Y((size_t)N, s);

@@ -835,6 +835,8 @@ int pcg_solve_batch(int n_sys, tam_amg_s* const* H, const int* m, const double* 
   for (int i = 0; i < n_sys; ++i)
     for (int k = 0; k < i; ++k) TAM_CHECK(H[i] != H[k], TAM_ERR_INVALID_ARG, "batch solve: a hierarchy appears twice");
   for (int i = 0; i < n_sys; ++i)
+    TAM_CHECK(H[i]->K->A.br == 3, TAM_ERR_UNSUPPORTED, "batch solve: 3x3-block (elastic) systems only");
+  for (int i = 0; i < n_sys; ++i)
     TAM_CHECK(H[i]->K->df_ok, TAM_ERR_INVALID_ARG,
               "batch solve: the FP32 V-cycle needs K's largest entry within 2^-" + std::to_string(kDfExpLimit) +
                   "..2^" + std::to_string(kDfExpLimit) + " (it is 2^" + std::to_string(H[i]->K->vmax_exp) + ")");

@@ -89,6 +89,7 @@ extern "C" int tam_matrix_residual_norm_noalloc(tam_matrix K, const double* b, c
   try {
     set_last_error("");
     TAM_CHECK(K && b && x && norm_host, TAM_ERR_INVALID_ARG, "tam_matrix_residual_norm_noalloc: NULL argument");
+    TAM_CHECK(K->A.br == 3, TAM_ERR_INVALID_ARG, "tam_matrix_residual_norm_noalloc: 3x3-block (elastic) K only");
     const unsigned grid = sell_grid(K->S);
     TAM_CHECK(grid <= (unsigned)TAM_NOALLOC_MAX_BLOCKS, TAM_ERR_INVALID_ARG,
               "tam_matrix_residual_norm_noalloc: matrix has more than 16384*128 = 2,097,152 block rows "

@@ -16,6 +16,7 @@
 // graph of one iteration can be replayed without host round trips.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "handles.cuh"
@@ -266,15 +267,19 @@ void cheb_step(const Level& L, const double* b, const double* x, double* d, doub
   const double* coef = L.consts.p + 2 + 2 * step;
   if (L.bs == 3)
     spop_apply<3, 3>(L.Aop, x, EpiCheb<3>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
-  else
+  else if (L.bs == 6)
     spop_apply<6, 6>(L.Aop, x, EpiCheb<6>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
+  else
+    spop_apply<1, 1>(L.Aop, x, EpiCheb<1>{b, x, L.dinv.p, coef, d, xn, L.n_rows, stop}, s);
 }
 
 void residual(const Level& L, const double* b, const double* x, double* t, const int* stop, cudaStream_t s) {
   if (L.bs == 3)
     spop_apply<3, 3>(L.Aop, x, EpiResidual<3>{b, t, L.n_rows, stop}, s);
-  else
+  else if (L.bs == 6)
     spop_apply<6, 6>(L.Aop, x, EpiResidual<6>{b, t, L.n_rows, stop}, s);
+  else
+    spop_apply<1, 1>(L.Aop, x, EpiResidual<1>{b, t, L.n_rows, stop}, s);
 }
 
 void restrict_to(const Level& L, const double* t, double* bc, const int* stop, cudaStream_t s) {
@@ -282,6 +287,7 @@ void restrict_to(const Level& L, const double* t, double* bc, const int* stop, c
   const int nr = L.R.n_rows;
   if (L.kdim == 6 && L.bs == 3) spop_apply<6, 3>(L.Rop, t, EpiStore<6>{bc, nr, stop}, s);
   else if (L.kdim == 6 && L.bs == 6) spop_apply<6, 6>(L.Rop, t, EpiStore<6>{bc, nr, stop}, s);
+  else if (L.kdim == 1) spop_apply<1, 1>(L.Rop, t, EpiStore<1>{bc, nr, stop}, s);
   else spop_apply<3, 3>(L.Rop, t, EpiStore<3>{bc, nr, stop}, s);
 }
 
@@ -289,6 +295,7 @@ void prolong_add(const Level& L, const double* xc, double* x, const int* stop, c
   const int nr = L.P.n_rows;
   if (L.kdim == 6 && L.bs == 3) spop_apply<3, 6>(L.Pop, xc, EpiAdd<3>{x, nr, stop}, s);
   else if (L.kdim == 6 && L.bs == 6) spop_apply<6, 6>(L.Pop, xc, EpiAdd<6>{x, nr, stop}, s);
+  else if (L.kdim == 1) spop_apply<1, 1>(L.Pop, xc, EpiAdd<1>{x, nr, stop}, s);
   else spop_apply<3, 3>(L.Pop, xc, EpiAdd<3>{x, nr, stop}, s);
 }
 
@@ -350,14 +357,24 @@ void precondition(tam_amg_s* H, const double* r, double* z, const int* stop, cud
   else vcycle_level(H, 0, r, z, stop, s);
 }
 
+// f(std::integral_constant<int, BR>) for K's block size (3: elasticity, 1: a scalar problem)
+template <class F>
+void by_block(int br, F&& f) {
+  if (br == 1) f(std::integral_constant<int, 1>());
+  else f(std::integral_constant<int, 3>());
+}
+
 void spmv_outer_pq(tam_amg_s* H, cudaStream_t s) {
   GridReduce gr{H->partials.p, H->ticket.p};
-  sell_spmv<3, 3>(H->K->S, H->p.p, EpiPq<3>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s, H->levels[0].Aop.df,
-                  /*acc=*/true);
+  by_block(H->K->A.br, [&](auto B) {
+    constexpr int BR = decltype(B)::value;
+    sell_spmv<BR, BR>(H->K->S, H->p.p, EpiPq<BR>{H->p.p, H->q.p, H->K->n_nodes, gr, H->sc.p}, s,
+                      H->levels[0].Aop.df, /*acc=*/true);
+  });
 }
 
 void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
-  const long long N = (long long)H->K->n_nodes * 3;
+  const long long N = (long long)H->K->n_nodes * H->K->A.br;
   GridReduce gr{H->partials.p, H->ticket.p};
   const int* stop = &H->sc.p->stop;
   spmv_outer_pq(H, s);
@@ -373,7 +390,10 @@ void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
 }  // namespace
 
 void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s) {
-  sell_spmv<3, 3>(K->S, x, EpiStore<3>{y, K->n_nodes, nullptr}, s, K->df_ok, /*acc=*/true);
+  by_block(K->A.br, [&](auto B) {
+    constexpr int BR = decltype(B)::value;
+    sell_spmv<BR, BR>(K->S, x, EpiStore<BR>{y, K->n_nodes, nullptr}, s, K->df_ok, /*acc=*/true);
+  });
 }
 
 double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaStream_t s) {
@@ -382,7 +402,10 @@ double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaSt
   DBuf<unsigned int> ticket(1, s);
   ticket.zero();
   GridReduce gr{partials.p, ticket.p};
-  sell_spmv<3, 3>(K->S, x, EpiResNorm<3>{b, K->n_nodes, gr, out.p}, s, /*df=*/false);
+  by_block(K->A.br, [&](auto B) {
+    constexpr int BR = decltype(B)::value;
+    sell_spmv<BR, BR>(K->S, x, EpiResNorm<BR>{b, K->n_nodes, gr, out.p}, s, /*df=*/false);
+  });
   return std::sqrt(read_back_double(out.p, s));
 }
 
@@ -393,7 +416,7 @@ void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cud
 int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
               double* rel, cudaStream_t s) {
   TAM_CHECK(b && x && rtol >= 0.0 && atol >= 0.0 && max_iter >= 0, TAM_ERR_INVALID_ARG, "amg_pcg_solve: bad argument");
-  const long long N = (long long)H->K->n_nodes * 3;
+  const long long N = (long long)H->K->n_nodes * H->K->A.br;
   GridReduce gr{H->partials.p, H->ticket.p};
   PcgScalars* sc = H->sc.p;
   if (!H->bs.p) H->bs = DBuf<double>((size_t)N, s);
@@ -405,8 +428,11 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(x, x, N, sc, -1);
   TAM_LAUNCH_CHECK();
   b = H->bs.p;
-  sell_spmv<3, 3>(H->K->S, x, EpiInitResidual<3>{b, H->r.p, H->K->n_nodes, gr, sc}, s, H->levels[0].Aop.df,
-                  /*acc=*/true);
+  by_block(H->K->A.br, [&](auto B) {
+    constexpr int BR = decltype(B)::value;
+    sell_spmv<BR, BR>(H->K->S, x, EpiInitResidual<BR>{b, H->r.p, H->K->n_nodes, gr, sc}, s, H->levels[0].Aop.df,
+                      /*acc=*/true);
+  });
   precondition(H, H->r.p, H->z.p, &sc->stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, sc, 1);
   TAM_LAUNCH_CHECK();
@@ -458,7 +484,10 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   }
   // final true residual, always a plain FP64 product; then x back to the caller's scale
   DBuf<double> rn(1, s);
-  sell_spmv<3, 3>(H->K->S, x, EpiResNorm<3>{b, H->K->n_nodes, gr, rn.p}, s, /*df=*/false);
+  by_block(H->K->A.br, [&](auto B) {
+    constexpr int BR = decltype(B)::value;
+    sell_spmv<BR, BR>(H->K->S, x, EpiResNorm<BR>{b, H->K->n_nodes, gr, rn.p}, s, /*df=*/false);
+  });
   pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(x, x, N, sc, +1);
   TAM_LAUNCH_CHECK();
   PcgScalars host;
@@ -494,7 +523,11 @@ void smooth_fine(tam_amg_s* H, const double* b, double* x, int degree, double lo
   double* cur = x;
   double* nxt = L.xb.p;
   for (int k = 0; k < degree; ++k) {
-    spop_apply<3, 3>(L.Aop, cur, EpiCheb<3>{b, cur, L.dinv.p, coef + 2 + 2 * k, L.d.p, nxt, L.n_rows, nullptr}, s);
+    by_block(L.bs, [&](auto B) {
+      constexpr int BR = decltype(B)::value;
+      spop_apply<BR, BR>(L.Aop, cur, EpiCheb<BR>{b, cur, L.dinv.p, coef + 2 + 2 * k, L.d.p, nxt, L.n_rows, nullptr},
+                         s);
+    });
     std::swap(cur, nxt);
   }
   if (cur != x) TAM_CUDA(cudaMemcpyAsync(x, cur, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, s));

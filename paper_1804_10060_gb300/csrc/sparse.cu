@@ -972,6 +972,7 @@ void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith 
   else if (m == 3 && k == 3 && n == 3) launch_numeric_any<3, 3, 3>(X, Y, C, arith, sp, s);
   else if (m == 6 && k == 6 && n == 3) launch_numeric_any<6, 6, 3>(X, Y, C, arith, sp, s);
   else if (m == 3 && k == 6 && n == 6) launch_numeric_any<3, 6, 6>(X, Y, C, arith, sp, s);
+  else if (m == 1 && k == 1 && n == 1) launch_numeric_any<1, 1, 1>(X, Y, C, arith, sp, s);
   else throw Error(TAM_ERR_UNSUPPORTED, "spgemm: block shape not instantiated");
 }
 

@@ -92,6 +92,15 @@ _SIGNATURES = {
     "tam_mlp_train_step": ([_vp, _ll, _vp, _vp, ctypes.c_float, _pd, _vp], _i),
     "tam_node_features": ([_i, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "tam_learned_guess": ([_vp, _vp, _vp, _vp, _i, _i, _vp, _pi, _pd, _vp], _i),
+    "tam_thermal_create": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _i, _vp, _vp, ctypes.POINTER(AmgParams),
+                            ctypes.POINTER(_vp), _vp], _i),
+    "tam_thermal_residual": ([_vp, _vp, _vp, _d, _d, _vp, _vp, _vp, _vp], _i),
+    "tam_thermal_export_jacobian": ([_vp, _vp, _vp, _vp, _pll, _vp], _i),
+    "tam_thermal_newton": ([_vp, _vp, _vp, _d, _d, _vp, _vp, _vp, _d, _i, _d, _i, _i, _pi, _pi, _pi, _pd, _vp],
+                           _i),
+    "tam_thermal_max_change": ([_vp, _vp, _ll, _pd, _vp], _i),
+    "tam_thermal_next_dt": ([_d, _d, _d, _d, _pd, _pi], _i),
+    "tam_thermal_destroy": ([_vp], _i),
     "tam_solve_elasticity_host": ([_i, _vp, _i, _i, _vp, _vp, _i, _vp, _vp, _d, _vp, _vp, _vp,
                                    ctypes.POINTER(AmgParams), _d, _i, _vp, _pi, _pd, _vp], _i),
 }
@@ -517,3 +526,99 @@ def problem_to_device(pb, device="cuda"):
                 cell_material=t(pb.cell_material, np.int32), mat_props=t(pb.mat_props, np.float64),
                 T=t(pb.T, np.float64), T_ref=pb.T_ref, body_force=t(pb.body_force, np.float64),
                 dirichlet_mask=t(pb.dirichlet_mask, np.uint8), u_dirichlet=t(pb.u_dirichlet, np.float64))
+
+
+# ---------------------------------------------------------------------------
+# The thermal problem (heat equation, theta-method, Newton)
+# ---------------------------------------------------------------------------
+class Thermal:
+    """Handle of a thermal problem on a mesh (device arrays kept alive here)."""
+
+    def __init__(self, coords, cells, cell_material, thermal_props, faces, dirichlet_mask=None, params=None,
+                 stream=None):
+        self._keep = [coords, cells, cell_material, faces, dirichlet_mask]
+        npc = int(cells.shape[1])
+        props = np.ascontiguousarray(np.asarray(thermal_props, dtype=np.float64))
+        h = _vp()
+        _check(lib.tam_thermal_create(int(coords.shape[0]), _dev(coords, torch.float64, "coords"), int(cells.shape[0]),
+                                      npc, _dev(cells, torch.int32, "cells"),
+                                      _dev(cell_material, torch.int32, "cell_material"), int(props.shape[0]),
+                                      props.ctypes.data_as(_vp), int(faces.shape[0]),
+                                      _dev(faces, torch.int32, "faces"),
+                                      _dev(dirichlet_mask, torch.uint8, "dirichlet_mask", allow_none=True),
+                                      ctypes.byref(params) if params is not None else None, ctypes.byref(h),
+                                      _stream(stream)))
+        self.handle = h
+        self.n = int(coords.shape[0])
+
+    def residual(self, T, T_old=None, dt=0.0, theta=1.0, beta=None, T_bc=None, stream=None):
+        F = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(lib.tam_thermal_residual(self.handle, _dev(T, torch.float64, "T"),
+                                        _dev(T_old, torch.float64, "T_old", allow_none=True), float(dt), float(theta),
+                                        _dev(beta, torch.float64, "beta", allow_none=True),
+                                        _dev(T_bc, torch.float64, "T_bc", allow_none=True), _dev(F, torch.float64, "F"),
+                                        _stream(stream)))
+        return F
+
+    def jacobian(self, stream=None):
+        """(row_ptr, col_idx, vals) of the last assembled Jacobian (device tensors)."""
+        nnz = ctypes.c_longlong()
+        _check(lib.tam_thermal_export_jacobian(self.handle, None, None, None, ctypes.byref(nnz), _stream(stream)))
+        rp = torch.empty(self.n + 1, dtype=torch.int32, device="cuda")
+        ci = torch.empty(max(nnz.value, 1), dtype=torch.int32, device="cuda")
+        v = torch.empty(max(nnz.value, 1), dtype=torch.float64, device="cuda")
+        _check(lib.tam_thermal_export_jacobian(self.handle, _vp(rp.data_ptr()), _vp(ci.data_ptr()), _vp(v.data_ptr()),
+                                               ctypes.byref(nnz), _stream(stream)))
+        return rp, ci[:nnz.value], v[:nnz.value]
+
+    def newton(self, T, T_old=None, dt=0.0, theta=1.0, beta=None, T_bc=None, T_dirichlet=None, rtol=1e-9,
+               max_newton=30, lin_rtol=1e-8, lin_max_iter=500, reuse=1, stream=None, raise_on_error=True):
+        """Newton on F(T) = 0 in place; returns dict(newton, linear, setups, rel, status)."""
+        it, li, su, rel = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        st = lib.tam_thermal_newton(self.handle, _dev(T, torch.float64, "T"),
+                                    _dev(T_old, torch.float64, "T_old", allow_none=True), float(dt), float(theta),
+                                    _dev(beta, torch.float64, "beta", allow_none=True),
+                                    _dev(T_bc, torch.float64, "T_bc", allow_none=True),
+                                    _dev(T_dirichlet, torch.float64, "T_dirichlet", allow_none=True), float(rtol),
+                                    int(max_newton), float(lin_rtol), int(lin_max_iter), int(reuse),
+                                    ctypes.byref(it), ctypes.byref(li), ctypes.byref(su), ctypes.byref(rel),
+                                    _stream(stream))
+        if raise_on_error:
+            _check(st)
+        return {"newton": it.value, "linear": li.value, "setups": su.value, "rel": rel.value, "status": st}
+
+    def destroy(self):
+        if self.handle:
+            lib.tam_thermal_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def tam_thermal_max_change(a, b, stream=None) -> float:
+    m = ctypes.c_double()
+    _check(lib.tam_thermal_max_change(_dev(a, torch.float64, "a"), _dev(b, torch.float64, "b"), int(a.numel()),
+                                      ctypes.byref(m), _stream(stream)))
+    return m.value
+
+
+def tam_thermal_next_dt(dt, max_change, dT_max, eps):
+    """Eq. dt_spec: (next dt, accepted)."""
+    d, ok = ctypes.c_double(), ctypes.c_int()
+    _check(lib.tam_thermal_next_dt(float(dt), float(max_change), float(dT_max), float(eps), ctypes.byref(d),
+                                   ctypes.byref(ok)))
+    return d.value, bool(ok.value)
+
+
+def thermal_to_device(tp, device="cuda"):
+    """Device tensors of a meshgen.ThermalProblem (mesh, faces, beta, T_bc, masks)."""
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+    out = dict(coords=t(tp.coords, np.float64), cells=t(tp.cells, np.int32), cell_material=t(tp.cell_material, np.int32),
+               faces=t(tp.faces, np.int32), beta=t(tp.beta, np.float64), T_bc=t(tp.T_bc, np.float64))
+    out["dirichlet_mask"] = t(tp.dirichlet_mask, np.uint8) if tp.dirichlet_mask is not None else None
+    out["T_dirichlet"] = t(tp.T_dirichlet, np.float64) if tp.T_dirichlet is not None else None
+    return out
