@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--setup-fp64", action="store_true",
                     help="--one-step: setup products in plain FP64 instead of double-float")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-guess variant and print it")
+    ap.add_argument("--no-transient", action="store_true", help="skip the transient thermoelastic variant")
+    ap.add_argument("--transient-only", action="store_true", help="run only the transient variant and print it")
     ap.add_argument("--dims", default=None, help="override box hexes, e.g. 64x16x16 (testing only)")
     ap.add_argument("--one-step", action="store_true",
                     help="run exactly one assemble+setup+solve (profiling target) and exit")
@@ -452,6 +454,8 @@ def native_arm(args):
         variants["batched_64_cases_8_meshes"] = batched_variant(tam, meshgen, stream, flush, world)
     if not args.no_learned:
         variants["learned_initial_guess"] = learned_variant(tam, meshgen, stream, world)
+    if not args.no_transient:
+        variants["transient_thermoelastic"] = transient_variant(tam, meshgen, stream, world)
 
     if rank != 0:
         return
@@ -766,6 +770,92 @@ def learned_variant(tam, meshgen, stream, world, n_train=16, train_steps=1500, e
     return out
 
 
+# the paper's transient: backward Euler, the time step adapted to at most 10 K
+# change per step (Eq. dt_spec), the thermal problem first, then the elastic
+# one with the new temperature (one-way coupling), on a P2 bladed disc
+TRANSIENT_DISC = dict(n_r=49, n_theta_per_blade=4, n_z=5, n_blades=48, n_r_blade=8, degree=2, blade_fraction=0.5)
+TRANSIENT_WORKLOAD = ("transient thermoelastic heating of a 48-blade P2 disc (305,280 tets): thermal Newton "
+                      "(theta = 1, c_v and kappa linear in T, hot-gas Robin faces on the rim and blades, cooled "
+                      "bore) on 460,416 DOF, then the elastic solve (1,381,248 DOF, centrifugal + thermal load, "
+                      "rtol 1e-8) per step; adaptive dt with dT_max 10 K, eps 0.8; hierarchies and the previous "
+                      "solution reused across steps vs rebuilt from scratch every step")
+
+
+def transient_variant(tam, meshgen, stream, world, n_steps=10):
+    """Time per accepted step with the preconditioners and previous solutions reused
+    (thermal hierarchy kept while it serves, elastic hierarchy from step 0, u_m as the
+    initial guess) against rebuilding them every step and starting from zero."""
+    import torch
+    pb = meshgen.bladed_disc_problem(**TRANSIENT_DISC, seed=7)
+    n = pb.n_nodes
+    dev = tam.problem_to_device(pb)
+
+    def run(reuse):
+        tp0 = meshgen.disc_thermal_problem(pb, t=0.0)
+        d0 = tam.thermal_to_device(tp0)
+        T = torch.full((n,), 300.0, dtype=torch.float64, device="cuda")
+        u = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+        gpu_ms = 0.0
+        rec = {"thermal_newton": 0, "thermal_cg": 0, "thermal_setups": 0, "elastic_cg": [], "rejected": 0,
+               "elastic_setups": 0}
+        with torch.cuda.stream(stream):
+            t0 = time.perf_counter()
+            th = tam.Thermal(d0["coords"], d0["cells"], d0["cell_material"], tp0.thermal_props, d0["faces"],
+                             stream=stream)
+            K, _ = tam.fem_assemble_elasticity(**dict(dev, T=T), stream=stream)
+            H = tam.amg_setup(K, dev["coords"], stream=stream)
+            rec["elastic_setups"] += 1
+            torch.cuda.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            t, dt, steps = 0.0, 0.02, 0
+            while steps < n_steps:
+                tp = meshgen.disc_thermal_problem(pb, t=t + dt)       # boundary data at t_{m+1} (host input)
+                beta = torch.from_numpy(tp.beta).cuda()
+                Tbc = torch.from_numpy(tp.T_bc).cuda()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                Tn = T.clone()
+                st = th.newton(Tn, T_old=T, dt=dt, theta=1.0, beta=beta, T_bc=Tbc, rtol=1e-9, lin_rtol=1e-8,
+                               reuse=1 if reuse else 0, stream=stream)
+                ch = tam.tam_thermal_max_change(Tn, T, stream=stream)
+                dt_next, ok = tam.tam_thermal_next_dt(dt, ch, 10.0, 0.8)
+                rec["thermal_newton"] += st["newton"]
+                rec["thermal_cg"] += st["linear"]
+                rec["thermal_setups"] += st["setups"]
+                if ok:
+                    b = tam.fem_assemble_load(K, **dict(dev, T=Tn), stream=stream)
+                    if not reuse:
+                        H.destroy()
+                        H = tam.amg_setup(K, dev["coords"], stream=stream)
+                        rec["elastic_setups"] += 1
+                        u.zero_()
+                    it, rel, s = tam.amg_pcg_solve(H, b, u, rtol=1e-8, stream=stream)
+                    rec["elastic_cg"].append(it)
+                    T, t, steps = Tn, t + dt, steps + 1
+                else:
+                    rec["rejected"] += 1
+                dt = dt_next
+                torch.cuda.synchronize()
+                gpu_ms += (time.perf_counter() - t0) * 1e3
+            H.destroy()
+            K.destroy()
+            th.destroy()
+        rec.update(ms_per_step=gpu_ms / n_steps, setup_ms_before_first_step=setup_ms, t_end=t,
+                   T_max=float(T.max()), elastic_cg_per_step=sum(rec["elastic_cg"]) / n_steps)
+        return rec
+
+    run(True)   # warm-up (module load, pools)
+    reused = run(True)
+    rebuilt = run(False)
+    dof = pb.n_dof + n
+    return {"workload": TRANSIENT_WORKLOAD, "thermal_dof": n, "elastic_dof": pb.n_dof, "steps": n_steps,
+            "value": world * dof / (reused["ms_per_step"] * 1e-3), "unit": "DOF/s (thermal + elastic DOF per step)",
+            "reused": reused, "rebuilt_every_step": rebuilt,
+            "speedup_from_reuse": rebuilt["ms_per_step"] / reused["ms_per_step"],
+            "timing": "host wall time of the library calls per accepted step (synchronising calls), boundary "
+                      "data generation excluded"}
+
+
 def spmv_only(args):
     """Assemble the box and launch only tam_matrix_spmv (a small, single-kernel profiling target)."""
     import torch
@@ -847,6 +937,14 @@ def main():
         stream = torch.cuda.Stream()
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         print(json.dumps(batched_variant(tam, meshgen, stream, flush, 1)), flush=True)
+        return
+    if args.transient_only:
+        import torch
+
+        from paper_1804_10060_gb300 import meshgen
+        from paper_1804_10060_gb300 import thermoamg as tam
+        stream = torch.cuda.Stream()
+        print(json.dumps(transient_variant(tam, meshgen, stream, 1)), flush=True)
         return
     if args.disc_only:
         import torch
