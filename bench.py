@@ -588,7 +588,7 @@ def batched_variant(tam, meshgen, stream, flush, world, reps=2):
                                                     [s["X"] for s in sys_], rtol=1e-8, stream=stream)
         rec.update(iters=its, rels=rels, status=st)
 
-    def sequential_step(keep=None):
+    def sequential_step(keep=None, hkey="H64"):
         its = []
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
@@ -596,7 +596,7 @@ def batched_variant(tam, meshgen, stream, flush, world, reps=2):
                 for k in range(s["B"].shape[0]):
                     b = loads(s, k, None)
                     x = torch.zeros_like(b)
-                    it, rel, st = tam.amg_pcg_solve(s["H64"], b, x, rtol=1e-8, stream=stream)
+                    it, rel, st = tam.amg_pcg_solve(s[hkey], b, x, rtol=1e-8, stream=stream)
                     its.append(it)
                     if keep is not None:
                         keep.append(x.reshape(-1))
@@ -623,6 +623,8 @@ def batched_variant(tam, meshgen, stream, flush, world, reps=2):
     ms_b = timed(batched_step)
     launches_b = (tam.kernel_launches() - launches0) // reps
     ms_s = timed(sequential_step)
+    seq32_its = sequential_step(hkey="H32")
+    ms_s32 = timed(lambda: sequential_step(hkey="H32"))
     # per-result error of the batched FP32-V-cycle solutions against the FP64 path's
     errs = []
     j = 0
@@ -630,7 +632,8 @@ def batched_variant(tam, meshgen, stream, flush, world, reps=2):
         for k in range(s["B"].shape[0]):
             errs.append(float(torch.linalg.norm(s["X"][k] - ref[j]) / torch.linalg.norm(ref[j])))
             j += 1
-    tiles = {s["pb"].name + f"_{s['pb'].n_dof}": tam.amg_batch_tiles(s["H32"])[0] for s in sys_}
+    tiles = {s["pb"].name + f"_{s['pb'].n_dof}": [tuple(t[i:i + 3]) for i in range(0, len(t), 3)]
+             for s in sys_ for t in [tam.amg_batch_tiles(s["H32"])[0]]}
     tune_ms = sum(tam.amg_batch_tiles(s["H32"])[1] for s in sys_)
     for s in sys_:
         s["H32"].destroy()
@@ -645,6 +648,9 @@ def batched_variant(tam, meshgen, stream, flush, world, reps=2):
             "fp64_one_by_one": {"value": world * dof_solves / (ms_s * 1e-3), "unit": "DOF/s", "ms_per_step": ms_s,
                                 "iterations_max": max(seq_its)},
             "speedup_vs_fp64_one_by_one": ms_s / ms_b,
+            "fp32_vcycle_one_by_one": {"value": world * dof_solves / (ms_s32 * 1e-3), "unit": "DOF/s",
+                                       "ms_per_step": ms_s32, "iterations_max": max(seq32_its)},
+            "speedup_vs_fp32_one_by_one": ms_s32 / ms_b,
             "setup_ms": {"fp32_hierarchies_incl_assembly": t_setup["fp32"], "fp64_hierarchies_incl_assembly":
                          t_setup["fp64"], "first_batched_call_ms_incl_autotune": first_ms, "autotune_ms": tune_ms},
             "tiles": tiles}

@@ -286,7 +286,9 @@ int amg_vcycle(tam_amg amg, const double* r, double* z, void* stream);
  * the vectors the double-float and FP32 products see sit inside FP32's
  * exponent range whatever the units of the problem; the scaling is exact (in
  * range the iterates are the unscaled ones times that power of two) and x is
- * scaled back before return.  Synchronising (once per check interval).
+ * scaled back before return.  The iterations run as one CUDA graph launch (a
+ * device-side loop over one captured iteration, ended by the stopping test),
+ * so the host waits once per solve.  Synchronising.
  * Errors: NOT_CONVERGED (x holds the last iterate), BREAKDOWN,
  * INDEFINITE_PRECOND, NAN, INVALID_ARG, CUDA. */
 int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double atol, int max_iter,
@@ -304,11 +306,12 @@ int amg_destroy(tam_amg amg);
  * side runs its own CG with its own stopping test ||r|| <= max(rtol ||b||,
  * atol); all SpMVs are multi-vector products: FP64 with K, FP32 in the
  * V-cycle (BF16 finest values for a hierarchy built with level_precision 2;
- * FP64 coarsest solve).  One CUDA graph advances every system by one
- * iteration (systems on parallel branches) and is replayed until all have
- * stopped.  The first call for a hierarchy and RHS count builds the FP32
- * copies and workspaces and times the candidate RHS tiles of every operator
- * (1, 2, 4 or 8 right-hand sides per thread), keeping the fastest.
+ * FP64 coarsest solve).  One CUDA graph launch runs the whole batch: a
+ * device-side loop whose body advances every system by one iteration (systems
+ * on parallel branches) until all have stopped.  The first call for a hierarchy and RHS count builds the FP32
+ * copies and workspaces and tunes the launch shape of every operator by
+ * timing candidates: right-hand sides per thread (1, 2, 4, 8), threads per
+ * CTA (64, 128, 256) and, for the block-CSR layouts, lanes per block row.
  * iters_host / rel_host (may be NULL): per right-hand side, systems in order.
  * Synchronising.  Errors: INVALID_ARG, NOT_CONVERGED, BREAKDOWN,
  * INDEFINITE_PRECOND, NAN, CUDA. */
@@ -316,9 +319,10 @@ int amg_pcg_solve_batch(int n_systems, const tam_amg* amg, const int* n_rhs, con
                         double* const* X, double rtol, double atol, int max_iter, int* iters_host,
                         double* rel_host, void* stream);
 
-/* RHS tiles chosen by the autotuner for `amg`: tiles[0] = K, then (A, P, R)
- * per smoothed level; returns the count in *n (host ints, cap entries) and the
- * tuning time in *tune_ms_host. */
+/* Launch shapes chosen by the autotuner for `amg`, as triples (right-hand
+ * sides per thread, threads per CTA, lanes per block row or 0 = as planned):
+ * K first, then (A, P, R) per smoothed level; *n receives the number of ints
+ * written (at most cap) and *tune_ms_host the tuning time. */
 int amg_batch_tiles(tam_amg amg, int* tiles_host, int cap, int* n, double* tune_ms_host);
 
 /* ------------------------------------------------------------------------

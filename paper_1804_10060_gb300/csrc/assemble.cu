@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(PAT_WARPS * 32)
 pattern_kernel(int n_nodes, int npc, const int* __restrict__ cells, const int* __restrict__ inc_ptr,
                const int* __restrict__ inc, const unsigned char* __restrict__ dmask,
                int* __restrict__ row_cnt, const int* __restrict__ row_ptr, int* __restrict__ col_idx,
-               int* __restrict__ overflow) {
+               int* __restrict__ overflow, int* __restrict__ big_list = nullptr, int big_cap = 0) {
   __shared__ int buf_all[PAT_WARPS][PAT_CAP];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * PAT_WARPS + wid;
@@ -84,7 +84,11 @@ pattern_kernel(int n_nodes, int npc, const int* __restrict__ cells, const int* _
   const int n_cand = di ? 1 : 1 + (e - s) * npc;
   if (n_cand > PAT_CAP) {
     if (lane == 0) {
-      atomicExch(overflow, 1);
+      // rows beyond the shared-memory capacity: to pattern_big_kernel when a
+      // list is given (it writes the count), else reported
+      const int k = big_list ? atomicAdd(overflow + 1, 1) : -1;
+      if (k >= 0 && k < big_cap) big_list[k] = i;
+      else atomicExch(overflow, 1);
       if (row_cnt) row_cnt[i] = FILL ? 0 : 1;
     }
     return;
@@ -130,11 +134,84 @@ pattern_kernel(int n_nodes, int npc, const int* __restrict__ cells, const int* _
 }
 
 // Candidate count of each row (upper bound of its pattern length): self plus
-// the nodes of its incident cells; 1 for a Dirichlet row.
+// the nodes of its incident cells; 1 for a Dirichlet row.  A row with more
+// candidates than the warp builder's shared memory holds (PAT_CAP) gets three
+// times that room: its candidates are sorted in global memory in the upper
+// two thirds (padded to a power of two) and its columns written to the front.
 __global__ void pattern_bound_kernel(int n_nodes, int npc, const int* __restrict__ inc_ptr,
                                      const unsigned char* __restrict__ dmask, int* __restrict__ bound) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_nodes) bound[i] = dmask[i] ? 1 : 1 + (inc_ptr[i + 1] - inc_ptr[i]) * npc;
+  if (i >= n_nodes) return;
+  const int b = dmask[i] ? 1 : 1 + (inc_ptr[i + 1] - inc_ptr[i]) * npc;
+  bound[i] = b > PAT_CAP ? 3 * b : b;
+}
+
+// One block per row whose candidates exceed PAT_CAP (the list built by
+// pattern_kernel): candidates gathered into the row's scratch range, padded
+// with INT_MAX to a power of two, bitonic-sorted by the block in global
+// memory, then the distinct ones compacted to the front of the range
+// (block-wide scan of the keep flags) and the count written to row_cnt.
+constexpr int BIG_THREADS = 256;
+
+__global__ void __launch_bounds__(BIG_THREADS)
+pattern_big_kernel(const int* __restrict__ list, int npc, const int* __restrict__ cells,
+                   const int* __restrict__ inc_ptr, const int* __restrict__ inc, const unsigned char* __restrict__ dmask,
+                   const int* __restrict__ bptr, int* __restrict__ tmp, int* __restrict__ row_cnt) {
+  __shared__ int wsum[BIG_THREADS / 32];
+  __shared__ int carry;
+  const int i = list[blockIdx.x];
+  const int s = inc_ptr[i], e = inc_ptr[i + 1];
+  const int n = 1 + (e - s) * npc;
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  int* cand = tmp + bptr[i] + n;  // [n, n + n2) of the 3n range
+  int* outp = tmp + bptr[i];
+  for (int t = threadIdx.x; t < n2; t += BIG_THREADS) {
+    int v = 0x7fffffff;
+    if (t == 0) v = i;
+    else if (t < n) {
+      const int j = cells[(size_t)inc[s + (t - 1) / npc] * npc + (t - 1) % npc];
+      if (!dmask[j]) v = j;
+    }
+    cand[t] = v;
+  }
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < n2; t += BIG_THREADS) {
+        const int x = t ^ j;
+        if (x > t) {
+          const int a = cand[t], b = cand[x];
+          if ((a > b) == ((t & k) == 0)) {
+            cand[t] = b;
+            cand[x] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < n2; base += BIG_THREADS) {
+    const int t = base + threadIdx.x;
+    const int v = t < n2 ? cand[t] : 0x7fffffff;
+    const int keep = (v != 0x7fffffff) && (t == 0 || cand[t - 1] != v);
+    int x = keep;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    int off = carry;
+    for (int w = 0; w < wid; ++w) off += wsum[w];
+    if (keep) outp[off + x - 1] = v;
+    __syncthreads();
+    if (threadIdx.x == BIG_THREADS - 1) carry = off + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) row_cnt[i] = carry;
 }
 
 // Rows written at their bound offsets in tmp, packed into col_idx (warp per row).
@@ -477,10 +554,10 @@ void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, con
   A.n_rows = A.n_cols = n_nodes;
   A.row_ptr = DBuf<int>((size_t)n_nodes + 1, s);
   unsigned pg = grid_for(n_nodes, PAT_WARPS);
-  if ((long long)n_nodes + (long long)npc * npc * n_cells < (1LL << 31)) {
+  if (3 * ((long long)n_nodes + (long long)npc * npc * n_cells) < (1LL << 31)) {
     // one sort pass: each row's sorted unique columns go to its candidate-
     // bound offset in a scratch array (the bounds' sum, at most
-    // n_nodes + npc^2 n_cells, fits the int32 scan), the counts give
+    // 3 (n_nodes + npc^2 n_cells), fits the int32 scan), the counts give
     // row_ptr, then pack
     DBuf<int> bptr((size_t)n_nodes + 1, s);
     pattern_bound_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, npc, inc_ptr.p, dmask, bptr.p);
@@ -488,13 +565,23 @@ void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, con
     exclusive_scan_i32(bptr.p, bptr.p, n_nodes, s);
     const long long total = read_back_int(bptr.p + n_nodes, s);
     DBuf<int> tmp((size_t)std::max(1LL, total), s);
+    // flag[1]: overflow beyond the list; big[0]: rows listed for pattern_big_kernel
+    const int big_cap = std::max(1, std::min(n_nodes, 1 << 20));
+    DBuf<int> big_list((size_t)big_cap, s), big(2, s);
+    big.zero();
     pattern_kernel<true><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
-                                                      bptr.p, tmp.p, flag + 1);
+                                                      bptr.p, tmp.p, big.p, big_list.p, big_cap);
     TAM_LAUNCH_CHECK();
+    int n_big = 0, big_over = 0;
+    read_back_int2(big.p + 1, big.p, &n_big, &big_over, s);
+    TAM_CHECK(big_over == 0, TAM_ERR_UNSUPPORTED, "fem_assemble: too many high-valence nodes for the pattern builder");
+    if (n_big > 0) {
+      pattern_big_kernel<<<n_big, BIG_THREADS, 0, s>>>(big_list.p, npc, cells, inc_ptr.p, inc.p, dmask, bptr.p, tmp.p,
+                                                      A.row_ptr.p);
+      TAM_LAUNCH_CHECK();
+    }
     exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
     A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
-    TAM_CHECK(read_back_int(flag + 1, s) == 0, TAM_ERR_UNSUPPORTED,
-              "fem_assemble: a node has too many incident cells for the pattern builder");
     A.col_idx = DBuf<int>((size_t)std::max(1LL, A.nnzb), s);
     pattern_pack_kernel<<<grid_for((long long)n_nodes * 32, 256), 256, 0, s>>>(n_nodes, bptr.p, tmp.p,
                                                                                A.row_ptr.p, A.col_idx.p);

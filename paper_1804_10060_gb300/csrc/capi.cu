@@ -347,7 +347,7 @@ int amg_pcg_solve_batch(int n_systems, const tam_amg* amg, const int* n_rhs, con
 int amg_batch_tiles(tam_amg amg, int* tiles_host, int cap, int* n, double* tune_ms_host) {
   return guarded([&] {
     TAM_CHECK(amg, TAM_ERR_INVALID_ARG, "amg_batch_tiles: NULL handle");
-    int count = amg->multi ? 1 + 3 * (int)(amg->levels.size() - 1) : 0;
+    int count = amg->multi ? 3 * (1 + 3 * (int)(amg->levels.size() - 1)) : 0;
     if (tiles_host) multi_tiles(amg, tiles_host, cap);
     if (n) *n = std::min(count, cap);
     if (tune_ms_host) *tune_ms_host = multi_tune_ms(amg);

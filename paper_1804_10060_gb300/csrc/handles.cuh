@@ -2,6 +2,7 @@
 // the C ABI wraps.
 #pragma once
 
+#include <functional>
 #include <memory>
 #include <vector>
 
@@ -34,6 +35,7 @@ struct PcgScalars {
   int stop;         // nonzero: every solver kernel returns at entry
   int status;       // TAM_OK or a TAM_ERR_* code
   int scale_exp;    // the solve runs on b 2^-scale_exp and x 2^-scale_exp (exact)
+  int loops;        // iterations the device-side loop has run (its failsafe count)
 };
 
 struct Level {
@@ -67,9 +69,16 @@ struct Level {
 // Multi-right-hand-side solve state (block of independent CGs sharing every
 // SpMV as a multi-vector product).  Vectors are interleaved [rows][bs][mp]
 // with the RHS index fastest; mp = RHS count padded to a multiple of 8.
+// Launch shape of one multi-RHS SpMM, picked by the autotuner: right-hand
+// sides per thread, threads per CTA (rows per CTA for thread-per-row SELL),
+// and lanes per block row for the block-CSR layout (0: the operator's own).
+struct MTile {
+  int tm = 8, threads = 128, lpr = 0;
+};
+
 struct MultiLevel {
   DBuf<float> b, xa, xb, d, t, y;
-  int tmA = 8, tmP = 8, tmR = 8;  // RHS per thread, picked by the autotuner
+  MTile tA, tP, tR;
 };
 
 struct MultiState {
@@ -80,7 +89,7 @@ struct MultiState {
   DBuf<double> partials;
   DBuf<unsigned int> tickets;     // one per RHS chunk
   std::vector<MultiLevel> lv;
-  int tmK = 8;
+  MTile tK;
   cudaGraphExec_t exec = nullptr;
   double* graph_x = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -157,6 +166,15 @@ void multi_tiles(tam_amg_s* H, int* out, int cap);
 
 int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
               double* rel, cudaStream_t s);
+
+// A CUDA graph whose one conditional WHILE node repeats the work enqueue(s)
+// puts on a stream (captured once as the node's body, followed by a one-thread
+// kernel that sets the loop condition) for as long as the device flag *stop is
+// 0 -- no host round trip per iteration.  Failsafe: at most *limit + limit_add
+// passes, counted in *count, which must be zero when the graph is launched.
+// *body_kernels receives the body's kernel count.
+cudaGraphExec_t build_loop_graph(const std::function<void(cudaStream_t)>& enqueue, const int* stop, int* count,
+                                 const int* limit, int limit_add, long long* body_kernels);
 
 void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s);
 double residual_norm_K(tam_matrix_s* K, const double* b, const double* x, cudaStream_t s);

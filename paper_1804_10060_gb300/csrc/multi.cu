@@ -23,6 +23,7 @@ namespace {
 constexpr int TPB = 256;
 constexpr int TMAX = 8;    // RHS per thread, compile-time register tile
 constexpr int MPMAX = 16;  // RHS per system
+constexpr int MT_MIN_THREADS = 64, MT_MAX_THREADS = 256;  // CTA sizes the autotuner tries
 enum { S_RHO = 0, S_ALPHA, S_BETA, S_RR, S_TOL2, S_BB, S_DONE, S_ITER, S_SCALE, S_COUNT };
 
 // 2^e for |e| <= 1000, built from its bits (exact)
@@ -199,11 +200,11 @@ __global__ void mdir_kernel(const double* __restrict__ z, double* __restrict__ p
 // DF: double-float products on K's split values (each value feeds tm
 // right-hand sides, so the FP64 version is far past GB300's FP64 rate).
 template <class Epi, bool DF>
-__global__ void __launch_bounds__(SPMV_THREADS)
+__global__ void __launch_bounds__(MT_MAX_THREADS)
 kspmm_kernel(SellView A, const double* __restrict__ x, int mp, int tm, Epi epi) {
   __shared__ double sh[32];
   if (epi.skip()) return;
-  const int pos = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   const int slice = pos >> 5, lane = pos & 31;
   const int row = sell_row(A.perm, pos, A.n_rows);
   const int j0 = blockIdx.y * tm;
@@ -364,12 +365,12 @@ struct EpiStoreKM {
 // df: the double-float kernel on K's split values (the hierarchy's level-0
 // choice, amg_params.spmv_fp64); false: plain FP64.
 template <class Epi>
-void kspmm(const Sell& S, const double* x, int mp, int tm, Epi epi, cudaStream_t s, bool df) {
-  dim3 g(sell_grid(S), mp / tm);
+void kspmm(const Sell& S, const double* x, int mp, const MTile& t, Epi epi, cudaStream_t s, bool df) {
+  dim3 g(grid_for((long long)S.n_slices * 32, t.threads), mp / t.tm);
   if (df && S.vals_df.p)
-    kspmm_kernel<Epi, true><<<g, SPMV_THREADS, 0, s>>>(view(S), x, mp, tm, epi);
+    kspmm_kernel<Epi, true><<<g, t.threads, 0, s>>>(view(S), x, mp, t.tm, epi);
   else
-    kspmm_kernel<Epi, false><<<g, SPMV_THREADS, 0, s>>>(view(S), x, mp, tm, epi);
+    kspmm_kernel<Epi, false><<<g, t.threads, 0, s>>>(view(S), x, mp, t.tm, epi);
   TAM_LAUNCH_CHECK();
 }
 
@@ -377,11 +378,11 @@ void kspmm(const Sell& S, const double* x, int mp, int tm, Epi epi, cudaStream_t
 // FP32 multi-vector SpMM for the V-cycle (SELL or lanes-per-row layouts)
 // -------------------------------------------------------------------------
 template <int BR, int BC, typename TV, class Epi>
-__global__ void __launch_bounds__(SPMV_THREADS)
+__global__ void __launch_bounds__(MT_MAX_THREADS)
 msell_kernel(int n_slices, const int* __restrict__ slice_ptr, const int* __restrict__ cols, const TV* __restrict__ vals,
              const float* __restrict__ x, int mp, int tm, const int* __restrict__ perm, Epi epi) {
   if (epi.skip()) return;
-  const int pos = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   const int slice = pos >> 5, lane = pos & 31;
   const int row = sell_row(perm, pos, epi.n_rows);
   const int j0 = blockIdx.y * tm;
@@ -417,11 +418,11 @@ msell_kernel(int n_slices, const int* __restrict__ slice_ptr, const int* __restr
 }
 
 template <int BR, int BC, typename TV, class Epi>
-__global__ void __launch_bounds__(SPMV_THREADS)
+__global__ void __launch_bounds__(MT_MAX_THREADS)
 mvec_kernel(int n_rows, const int* __restrict__ rp, const int* __restrict__ ci, const TV* __restrict__ v,
             const float* __restrict__ x, int mp, int tm, int lpr_log2, Epi epi) {
   if (epi.skip()) return;
-  const int t = blockIdx.x * SPMV_THREADS + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int lpr = 1 << lpr_log2;
   const int row = t >> lpr_log2, sub = t & (lpr - 1);
   const int j0 = blockIdx.y * tm;
@@ -528,20 +529,21 @@ struct EpiPutMF {
 };
 
 template <int BR, int BC, typename TV, class Epi>
-void mspmm(const SpOpLow<TV>& o, const float* x, int mp, int tm, Epi epi, cudaStream_t s) {
+void mspmm(const SpOpLow<TV>& o, const float* x, int mp, const MTile& t, Epi epi, cudaStream_t s) {
   const SpOp& op = o.op;
   if (op.lpr == 0) {
     const Sell& S = *op.S;
-    dim3 g(sell_grid(S), mp / tm);
-    msell_kernel<BR, BC, TV, Epi><<<g, SPMV_THREADS, 0, s>>>(S.n_slices, S.slice_ptr.p, S.cols.p, o.vals, x, mp, tm, S.perm.p,
-                                                              epi);
+    dim3 g(grid_for((long long)S.n_slices * 32, t.threads), mp / t.tm);
+    msell_kernel<BR, BC, TV, Epi><<<g, t.threads, 0, s>>>(S.n_slices, S.slice_ptr.p, S.cols.p, o.vals, x, mp, t.tm,
+                                                          S.perm.p, epi);
   } else {
     const Bsr& B = *op.B;
+    const int lpr = t.lpr ? t.lpr : op.lpr;
     int lg = 0;
-    while ((1 << lg) < op.lpr) ++lg;
-    dim3 g(grid_for((long long)B.n_rows * op.lpr, SPMV_THREADS), mp / tm);
-    mvec_kernel<BR, BC, TV, Epi><<<g, SPMV_THREADS, 0, s>>>(B.n_rows, B.row_ptr.p, B.col_idx.p, o.vals, x, mp, tm,
-                                                             lg, epi);
+    while ((1 << lg) < lpr) ++lg;
+    dim3 g(grid_for((long long)B.n_rows << lg, t.threads), mp / t.tm);
+    mvec_kernel<BR, BC, TV, Epi><<<g, t.threads, 0, s>>>(B.n_rows, B.row_ptr.p, B.col_idx.p, o.vals, x, mp, t.tm, lg,
+                                                         epi);
   }
   TAM_LAUNCH_CHECK();
 }
@@ -574,9 +576,9 @@ __global__ void mcoarse_kernel(const double* __restrict__ A, const TI* __restric
 
 // A x on a level with its FP32 / BF16 values
 template <int BS, class Epi>
-void level_mspmm(const Level& L, const float* x, int mp, int tm, Epi epi, cudaStream_t s) {
-  if (L.A16.vals) mspmm<BS, BS, __nv_bfloat16>(L.A16, x, mp, tm, epi, s);
-  else mspmm<BS, BS, float>(L.A32, x, mp, tm, epi, s);
+void level_mspmm(const Level& L, const float* x, int mp, const MTile& t, Epi epi, cudaStream_t s) {
+  if (L.A16.vals) mspmm<BS, BS, __nv_bfloat16>(L.A16, x, mp, t, epi, s);
+  else mspmm<BS, BS, float>(L.A32, x, mp, t, epi, s);
 }
 
 template <typename TB, typename TO>
@@ -584,31 +586,31 @@ void mcheb(const Level& L, const MultiLevel& ML, const TB* b, const float* x, TO
            const int* stop, cudaStream_t s) {
   const float* coef = L.consts32.p + 2 + 2 * step;
   if (L.bs == 3)
-    level_mspmm<3>(L, x, mp, ML.tmA, EpiChebMF<3, TB, TO>{b, x, L.dinv32.p, coef, ML.d.p, xn, L.n_rows, mp, stop}, s);
+    level_mspmm<3>(L, x, mp, ML.tA, EpiChebMF<3, TB, TO>{b, x, L.dinv32.p, coef, ML.d.p, xn, L.n_rows, mp, stop}, s);
   else
-    level_mspmm<6>(L, x, mp, ML.tmA, EpiChebMF<6, TB, TO>{b, x, L.dinv32.p, coef, ML.d.p, xn, L.n_rows, mp, stop}, s);
+    level_mspmm<6>(L, x, mp, ML.tA, EpiChebMF<6, TB, TO>{b, x, L.dinv32.p, coef, ML.d.p, xn, L.n_rows, mp, stop}, s);
 }
 
 template <typename TB>
 void mresidual(const Level& L, const MultiLevel& ML, const TB* b, const float* x, int mp, const int* stop,
                cudaStream_t s) {
-  if (L.bs == 3) level_mspmm<3>(L, x, mp, ML.tmA, EpiResMF<3, TB>{b, ML.t.p, L.n_rows, mp, stop}, s);
-  else level_mspmm<6>(L, x, mp, ML.tmA, EpiResMF<6, TB>{b, ML.t.p, L.n_rows, mp, stop}, s);
+  if (L.bs == 3) level_mspmm<3>(L, x, mp, ML.tA, EpiResMF<3, TB>{b, ML.t.p, L.n_rows, mp, stop}, s);
+  else level_mspmm<6>(L, x, mp, ML.tA, EpiResMF<6, TB>{b, ML.t.p, L.n_rows, mp, stop}, s);
 }
 
 void mrestrict(const Level& L, const MultiLevel& ML, float* bc, int mp, const int* stop, cudaStream_t s) {
   const int nr = L.R.n_rows;
-  if (L.kdim == 6 && L.bs == 3) mspmm<6, 3, float>(L.R32, ML.t.p, mp, ML.tmR, EpiPutMF<6, false>{bc, nr, mp, stop}, s);
-  else if (L.kdim == 6) mspmm<6, 6, float>(L.R32, ML.t.p, mp, ML.tmR, EpiPutMF<6, false>{bc, nr, mp, stop}, s);
-  else mspmm<3, 3, float>(L.R32, ML.t.p, mp, ML.tmR, EpiPutMF<3, false>{bc, nr, mp, stop}, s);
+  if (L.kdim == 6 && L.bs == 3) mspmm<6, 3, float>(L.R32, ML.t.p, mp, ML.tR, EpiPutMF<6, false>{bc, nr, mp, stop}, s);
+  else if (L.kdim == 6) mspmm<6, 6, float>(L.R32, ML.t.p, mp, ML.tR, EpiPutMF<6, false>{bc, nr, mp, stop}, s);
+  else mspmm<3, 3, float>(L.R32, ML.t.p, mp, ML.tR, EpiPutMF<3, false>{bc, nr, mp, stop}, s);
 }
 
 void mprolong(const Level& L, const MultiLevel& ML, const float* xc, float* x, int mp, const int* stop,
               cudaStream_t s) {
   const int nr = L.P.n_rows;
-  if (L.kdim == 6 && L.bs == 3) mspmm<3, 6, float>(L.P32, xc, mp, ML.tmP, EpiPutMF<3, true>{x, nr, mp, stop}, s);
-  else if (L.kdim == 6) mspmm<6, 6, float>(L.P32, xc, mp, ML.tmP, EpiPutMF<6, true>{x, nr, mp, stop}, s);
-  else mspmm<3, 3, float>(L.P32, xc, mp, ML.tmP, EpiPutMF<3, true>{x, nr, mp, stop}, s);
+  if (L.kdim == 6 && L.bs == 3) mspmm<3, 6, float>(L.P32, xc, mp, ML.tP, EpiPutMF<3, true>{x, nr, mp, stop}, s);
+  else if (L.kdim == 6) mspmm<6, 6, float>(L.P32, xc, mp, ML.tP, EpiPutMF<6, true>{x, nr, mp, stop}, s);
+  else mspmm<3, 3, float>(L.P32, xc, mp, ML.tP, EpiPutMF<3, true>{x, nr, mp, stop}, s);
 }
 
 template <typename TB, typename TO>
@@ -667,16 +669,42 @@ float time_ms(F&& launch, cudaStream_t s) {
   return ms;
 }
 
+// Coordinate search over the launch shape of one operator: RHS per thread
+// (1, 2, 4, 8), then threads per CTA (64, 128, 256), then -- for the
+// block-CSR layout -- lanes per block row (half, the planned, double), each
+// candidate timed once (warm-up + 3 launches) with the others fixed.
 template <class F>
-int pick_tm(int mp, F&& run, cudaStream_t s) {
-  int best = 1;
+MTile pick_tile(int mp, int planned_lpr, F&& run, cudaStream_t s) {
+  MTile best;
   float best_ms = 1e30f;
-  for (int tm : {1, 2, 4, 8}) {
-    if (tm > mp || mp % tm) continue;
-    const float ms = time_ms([&] { run(tm); }, s);
+  auto consider = [&](MTile t) {
+    const float ms = time_ms([&] { run(t); }, s);
     if (ms < best_ms) {
       best_ms = ms;
-      best = tm;
+      best = t;
+    }
+  };
+  MTile t0;
+  for (int tm : {1, 2, 4, 8}) {
+    if (tm > mp || mp % tm) continue;
+    MTile t = t0;
+    t.tm = tm;
+    consider(t);
+  }
+  const MTile after_tm = best;
+  for (int th : {MT_MIN_THREADS, 128, MT_MAX_THREADS}) {
+    if (th == after_tm.threads) continue;
+    MTile t = after_tm;
+    t.threads = th;
+    consider(t);
+  }
+  if (planned_lpr > 0) {
+    const MTile after_th = best;
+    for (int l : {planned_lpr / 2, planned_lpr * 2}) {
+      if (l < 1 || l > 32) continue;
+      MTile t = after_th;
+      t.lpr = l;
+      consider(t);
     }
   }
   return best;
@@ -686,30 +714,28 @@ void autotune(tam_amg_s* H, cudaStream_t s) {
   MultiState& MS = *H->multi;
   const int mp = MS.mp;
   auto t0 = std::chrono::steady_clock::now();
-  MS.tmK = pick_tm(mp, [&](int tm) {
-    kspmm(H->K->S, MS.p.p, mp, tm, EpiStoreKM{MS.q.p, H->K->n_nodes, mp}, s, H->levels[0].Aop.df);
+  MS.tK = pick_tile(mp, 0, [&](const MTile& t) {
+    kspmm(H->K->S, MS.p.p, mp, t, EpiStoreKM{MS.q.p, H->K->n_nodes, mp}, s, H->levels[0].Aop.df);
   }, s);
   for (size_t l = 0; l + 1 < H->levels.size(); ++l) {
     Level& L = H->levels[l];
     MultiLevel& ML = MS.lv[l];
     MultiLevel& MC = MS.lv[l + 1];
-    ML.tmA = pick_tm(mp, [&](int tm) {
-      if (L.bs == 3) level_mspmm<3>(L, ML.xa.p, mp, tm, EpiPutMF<3, false>{ML.t.p, L.n_rows, mp, nullptr}, s);
-      else level_mspmm<6>(L, ML.xa.p, mp, tm, EpiPutMF<6, false>{ML.t.p, L.n_rows, mp, nullptr}, s);
+    ML.tA = pick_tile(mp, L.A32.op.lpr, [&](const MTile& t) {
+      if (L.bs == 3) level_mspmm<3>(L, ML.xa.p, mp, t, EpiPutMF<3, false>{ML.t.p, L.n_rows, mp, nullptr}, s);
+      else level_mspmm<6>(L, ML.xa.p, mp, t, EpiPutMF<6, false>{ML.t.p, L.n_rows, mp, nullptr}, s);
     }, s);
-    ML.tmR = pick_tm(mp, [&](int tm) {
-      MultiLevel tmp;
-      (void)tmp;
+    ML.tR = pick_tile(mp, L.R32.op.lpr, [&](const MTile& t) {
       const int nr = L.R.n_rows;
-      if (L.kdim == 6 && L.bs == 3) mspmm<6, 3, float>(L.R32, ML.t.p, mp, tm, EpiPutMF<6, false>{MC.b.p, nr, mp, nullptr}, s);
-      else if (L.kdim == 6) mspmm<6, 6, float>(L.R32, ML.t.p, mp, tm, EpiPutMF<6, false>{MC.b.p, nr, mp, nullptr}, s);
-      else mspmm<3, 3, float>(L.R32, ML.t.p, mp, tm, EpiPutMF<3, false>{MC.b.p, nr, mp, nullptr}, s);
+      if (L.kdim == 6 && L.bs == 3) mspmm<6, 3, float>(L.R32, ML.t.p, mp, t, EpiPutMF<6, false>{MC.b.p, nr, mp, nullptr}, s);
+      else if (L.kdim == 6) mspmm<6, 6, float>(L.R32, ML.t.p, mp, t, EpiPutMF<6, false>{MC.b.p, nr, mp, nullptr}, s);
+      else mspmm<3, 3, float>(L.R32, ML.t.p, mp, t, EpiPutMF<3, false>{MC.b.p, nr, mp, nullptr}, s);
     }, s);
-    ML.tmP = pick_tm(mp, [&](int tm) {
+    ML.tP = pick_tile(mp, L.P32.op.lpr, [&](const MTile& t) {
       const int nr = L.P.n_rows;
-      if (L.kdim == 6 && L.bs == 3) mspmm<3, 6, float>(L.P32, MC.y.p, mp, tm, EpiPutMF<3, false>{ML.xb.p, nr, mp, nullptr}, s);
-      else if (L.kdim == 6) mspmm<6, 6, float>(L.P32, MC.y.p, mp, tm, EpiPutMF<6, false>{ML.xb.p, nr, mp, nullptr}, s);
-      else mspmm<3, 3, float>(L.P32, MC.y.p, mp, tm, EpiPutMF<3, false>{ML.xb.p, nr, mp, nullptr}, s);
+      if (L.kdim == 6 && L.bs == 3) mspmm<3, 6, float>(L.P32, MC.y.p, mp, t, EpiPutMF<3, false>{ML.xb.p, nr, mp, nullptr}, s);
+      else if (L.kdim == 6) mspmm<6, 6, float>(L.P32, MC.y.p, mp, t, EpiPutMF<6, false>{ML.xb.p, nr, mp, nullptr}, s);
+      else mspmm<3, 3, float>(L.P32, MC.y.p, mp, t, EpiPutMF<3, false>{ML.xb.p, nr, mp, nullptr}, s);
     }, s);
   }
   MS.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -729,7 +755,8 @@ void ensure_multi(tam_amg_s* H, int mp, cudaStream_t s) {
   MS.sc = DBuf<double>(S_COUNT * (size_t)mp, s);
   MS.flags = DBuf<int>(4, s);
   MS.flags.zero();
-  const unsigned g = std::max<unsigned>(sell_grid(H->K->S), (unsigned)sm_count() * 8u);
+  const unsigned g = std::max<unsigned>(grid_for((long long)H->K->S.n_slices * 32, MT_MIN_THREADS),
+                                        (unsigned)sm_count() * 8u);
   MS.partials = DBuf<double>((size_t)g * std::max(TMAX, MPMAX) * (MPMAX / 1 + 1), s);
   MS.tickets = DBuf<unsigned int>(MPMAX + 1, s);
   MS.tickets.zero();
@@ -751,7 +778,7 @@ void enqueue_multi_iteration(tam_amg_s* H, cudaStream_t s) {
   const long long n3 = (long long)H->K->n_nodes * 3;
   int* flags = MS.flags.p;
   GridReduce gk{MS.partials.p, MS.tickets.p};
-  kspmm(H->K->S, MS.p.p, mp, MS.tmK, EpiPqM{MS.p.p, MS.q.p, H->K->n_nodes, mp, gk, MS.sc.p, flags}, s, H->levels[0].Aop.df);
+  kspmm(H->K->S, MS.p.p, mp, MS.tK, EpiPqM{MS.p.p, MS.q.p, H->K->n_nodes, mp, gk, MS.sc.p, flags}, s, H->levels[0].Aop.df);
   GridReduce ge{MS.partials.p, MS.tickets.p + MPMAX};
   mupdate_kernel<<<vgrid(n3), TPB, 0, s>>>(MS.x.p, MS.r.p, MS.p.p, MS.q.p, n3, mp, ge, MS.sc.p, flags);
   TAM_LAUNCH_CHECK();
@@ -779,7 +806,7 @@ void start_multi(tam_amg_s* H, int m, const double* B, const double* X, double r
   mscale_in_kernel<<<vgrid(n3 * mp), TPB, 0, s>>>(MS.b.p, MS.x.p, n3, mp, MS.sc.p);
   TAM_LAUNCH_CHECK();
   GridReduce gk{MS.partials.p, MS.tickets.p};
-  kspmm(H->K->S, MS.x.p, mp, MS.tmK,
+  kspmm(H->K->S, MS.x.p, mp, MS.tK,
         EpiResInitM{MS.b.p, MS.r.p, H->K->n_nodes, mp, gk, MS.sc.p, nullptr, MS.flags.p}, s, H->levels[0].Aop.df);
   mcheck_kernel<<<1, 32, 0, s>>>(MS.sc.p, mp, MS.flags.p);
   TAM_LAUNCH_CHECK();
@@ -795,7 +822,7 @@ int finish_multi(tam_amg_s* H, int m, const double* B, double* X, int* iters, do
   DBuf<double> rn(mp, s);
   GridReduce gk{MS.partials.p, MS.tickets.p};
   // the reported true residual is always a plain FP64 product
-  kspmm(H->K->S, MS.x.p, mp, MS.tmK, EpiResInitM{MS.b.p, nullptr, H->K->n_nodes, mp, gk, MS.sc.p, rn.p, MS.flags.p},
+  kspmm(H->K->S, MS.x.p, mp, MS.tK, EpiResInitM{MS.b.p, nullptr, H->K->n_nodes, mp, gk, MS.sc.p, rn.p, MS.flags.p},
         s, false);
   deinterleave_kernel<<<vgrid(n3 * m), TPB, 0, s>>>(MS.x.p, X, m, mp, n3, MS.sc.p);
   TAM_LAUNCH_CHECK();
@@ -841,70 +868,48 @@ int pcg_solve_batch(int n_sys, tam_amg_s* const* H, const int* m, const double* 
               "batch solve: the FP32 V-cycle needs K's largest entry within 2^-" + std::to_string(kDfExpLimit) +
                   "..2^" + std::to_string(kDfExpLimit) + " (it is 2^" + std::to_string(H[i]->K->vmax_exp) + ")");
   for (int i = 0; i < n_sys; ++i) start_multi(H[i], m[i], B[i], X[i], rtol, atol, max_iter, s);
-  // one graph: every system's iteration on its own branch, joined, then a
-  // flag telling whether all systems have stopped
+  // one graph: a device-side WHILE loop whose body advances every system by
+  // one iteration (each system on its own branch, joined), then a flag telling
+  // whether all systems have stopped -- one launch for the whole batch solve
   DBuf<int*> fl(n_sys, s);
-  DBuf<int> all(1, s);
+  DBuf<int> all(2, s);  // [0] all stopped, [1] loop count
+  all.zero();
   std::vector<int*> hf(n_sys);
   for (int i = 0; i < n_sys; ++i) hf[i] = H[i]->multi->flags.p;
   TAM_CUDA(cudaMemcpyAsync(fl.p, hf.data(), sizeof(int*) * n_sys, cudaMemcpyHostToDevice, s));
-  TAM_CUDA(cudaStreamSynchronize(s));
-  cudaStream_t cs;
-  TAM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  std::vector<cudaStream_t> br(n_sys);
-  std::vector<cudaEvent_t> ev(n_sys + 1);
-  for (int i = 0; i < n_sys; ++i) TAM_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
-  for (auto& e : ev) TAM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  cudaGraph_t g = nullptr;
+  std::vector<cudaStream_t> br(n_sys, nullptr);
+  std::vector<cudaEvent_t> ev(n_sys + 1, nullptr);
   cudaGraphExec_t exec = nullptr;
-  long long kernels = 0;
   auto cleanup = [&] {
     if (exec) cudaGraphExecDestroy(exec);
-    if (g) cudaGraphDestroy(g);
-    for (auto& e : ev) cudaEventDestroy(e);
-    for (auto& b : br) cudaStreamDestroy(b);
-    cudaStreamDestroy(cs);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto& b : br)
+      if (b) cudaStreamDestroy(b);
   };
+  long long kernels = 0;
   try {
-    TAM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    captured_and_reset();
-    g_capturing = true;
-    TAM_CUDA(cudaEventRecord(ev[n_sys], cs));
-    for (int i = 0; i < n_sys; ++i) {
-      TAM_CUDA(cudaStreamWaitEvent(br[i], ev[n_sys], 0));
-      enqueue_multi_iteration(H[i], br[i]);
-      TAM_CUDA(cudaEventRecord(ev[i], br[i]));
-      TAM_CUDA(cudaStreamWaitEvent(cs, ev[i], 0));
-    }
-    all_stop_kernel<<<1, 32, 0, cs>>>(fl.p, n_sys, all.p);
-    TAM_LAUNCH_CHECK();
-    g_capturing = false;
-    kernels = captured_and_reset();
-    TAM_CUDA(cudaStreamEndCapture(cs, &g));
-    TAM_CUDA(cudaGraphInstantiate(&exec, g, 0));
-    HostScalars& hs = host_scalars();
-    int launched = 0;
-    while (launched < max_iter) {
-      const int todo = std::min(8, max_iter - launched);
-      for (int k = 0; k < todo; ++k) {
-        TAM_CUDA(cudaGraphLaunch(exec, s));
-        count_graph_launch(kernels);
-      }
-      launched += todo;
-      TAM_CUDA(cudaMemcpyAsync(hs.ll, all.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-      TAM_CUDA(cudaStreamSynchronize(s));
-      if (*reinterpret_cast<int*>(hs.ll)) break;
-    }
+    for (int i = 0; i < n_sys; ++i) TAM_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
+    for (auto& e : ev) TAM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    exec = build_loop_graph(
+        [&](cudaStream_t cs) {
+          TAM_CUDA(cudaEventRecord(ev[n_sys], cs));
+          for (int i = 0; i < n_sys; ++i) {
+            TAM_CUDA(cudaStreamWaitEvent(br[i], ev[n_sys], 0));
+            enqueue_multi_iteration(H[i], br[i]);
+            TAM_CUDA(cudaEventRecord(ev[i], br[i]));
+            TAM_CUDA(cudaStreamWaitEvent(cs, ev[i], 0));
+          }
+          all_stop_kernel<<<1, 32, 0, cs>>>(fl.p, n_sys, all.p);
+          TAM_LAUNCH_CHECK();
+        },
+        all.p, all.p + 1, H[0]->multi->flags.p + 2, 2, &kernels);
+    TAM_CUDA(cudaGraphLaunch(exec, s));
+    int loops = 0;
+    TAM_CUDA(cudaMemcpyAsync(&loops, all.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TAM_CUDA(cudaStreamSynchronize(s));
+    count_graph_launch(kernels * loops);
   } catch (...) {
-    g_capturing = false;
-    captured_and_reset();
-    // a failure during capture leaves cs capturing: end it and drop the partial graph
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(cs, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) {
-      cudaGraph_t partial = nullptr;
-      cudaStreamEndCapture(cs, &partial);
-      if (partial) cudaGraphDestroy(partial);
-    }
     cudaGetLastError();
     cleanup();
     throw;
@@ -923,12 +928,17 @@ double multi_tune_ms(tam_amg_s* H) { return H->multi ? H->multi->tune_ms : 0.0; 
 void multi_tiles(tam_amg_s* H, int* out, int cap) {
   int k = 0;
   if (!H->multi) return;
-  if (k < cap) out[k++] = H->multi->tmK;
-  for (auto& ML : H->multi->lv) {
-    if (k + 3 > cap) break;
-    out[k++] = ML.tmA;
-    out[k++] = ML.tmP;
-    out[k++] = ML.tmR;
+  auto put = [&](const MTile& t) {
+    if (k + 3 > cap) return;
+    out[k++] = t.tm;
+    out[k++] = t.threads;
+    out[k++] = t.lpr;
+  };
+  put(H->multi->tK);
+  for (size_t l = 0; l + 1 < H->multi->lv.size(); ++l) {
+    put(H->multi->lv[l].tA);
+    put(H->multi->lv[l].tP);
+    put(H->multi->lv[l].tR);
   }
 }
 

@@ -16,6 +16,7 @@
 // graph of one iteration can be replayed without host round trips.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <type_traits>
 #include <vector>
 
@@ -115,6 +116,7 @@ __global__ void pcg_start_kernel(const double* __restrict__ b, long long N, Grid
     sc->status = TAM_OK;
     sc->rho = sc->alpha = sc->beta = 0.0;
     sc->rr = 0.0;
+    sc->loops = 0;
   }
 }
 
@@ -259,6 +261,14 @@ struct EpiResNorm {
 
 unsigned vec_grid(long long N) { return stride_grid(N, TPB, 8); }
 
+// The last node of a loop body: continue while *stop == 0 and the failsafe
+// count stays below *limit + add.
+__global__ void loop_control_kernel(cudaGraphConditionalHandle h, const int* __restrict__ stop, int* __restrict__ count,
+                                    const int* __restrict__ limit, int add) {
+  const int c = ++*count;
+  cudaGraphSetConditional(h, (*stop == 0 && c < *limit + add) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // Dispatch on block shapes (3x3, 6x6 for A; 3x6, 6x3, 6x6, 3x3 for P and R)
 // ---------------------------------------------------------------------------
@@ -389,6 +399,55 @@ void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
 
 }  // namespace
 
+cudaGraphExec_t build_loop_graph(const std::function<void(cudaStream_t)>& enqueue, const int* stop, int* count,
+                                 const int* limit, int limit_add, long long* body_kernels) {
+  cudaGraph_t g = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool capturing = false;
+  try {
+    TAM_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    TAM_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    TAM_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    TAM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    TAM_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    capturing = true;
+    captured_and_reset();
+    g_capturing = true;
+    enqueue(cs);
+    loop_control_kernel<<<1, 1, 0, cs>>>(h, stop, count, limit, limit_add);
+    TAM_LAUNCH_CHECK();
+    g_capturing = false;
+    *body_kernels = captured_and_reset();
+    cudaGraph_t out = nullptr;
+    capturing = false;
+    TAM_CUDA(cudaStreamEndCapture(cs, &out));
+    TAM_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  } catch (...) {
+    g_capturing = false;
+    captured_and_reset();
+    if (capturing) {
+      cudaGraph_t partial = nullptr;
+      cudaStreamEndCapture(cs, &partial);
+    }
+    cudaGetLastError();
+    if (cs) cudaStreamDestroy(cs);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cudaStreamDestroy(cs);
+  cudaGraphDestroy(g);
+  return exec;
+}
+
 void spmv_K(tam_matrix_s* K, const double* x, double* y, cudaStream_t s) {
   by_block(K->A.br, [&](auto B) {
     constexpr int BR = decltype(B)::value;
@@ -436,52 +495,19 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   precondition(H, H->r.p, H->z.p, &sc->stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, sc, 1);
   TAM_LAUNCH_CHECK();
-  // one iteration as a CUDA graph, rebuilt if the target vector changed
+  // the iterations as one graph: a device-side WHILE loop over one iteration
+  // (rebuilt when the target vector or the stream changes), one launch per solve
   if (!H->iter_exec || H->graph_x != x || H->graph_stream != s) {
     if (H->iter_exec) {
       cudaGraphExecDestroy(H->iter_exec);
       H->iter_exec = nullptr;
     }
-    cudaStream_t cs;
-    TAM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    TAM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    captured_and_reset();
-    g_capturing = true;
-    try {
-      enqueue_iteration(H, x, cs);
-    } catch (...) {
-      g_capturing = false;
-      captured_and_reset();
-      cudaStreamEndCapture(cs, &g);
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      cudaStreamDestroy(cs);
-      throw;
-    }
-    g_capturing = false;
-    H->graph_kernels = captured_and_reset();
-    TAM_CUDA(cudaStreamEndCapture(cs, &g));
-    TAM_CUDA(cudaGraphInstantiate(&H->iter_exec, g, 0));
-    cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
+    H->iter_exec = build_loop_graph([&](cudaStream_t cs) { enqueue_iteration(H, x, cs); }, &sc->stop, &sc->loops,
+                                    &sc->max_iter, 2, &H->graph_kernels);
     H->graph_x = x;
     H->graph_stream = s;
   }
-  HostScalars& hs = host_scalars();
-  const int chunk = 8;
-  int launched = 0;
-  while (launched < max_iter) {
-    int todo = std::min(chunk, max_iter - launched);
-    for (int i = 0; i < todo; ++i) {
-      TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
-      count_graph_launch(H->graph_kernels);
-    }
-    launched += todo;
-    TAM_CUDA(cudaMemcpyAsync(hs.ll, &sc->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TAM_CUDA(cudaStreamSynchronize(s));
-    if (*reinterpret_cast<int*>(hs.ll)) break;
-  }
+  TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
   // final true residual, always a plain FP64 product; then x back to the caller's scale
   DBuf<double> rn(1, s);
   by_block(H->K->A.br, [&](auto B) {
@@ -493,6 +519,7 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   PcgScalars host;
   TAM_CUDA(cudaMemcpyAsync(&host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   double rr = read_back_double(rn.p, s);  // synchronises the stream
+  count_graph_launch(H->graph_kernels * host.loops);
   if (iters) *iters = host.iter;
   double nb = std::sqrt(host.bb);
   if (rel) *rel = nb > 0 ? std::sqrt(rr) / nb : std::sqrt(rr);

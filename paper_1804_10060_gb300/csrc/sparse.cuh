@@ -94,21 +94,19 @@ __device__ __forceinline__ void df_fma(float2& a, float2 x, float2 y) {
   a.y = __fadd_rn(a.y, __fadd_rn(err, e));
 }
 
-// a += b for two unevaluated sums, accurately: TwoSum of the high parts and
-// of the low parts, renormalised twice (the result keeps about 2^-48 of |a + b|)
-__device__ __forceinline__ void df_add_acc(float2& a, float2 b) {
-  float sh = __fadd_rn(a.x, b.x);
-  float bp = __fadd_rn(sh, -a.x);
-  float sl = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(sh, -bp)), __fadd_rn(b.x, -bp));
-  const float th = __fadd_rn(a.y, b.y);
-  bp = __fadd_rn(th, -a.y);
-  const float tl = __fadd_rn(__fadd_rn(a.y, -__fadd_rn(th, -bp)), __fadd_rn(b.y, -bp));
-  sl = __fadd_rn(sl, th);
-  float h = __fadd_rn(sh, sl);
-  sl = __fadd_rn(sl, -__fadd_rn(h, -sh));
-  sl = __fadd_rn(sl, tl);
-  a.x = __fadd_rn(h, sl);
-  a.y = __fadd_rn(sl, -__fadd_rn(a.x, -h));
+// df_fma with the lo * lo product kept as well (the accurate SpMV: the dropped
+// term is otherwise up to 2^-48 of each product)
+__device__ __forceinline__ void df_fma4(float2& a, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = fmaf(x.x, y.x, -p);
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  e = fmaf(x.y, y.y, e);
+  const float s = __fadd_rn(a.x, p);
+  const float bp = __fadd_rn(s, -a.x);
+  const float err = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
+  a.x = s;
+  a.y = __fadd_rn(a.y, __fadd_rn(err, e));
 }
 
 // a += b for two unevaluated sums hi + lo: TwoSum of the high parts, the
@@ -237,9 +235,9 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
     const int* __restrict__ cp = A.cols + (size_t)k0 * 32 + lane;
     if constexpr (DF) {
       const float2* __restrict__ vp = A.vals_df + (size_t)k0 * 32 * BR * BC + lane;
-      float2 ad[BR], od[BR];
+      float2 ad[BR];
 #pragma unroll
-      for (int r = 0; r < BR; ++r) ad[r] = od[r] = make_float2(0.f, 0.f);
+      for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
 #pragma unroll 2
       for (int k = k0; k < k1; ++k) {
         float2 vv[BR * BC];  // the slot's values first, then the gather
@@ -252,17 +250,20 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
-          for (int j = 0; j < BC; ++j) df_fma(ad[r], vv[r * BC + j], xv[j]);
+          for (int j = 0; j < BC; ++j) {
+            if constexpr (ACC) df_fma4(ad[r], vv[r * BC + j], xv[j]);
+            else df_fma(ad[r], vv[r * BC + j], xv[j]);
+          }
         if constexpr (ACC) {
-          // ACC: the running double-float sum restarts every 4 slots and is
-          // added into an outer one accurately, so that the low part never
-          // carries more than 4 slots' rounding: about 2^-47 of
-          // sum_j |A_ij x_j| per row whatever the row's length (the sloppy
-          // running sum drifts to ~2^-45 on long P2 rows)
-          if (((k - k0) & 3) == 3) {  // uniform over the warp (one slice)
+          // ACC: the double-float sum restarts every 2 slots and is added
+          // into an FP64 sum, so that the low part never carries more than 2
+          // slots' rounding: a few 2^-48 of sum_j |A_ij x_j| per row whatever
+          // the row's length (the running double-float sum drifts to ~2^-45 on
+          // long P2 rows), for 1.5 FP64 adds per row and slot pair
+          if ((k - k0) & 1) {  // uniform over the warp (one slice)
 #pragma unroll
             for (int r = 0; r < BR; ++r) {
-              df_add_acc(od[r], ad[r]);
+              acc[r] += df_to_double(ad[r]);
               ad[r] = make_float2(0.f, 0.f);
             }
           }
@@ -271,10 +272,7 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
         vp += 32 * BR * BC;
       }
 #pragma unroll
-      for (int r = 0; r < BR; ++r) {
-        if constexpr (ACC) df_add_acc(ad[r], od[r]);
-        acc[r] = df_to_double(ad[r]);
-      }
+      for (int r = 0; r < BR; ++r) acc[r] += df_to_double(ad[r]);
     } else {
       const double* __restrict__ vp = A.vals + (size_t)k0 * 32 * BR * BC + lane;
 #pragma unroll 2

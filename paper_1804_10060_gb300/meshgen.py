@@ -527,3 +527,74 @@ def disc_thermal_problem(pb: Problem, t: float = 0.0, seed: int = 11) -> Thermal
     props = np.array([[1.0, 1.0, 5e-4, 0.05, 5e-5]])
     return ThermalProblem(pb.coords, pb.cells, np.zeros(pb.n_cells, np.int32), props, faces[sel],
                           beta, T_bc)
+
+
+# ----------------------------------------------------------------------------
+# Unstructured meshes: Delaunay tetrahedralisations of seeded point sets
+# ----------------------------------------------------------------------------
+
+def delaunay_box(n: int = 12, lx: float = 2.0, ly: float = 1.0, lz: float = 1.0, seed: int = 1,
+                 jitter: float = 0.35, hub: int = 0):
+    """Unstructured tets of the box [0,lx]x[0,ly]x[0,lz] (Delaunay of seeded points).
+
+    Points: a lattice of spacing h = ly / n, every point moved by a seeded
+    uniform offset of up to jitter*h along the box directions it is free in
+    (points on a face stay on it, edge and corner points stay put), so the
+    valences and cell shapes are irregular.  hub > 0 adds, around the box
+    centre, a point ringed by `hub` points on a sphere of radius h/2 (seeded,
+    quasi-uniform): the centre touches about 2 hub cells, a node of very high
+    valence.  Cells of (near) zero volume from co-planar hull points are
+    dropped; every cell is oriented positively.  Returns (coords, cells,
+    quality) with quality = dict(min_volume, min_dihedral_deg, max_valence).
+    """
+    from scipy.spatial import Delaunay
+    h = ly / n
+    nx, ny, nz = max(1, round(lx / h)), n, max(1, round(lz / h))
+    g = np.stack(np.meshgrid(np.linspace(0, lx, nx + 1), np.linspace(0, ly, ny + 1), np.linspace(0, lz, nz + 1),
+                             indexing="ij"), axis=-1).reshape(-1, 3)
+    rng = np.random.default_rng(seed)
+    L = np.array([lx, ly, lz])
+    free = (g > 1e-12) & (g < L - 1e-12)
+    g = g + free * rng.uniform(-jitter * h, jitter * h, g.shape)
+    pts = [g]
+    if hub:
+        c = L / 2.0
+        far = np.linalg.norm(g - c, axis=1) > 0.75 * h
+        pts = [g[far], c[None]]
+        k = np.arange(hub) + 0.5                                 # Fibonacci sphere
+        phi = np.arccos(1.0 - 2.0 * k / hub)
+        th = np.pi * (1.0 + 5 ** 0.5) * k + rng.uniform(0, 2 * np.pi)
+        pts.append(c + 0.5 * h * np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], axis=1))
+    coords = np.concatenate(pts)
+    cells = Delaunay(coords, qhull_options="Qbb Qc Qz Q12").simplices.astype(np.int64)
+    x = coords[cells]
+    vol = np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), x[:, 3] - x[:, 0]) / 6.0
+    keep = np.abs(vol) > 1e-10 * h ** 3
+    cells, vol = cells[keep], vol[keep]
+    neg = vol < 0
+    cells[neg] = cells[neg][:, [0, 1, 3, 2]]
+    used = np.unique(cells)
+    remap = -np.ones(coords.shape[0], np.int64)
+    remap[used] = np.arange(used.size)
+    coords, cells = coords[used], remap[cells]
+    order = spatial_order(coords, h)
+    coords, cells, _ = renumber_nodes(coords, cells.astype(np.int32), order)
+    mv, md = mesh_quality(coords, cells)
+    val = np.bincount(cells.ravel(), minlength=coords.shape[0])
+    q = dict(min_volume=mv, min_dihedral_deg=md, max_valence=int(val.max()))
+    return coords, cells.astype(np.int32), q
+
+
+def delaunay_box_problem(n: int = 12, degree: int = 1, seed: int = 1, hub: int = 0) -> Problem:
+    """The two-material box load case (slab_box_problem's materials, temperature
+    recipe and clamp at x = 0) on an unstructured Delaunay mesh of [0,2]x[0,1]^2."""
+    coords, cells, q = delaunay_box(n, seed=seed, hub=hub)
+    if degree == 2:
+        coords, cells, _ = p1_to_p2(coords, cells)
+    xc = cell_centroids(coords, cells)
+    mat = (np.floor(xc[:, 0] / 0.5).astype(np.int64) % 2).astype(np.int32)
+    T = fourier_temperature(coords, 2024, scale=(2.0, 1.0, 1.0))
+    mask = (coords[:, 0] <= 1e-12).astype(np.uint8)
+    return Problem(name=f"delaunay_p{degree}", coords=coords, cells=cells, cell_material=mat,
+                   mat_props=np.array([[1.0, 0.3, 1e-3], [10.0, 0.3, 1e-3]]), T=T, T_ref=0.0, body_force=None,
+                   dirichlet_mask=mask, u_dirichlet=None, meta=dict(q, n=n, seed=seed, hub=hub))

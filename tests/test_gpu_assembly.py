@@ -62,11 +62,12 @@ def test_assembly_matches_oracle(degree, n):
             assert not np.any(pb.dirichlet_mask[row[row != i]])
 
 
-# Per-row bound of the double-float SpMV: |y_i - (K x)_i| <= 1e-14 sum_j |K_ij x_j|.
+# Per-row bound of the outer double-float SpMV: |y_i - (K x)_i| <= 1e-14 sum_j |K_ij x_j|.
 # Each product's operands are split to within 2^-49 relative (round to
-# nearest), the dropped lo*lo term is below 2^-48 of the product, and the FP32
-# rounding of the cross terms and of the running low part adds a few 2^-48;
-# these errors are unbiased, so a row's total, measured against the sum of the
+# nearest), every partial product including lo*lo is kept, and the FP32
+# rounding of the cross terms and of the low part (restarted every two slots,
+# its sum added in FP64) adds a few 2^-48 of the magnitudes involved; the
+# errors are unbiased, so a row's total, measured against the sum of the
 # magnitudes of its terms (which absorbs cancellation), stays below 1e-14
 # (about 2.8 * 2^-48).
 SPMV_ROW_TOL = 1e-14
@@ -80,9 +81,10 @@ def test_spmv_matches_exact_products(degree):
     K, _ = tam.fem_assemble_elasticity(**d)
     rp, ci, v = tam.tam_matrix_export_bsr(K)
     Kg = bsr_to_csr(rp, ci, v, pb.n_nodes)
-    x = torch.randn(pb.n_nodes, 3, dtype=torch.float64, device="cuda")
+    xs = np.random.default_rng(21 + degree).standard_normal((pb.n_nodes, 3))
+    x = torch.from_numpy(xs).cuda()
     y = tam.tam_matrix_spmv(K, x).cpu().numpy().ravel()
-    y_ex, s = exact_spmv(Kg, x.cpu().numpy().ravel())
+    y_ex, s = exact_spmv(Kg, xs.ravel())
     err = np.abs(y - y_ex)
     assert np.all(err <= SPMV_ROW_TOL * s), (err / np.maximum(s, 1e-300)).max()
 

@@ -76,7 +76,9 @@ def test_batch_of_load_cases_matches_single_solves():
         u = _oracle_solution(pb, T, body)
         assert np.linalg.norm(X[k].cpu().numpy() - u) <= 1e-6 * np.linalg.norm(u)
     tiles, tune_ms = tam.amg_batch_tiles(H)
-    assert tiles and all(t in (1, 2, 4, 8) for t in tiles) and tune_ms > 0
+    assert tiles and len(tiles) % 3 == 0 and tune_ms > 0
+    for tm, threads, lpr in zip(tiles[0::3], tiles[1::3], tiles[2::3]):
+        assert tm in (1, 2, 4, 8) and threads in (64, 128, 256) and lpr in (0, 1, 2, 4, 8, 16, 32)
 
 
 def test_batch_of_uneven_meshes_in_one_graph():
