@@ -1091,6 +1091,7 @@ void amg_refresh_finest(tam_amg_s* H, cudaStream_t s) {
     cudaGraphExecDestroy(H->iter_exec);
     H->iter_exec = nullptr;
   }
+  H->multi.reset();  // its FP32 copies and batch graph belong to the old operator
 }
 
 }  // namespace tam

@@ -90,13 +90,21 @@ struct MultiState {
   DBuf<unsigned int> tickets;     // one per RHS chunk
   std::vector<MultiLevel> lv;
   MTile tK;
-  cudaGraphExec_t exec = nullptr;
-  double* graph_x = nullptr;
-  cudaStream_t graph_stream = nullptr;
   double tune_ms = 0.0;
-  ~MultiState() {
-    if (exec) cudaGraphExecDestroy(exec);
-  }
+  unsigned long long serial = 0;  // unique per workspace: batch graphs are keyed on it
+  // the last batch solve's loop graph, kept by the batch's first system: valid
+  // while the batch names the same workspaces (serials) in the same order
+  struct BatchGraph {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec = nullptr;
+    DBuf<int*> fl;   // the systems' flag arrays
+    DBuf<int> all;   // [0] all stopped, [1] loop count
+    long long kernels = 0;
+    ~BatchGraph() {
+      if (exec) cudaGraphExecDestroy(exec);
+    }
+  };
+  std::unique_ptr<BatchGraph> batch;
 };
 
 }  // namespace tam
@@ -109,16 +117,14 @@ struct tam_amg_s {
   tam::DBuf<double> coarse_inv;          // [n_coarse * n_coarse]
   // PCG workspace
   tam::DBuf<double> r, z, p, q;
-  tam::DBuf<double> bs;                  // b scaled by the solve's power of two
+  tam::DBuf<double> bs, xs;              // b and x scaled by the solve's power of two
   tam::DBuf<tam::PcgScalars> sc;
   tam::DBuf<double> partials;            // grid-reduction partials
   tam::DBuf<unsigned int> ticket;
   int max_grid = 0;
-  // captured V-cycle + iteration graph (rebuilt when buffers change)
+  // captured V-cycle + iteration graph (on the hierarchy's own vectors; rebuilt
+  // when the finest level is refreshed)
   cudaGraphExec_t iter_exec = nullptr;
-  const double* graph_b = nullptr;
-  double* graph_x = nullptr;
-  cudaStream_t graph_stream = nullptr;
   long long graph_kernels = 0;           // kernel nodes in iter_exec
   double setup_ms[8] = {};               // setup phase times, see amg_setup_stats
   // Chebyshev coefficients of the last smooth_fine call (degree, interval)

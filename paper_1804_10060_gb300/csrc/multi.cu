@@ -12,6 +12,7 @@
 // per thread) is chosen per operator by timing the candidates once per
 // hierarchy and RHS count (the autotuner below).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 
@@ -744,9 +745,11 @@ void autotune(tam_amg_s* H, cudaStream_t s) {
 void ensure_multi(tam_amg_s* H, int mp, cudaStream_t s) {
   if (!H->levels[0].dinv32.p) build_low_precision(H, s);
   if (H->multi && H->multi->mp == mp) return;
+  static std::atomic<unsigned long long> serials{0};
   H->multi.reset(new MultiState());
   MultiState& MS = *H->multi;
   MS.mp = mp;
+  MS.serial = ++serials;
   const size_t n3 = (size_t)H->K->n_nodes * 3;
   for (auto* v : {&MS.b, &MS.x, &MS.r, &MS.z, &MS.p, &MS.q}) {
     *v = DBuf<double>(n3 * mp, s);
@@ -870,51 +873,60 @@ int pcg_solve_batch(int n_sys, tam_amg_s* const* H, const int* m, const double* 
   for (int i = 0; i < n_sys; ++i) start_multi(H[i], m[i], B[i], X[i], rtol, atol, max_iter, s);
   // one graph: a device-side WHILE loop whose body advances every system by
   // one iteration (each system on its own branch, joined), then a flag telling
-  // whether all systems have stopped -- one launch for the whole batch solve
-  DBuf<int*> fl(n_sys, s);
-  DBuf<int> all(2, s);  // [0] all stopped, [1] loop count
-  all.zero();
-  std::vector<int*> hf(n_sys);
-  for (int i = 0; i < n_sys; ++i) hf[i] = H[i]->multi->flags.p;
-  TAM_CUDA(cudaMemcpyAsync(fl.p, hf.data(), sizeof(int*) * n_sys, cudaMemcpyHostToDevice, s));
-  std::vector<cudaStream_t> br(n_sys, nullptr);
-  std::vector<cudaEvent_t> ev(n_sys + 1, nullptr);
-  cudaGraphExec_t exec = nullptr;
-  auto cleanup = [&] {
-    if (exec) cudaGraphExecDestroy(exec);
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-    for (auto& b : br)
-      if (b) cudaStreamDestroy(b);
-  };
-  long long kernels = 0;
-  try {
-    for (int i = 0; i < n_sys; ++i) TAM_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
-    for (auto& e : ev) TAM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    exec = build_loop_graph(
-        [&](cudaStream_t cs) {
-          TAM_CUDA(cudaEventRecord(ev[n_sys], cs));
-          for (int i = 0; i < n_sys; ++i) {
-            TAM_CUDA(cudaStreamWaitEvent(br[i], ev[n_sys], 0));
-            enqueue_multi_iteration(H[i], br[i]);
-            TAM_CUDA(cudaEventRecord(ev[i], br[i]));
-            TAM_CUDA(cudaStreamWaitEvent(cs, ev[i], 0));
-          }
-          all_stop_kernel<<<1, 32, 0, cs>>>(fl.p, n_sys, all.p);
-          TAM_LAUNCH_CHECK();
-        },
-        all.p, all.p + 1, H[0]->multi->flags.p + 2, 2, &kernels);
-    TAM_CUDA(cudaGraphLaunch(exec, s));
-    int loops = 0;
-    TAM_CUDA(cudaMemcpyAsync(&loops, all.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TAM_CUDA(cudaStreamSynchronize(s));
-    count_graph_launch(kernels * loops);
-  } catch (...) {
-    cudaGetLastError();
+  // whether all systems have stopped -- one launch for the whole batch solve;
+  // built once per set of systems and kept by the first one
+  std::vector<unsigned long long> key(n_sys);
+  for (int i = 0; i < n_sys; ++i) key[i] = H[i]->multi->serial;
+  auto& G = H[0]->multi->batch;
+  if (!G || G->key != key) {
+    G.reset();
+    std::unique_ptr<MultiState::BatchGraph> g(new MultiState::BatchGraph());
+    g->key = key;
+    g->fl = DBuf<int*>(n_sys, s);
+    g->all = DBuf<int>(2, s);
+    std::vector<int*> hf(n_sys);
+    for (int i = 0; i < n_sys; ++i) hf[i] = H[i]->multi->flags.p;
+    TAM_CUDA(cudaMemcpyAsync(g->fl.p, hf.data(), sizeof(int*) * n_sys, cudaMemcpyHostToDevice, s));
+    std::vector<cudaStream_t> br(n_sys, nullptr);
+    std::vector<cudaEvent_t> ev(n_sys + 1, nullptr);
+    auto cleanup = [&] {
+      for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+      for (auto& b : br)
+        if (b) cudaStreamDestroy(b);
+    };
+    try {
+      for (int i = 0; i < n_sys; ++i) TAM_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
+      for (auto& e : ev) TAM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      int* const* fl = g->fl.p;
+      int* all = g->all.p;
+      g->exec = build_loop_graph(
+          [&](cudaStream_t cs) {
+            TAM_CUDA(cudaEventRecord(ev[n_sys], cs));
+            for (int i = 0; i < n_sys; ++i) {
+              TAM_CUDA(cudaStreamWaitEvent(br[i], ev[n_sys], 0));
+              enqueue_multi_iteration(H[i], br[i]);
+              TAM_CUDA(cudaEventRecord(ev[i], br[i]));
+              TAM_CUDA(cudaStreamWaitEvent(cs, ev[i], 0));
+            }
+            all_stop_kernel<<<1, 32, 0, cs>>>(fl, n_sys, all);
+            TAM_LAUNCH_CHECK();
+          },
+          all, all + 1, H[0]->multi->flags.p + 2, 2, &g->kernels);
+    } catch (...) {
+      cudaGetLastError();
+      cleanup();
+      throw;
+    }
     cleanup();
-    throw;
+    G = std::move(g);
   }
-  cleanup();
+  TAM_CUDA(cudaMemsetAsync(G->all.p, 0, 2 * sizeof(int), s));
+  TAM_CUDA(cudaGraphLaunch(G->exec, s));
+  int loops = 0;
+  TAM_CUDA(cudaMemcpyAsync(&loops, G->all.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TAM_CUDA(cudaStreamSynchronize(s));
+  count_graph_launch(G->kernels * loops);
   int status = TAM_OK, off = 0;
   for (int i = 0; i < n_sys; ++i) {
     const int st = finish_multi(H[i], m[i], B[i], X[i], iters ? iters + off : nullptr, rel ? rel + off : nullptr, s);

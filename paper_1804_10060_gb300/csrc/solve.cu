@@ -479,14 +479,19 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   GridReduce gr{H->partials.p, H->ticket.p};
   PcgScalars* sc = H->sc.p;
   if (!H->bs.p) H->bs = DBuf<double>((size_t)N, s);
-  // the solve runs on b 2^-e and x 2^-e (e from ||b|| and K's range, see centering_exp)
+  if (!H->xs.p) H->xs = DBuf<double>((size_t)N, s);
+  // the solve runs on its own copies b 2^-e and x 2^-e (e from ||b|| and K's
+  // range, see centering_exp), so the iteration graph never depends on the
+  // caller's buffers
+  double* const xu = x;
   pcg_start_kernel<<<vec_grid(N), TPB, 0, s>>>(b, N, gr, sc, rtol, atol, max_iter, H->K->vmax_exp / 2);
   TAM_LAUNCH_CHECK();
   pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(b, H->bs.p, N, sc, -1);
   TAM_LAUNCH_CHECK();
-  pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(x, x, N, sc, -1);
+  pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(xu, H->xs.p, N, sc, -1);
   TAM_LAUNCH_CHECK();
   b = H->bs.p;
+  x = H->xs.p;
   by_block(H->K->A.br, [&](auto B) {
     constexpr int BR = decltype(B)::value;
     sell_spmv<BR, BR>(H->K->S, x, EpiInitResidual<BR>{b, H->r.p, H->K->n_nodes, gr, sc}, s, H->levels[0].Aop.df,
@@ -495,18 +500,11 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   precondition(H, H->r.p, H->z.p, &sc->stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, sc, 1);
   TAM_LAUNCH_CHECK();
-  // the iterations as one graph: a device-side WHILE loop over one iteration
-  // (rebuilt when the target vector or the stream changes), one launch per solve
-  if (!H->iter_exec || H->graph_x != x || H->graph_stream != s) {
-    if (H->iter_exec) {
-      cudaGraphExecDestroy(H->iter_exec);
-      H->iter_exec = nullptr;
-    }
+  // the iterations as one graph: a device-side WHILE loop over one iteration,
+  // built on the first solve with this hierarchy, one launch per solve
+  if (!H->iter_exec)
     H->iter_exec = build_loop_graph([&](cudaStream_t cs) { enqueue_iteration(H, x, cs); }, &sc->stop, &sc->loops,
                                     &sc->max_iter, 2, &H->graph_kernels);
-    H->graph_x = x;
-    H->graph_stream = s;
-  }
   TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
   // final true residual, always a plain FP64 product; then x back to the caller's scale
   DBuf<double> rn(1, s);
@@ -514,7 +512,7 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
     constexpr int BR = decltype(B)::value;
     sell_spmv<BR, BR>(H->K->S, x, EpiResNorm<BR>{b, H->K->n_nodes, gr, rn.p}, s, /*df=*/false);
   });
-  pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(x, x, N, sc, +1);
+  pcg_scale_kernel<<<vec_grid(N), TPB, 0, s>>>(x, xu, N, sc, +1);
   TAM_LAUNCH_CHECK();
   PcgScalars host;
   TAM_CUDA(cudaMemcpyAsync(&host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
