@@ -242,8 +242,10 @@ int amg_level_export(tam_amg amg, int level, int which, int* n_rows, int* n_cols
 /* SpMV layout the setup chose for one operator of `level` (which = 0 A_level,
  * 1 P, 2 R), host ints: *kind 0 = SELL-32, one thread per block row; 1 =
  * lanes per row over the interleaved lanes-per-row store; 2 = lanes per row
- * over the block-CSR arrays; 3 = whole warps per row over the 8-lane store.
- * *lanes = lanes (kinds 1, 2) or threads (kind 3) per row, 1 for kind 0;
+ * over the block-CSR arrays; 3 = whole warps per row over the 8-lane store;
+ * 4 = block-row lanes over the block-CSR arrays (one lane per row of each
+ * block, 6-row blocks).  *lanes = lanes (kinds 1, 2) or threads (kinds 3, 4)
+ * per row, 1 for kind 0;
  * *df = 1 when its products run in double-float on split values.  The
  * layouts differ only in arithmetic order, not in the operator (Sec. 2.1
  * V-cycle); exposed so that parity tests can name the kernel they cover.

@@ -423,22 +423,17 @@ __global__ void agg_sort_kernel(const int* __restrict__ ap, int n_agg, const int
   }
 }
 
-// warp per aggregate: modified Gram-Schmidt in place on the P_tent blocks
-// (rows: member nodes in increasing id, bs rows each; columns: k modes).
-__global__ void ptent_qr_kernel(const int* __restrict__ ap, const int* __restrict__ mem, int n_agg,
-                                const int* __restrict__ prp, double* __restrict__ pv, int bs, int k, double droptol,
-                                double* __restrict__ Bc) {
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (w >= n_agg) return;
-  const int s = ap[w], e = ap[w + 1];
-  const int rows = (e - s) * bs;
-  double R[6][6];
-  for (int a = 0; a < 6; ++a)
-    for (int b = 0; b < 6; ++b) R[a][b] = 0.0;
-  auto elem = [&](int row, int col) -> double& {
-    int node = mem[s + row / bs];
-    return pv[(size_t)prp[node] * bs * k + (row % bs) * k + col];
-  };
+// warp per aggregate: modified Gram-Schmidt on the P_tent blocks (rows:
+// member nodes in increasing id, bs rows each; columns: k modes).  An
+// aggregate of at most QR_CAP rows is copied into the warp's shared-memory
+// tile once, orthonormalised there and written back (the global path walks
+// the node map for every access of every pass); larger ones work in place.
+// Both paths do the same operations in the same order.
+constexpr int QR_WARPS = 4, QR_CAP = 192;
+
+template <class F>
+__device__ __forceinline__ void mgs_columns(int rows, int k, int lane, double droptol, double (&R)[6][6],
+                                            const F& elem) {
   for (int c = 0; c < k; ++c) {
     double nn = 0.0;
     for (int r = lane; r < rows; r += 32) { double x = elem(r, c); nn += x * x; }
@@ -459,6 +454,35 @@ __global__ void ptent_qr_kernel(const int* __restrict__ ap, const int* __restric
     const double inv = keep ? 1.0 / nv : 0.0;
     for (int r = lane; r < rows; r += 32) elem(r, c) *= inv;
     __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(QR_WARPS * 32)
+ptent_qr_kernel(const int* __restrict__ ap, const int* __restrict__ mem, int n_agg, const int* __restrict__ prp,
+                double* __restrict__ pv, int bs, int k, double droptol, double* __restrict__ Bc) {
+  __shared__ double tile[QR_WARPS][QR_CAP * 6];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * QR_WARPS + wid;
+  if (w >= n_agg) return;  // warp-uniform; no block-wide barrier below
+  const int s = ap[w], e = ap[w + 1];
+  const int rows = (e - s) * bs;
+  double R[6][6];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) R[a][b] = 0.0;
+  auto gaddr = [&](int row, int col) -> double* {
+    const int node = mem[s + row / bs];
+    return pv + (size_t)prp[node] * bs * k + (row % bs) * k + col;
+  };
+  if (rows <= QR_CAP) {
+    double* t = tile[wid];
+    for (int r = lane; r < rows; r += 32)
+      for (int c = 0; c < k; ++c) t[r * k + c] = *gaddr(r, c);
+    __syncwarp();
+    mgs_columns(rows, k, lane, droptol, R, [&](int r, int c) -> double& { return t[r * k + c]; });
+    for (int r = lane; r < rows; r += 32)
+      for (int c = 0; c < k; ++c) *gaddr(r, c) = t[r * k + c];
+  } else {
+    mgs_columns(rows, k, lane, droptol, R, [&](int r, int c) -> double& { return *gaddr(r, c); });
   }
   if (lane == 0)
     for (int a = 0; a < k; ++a)
@@ -627,6 +651,17 @@ static void plan_spop(SpOp& op, Bsr& A, Sell& S, LprStore& store, int spmv_fp64,
     return;
   }
   op.tpr = rows_tpr(A.n_rows, A.nnzb, op.lpr);
+  if (A.br == 6 && A.bc == 6 && (op.tpr || op.lpr != 8)) {
+    // 6x6 blocks in few long rows or in short rows (all but the many medium
+    // rows that take the 8-lane store): block-row lanes over the
+    // block-CSR arrays, double-float unless FP64 is forced (the FP64 pipe
+    // would bound it, as on the whole-warp rows below)
+    op.tpr = 0;
+    op.brw = blockrow_wpr(A.n_rows, A.nnzb, A.br);
+    if (spmv_fp64 != 1) op.df = df = true;
+    if (df) build_df_values(A, s);
+    return;
+  }
   if (op.tpr && spmv_fp64 != 1) op.df = df = true;
   const int store_lpr = op.tpr ? ROWS_LPR : (lpr_store_pays(op.lpr) ? op.lpr : 0);
   if (store_lpr) {
@@ -808,8 +843,8 @@ static void tentative(Level& L, const double* B, double droptol, DBuf<double>& B
   agg_sort_kernel<<<grid_for((long long)na * 32, TPB), TPB, 0, s>>>(ap.p, na, mem.p, sorted.p);
   TAM_LAUNCH_CHECK();
   Bc = DBuf<double>((size_t)na * k * k, s);
-  ptent_qr_kernel<<<grid_for((long long)na * 32, TPB), TPB, 0, s>>>(ap.p, sorted.p, na, Pt.row_ptr.p, Pt.vals.p, bs,
-                                                                    k, 1e-10, Bc.p);
+  ptent_qr_kernel<<<grid_for(na, QR_WARPS), QR_WARPS * 32, 0, s>>>(ap.p, sorted.p, na, Pt.row_ptr.p, Pt.vals.p, bs,
+                                                                   k, 1e-10, Bc.p);
   TAM_LAUNCH_CHECK();
   (void)droptol;
 }

@@ -232,7 +232,10 @@ int amg_level_spmv_plan(tam_amg amg, int level, int which, int* kind, int* lanes
     TAM_CHECK(which == 0 || L.n_agg > 0, TAM_ERR_INVALID_ARG, "amg_level_spmv_plan: the coarsest level has no P/R");
     const SpOp& op = which == 0 ? L.Aop : which == 1 ? L.Pop : L.Rop;
     int k = 0, ln = 0;
-    if (op.lpr == 0) {
+    if (op.brw) {
+      k = 4;
+      ln = op.brw * 32;
+    } else if (op.lpr == 0) {
       k = 0;
       ln = 1;
     } else if (op.L && op.tpr) {
@@ -246,7 +249,8 @@ int amg_level_spmv_plan(tam_amg amg, int level, int which, int* kind, int* lanes
       ln = op.lpr;
     }
     bool split = false;
-    if (op.lpr == 0) split = op.df && op.S && op.S->vals_df.p;
+    if (op.brw) split = op.df && op.B && op.B->vals_df.p;
+    else if (op.lpr == 0) split = op.df && op.S && op.S->vals_df.p;
     else if (op.L) split = op.df && op.L->vals_df.p;
     else split = op.df && op.B && op.B->vals_df.p;
     if (kind) *kind = k;

@@ -599,6 +599,125 @@ lpr_rows_kernel(LprView A, const double* __restrict__ x, Epi epi) {
   epi((sub == 0 && row < A.n_rows) ? row : A.n_rows, acc, sh);
 }
 
+// Block-row lanes (the coarse levels' 6x6 operators): BR lanes per block,
+// lane r of a group multiplies row r of the block by x_c, so a warp step
+// covers G = 32 / BR consecutive blocks of a row, each lane reading its BC
+// values with 16-byte loads from the block-CSR arrays (a row's blocks are
+// contiguous: one coalesced span per step).  Lane r of a group loads and
+// splits x_c[r] only; the group shares the column's BC entries by shuffles.
+// Used for the 6x6 operators with few long rows (coarse levels, restrictions)
+// or short rows (coarse prolongations); the level-1-like operators with many
+// medium rows keep the 8-lane store, whose six independent row sums per lane
+// ran 20% faster there.
+// WPR warps per row take every WPR-th step.  No thread holds a whole block,
+// so the kernel runs at ~50 registers and many warps per SM hide the gather
+// latency (the 8-lane and whole-warp-row kernels hold 36 values per thread:
+// 128 registers, a quarter of the warps).  Sums: a lane's own blocks in
+// order (even and odd columns apart, then together), then the groups of a
+// warp in order, then the row's warps in order.
+constexpr int BLOCKROW_THREADS = 256;
+
+template <int BR, int BC, int WPR, class Epi, bool DF>
+__global__ void __launch_bounds__(BLOCKROW_THREADS)
+blockrow_spmv_kernel(BsrView A, const double* __restrict__ x, Epi epi) {
+  static_assert(BC <= BR && BR <= 32 && (BLOCKROW_THREADS / 32) % WPR == 0, "blockrow_spmv_kernel: shape");
+  constexpr int G = 32 / BR, W = BLOCKROW_THREADS / 32, RPB = W / WPR, BB = BR * BC;
+  using P = typename std::conditional<DF, float2, double>::type;
+  __shared__ double sh[32];
+  __shared__ P part[W][BR];
+  if (epi.skip()) return;  // block-uniform (a device flag)
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * RPB + wid / WPR, wr = wid % WPR;
+  const int g = lane / BR, r = lane - g * BR;
+  const bool act = g < G;
+  P ad;
+  if constexpr (DF) ad = make_float2(0.f, 0.f);
+  else ad = 0.0;
+  if (row < A.n_rows) {  // warp-uniform
+    // two accumulators (even and odd j) halve the dependent chain of
+    // double-float updates per step
+    P ad1;
+    if constexpr (DF) ad1 = make_float2(0.f, 0.f);
+    else ad1 = 0.0;
+    const int p1 = A.rp[row + 1];
+    for (int base = A.rp[row] + wr * G; base < p1; base += WPR * G) {
+      const int p = base + g;
+      const bool has = act && p < p1;
+      double xr = 0.0;
+      if (has && r < BC) xr = __ldg(x + (size_t)__ldg(A.ci + p) * BC + r);
+      if constexpr (DF) {
+        float2 v[BC];
+        if (has) block_load<BC>(A.v_df + (size_t)p * BB + r * BC, v);
+        const float2 xs = split_bits(xr);
+#pragma unroll
+        for (int j = 0; j < BC; ++j) {
+          const float2 xj = make_float2(__shfl_sync(0xffffffffu, xs.x, g * BR + j),
+                                        __shfl_sync(0xffffffffu, xs.y, g * BR + j));
+          if (has) df_fma((j & 1) ? ad1 : ad, v[j], xj);
+        }
+      } else {
+        double v[BC];
+        if (has) block_load<BC>(A.v + (size_t)p * BB + r * BC, v);
+#pragma unroll
+        for (int j = 0; j < BC; ++j) {
+          const double xj = __shfl_sync(0xffffffffu, xr, g * BR + j);
+          if (has) {
+            if (j & 1) ad1 = fma(v[j], xj, ad1);
+            else ad = fma(v[j], xj, ad);
+          }
+        }
+      }
+    }
+    if constexpr (DF) df_add(ad, ad1);
+    else ad += ad1;
+  }
+  // groups of the warp, in order, into lanes 0 .. BR-1
+#pragma unroll
+  for (int gg = 1; gg < G; ++gg) {
+    if constexpr (DF) {
+      const float2 o = make_float2(__shfl_sync(0xffffffffu, ad.x, gg * BR + r),
+                                   __shfl_sync(0xffffffffu, ad.y, gg * BR + r));
+      if (lane < BR) df_add(ad, o);
+    } else {
+      const double o = __shfl_sync(0xffffffffu, ad, gg * BR + r);
+      if (lane < BR) ad += o;
+    }
+  }
+  if constexpr (WPR > 1) {
+    if (lane < BR) part[wid][lane] = ad;
+    __syncthreads();
+    if (wr == 0 && lane < BR)
+#pragma unroll
+      for (int w = 1; w < WPR; ++w) {
+        if constexpr (DF) df_add(ad, part[wid + w][lane]);
+        else ad += part[wid + w][lane];
+      }
+  }
+  double acc[BR];
+#pragma unroll
+  for (int k = 0; k < BR; ++k) {
+    if constexpr (DF) {
+      const float2 t = make_float2(__shfl_sync(0xffffffffu, ad.x, k), __shfl_sync(0xffffffffu, ad.y, k));
+      acc[k] = df_to_double(t);
+    } else {
+      acc[k] = __shfl_sync(0xffffffffu, ad, k);
+    }
+  }
+  const bool lead = wr == 0 && lane == 0 && row < A.n_rows;
+  epi(lead ? row : A.n_rows, acc, sh);
+}
+
+// Warps per row for blockrow_spmv_kernel: enough warps for two waves of 32
+// resident warps per SM, while each warp keeps at least four steps.
+inline int blockrow_wpr(int n_rows, long long nnzb, int br) {
+  if (n_rows <= 0) return 1;
+  const long long want = 2LL * sm_count() * 32;
+  const double steps = (double)nnzb / n_rows / (32 / br);
+  int w = 1;
+  while (w < 8 && (long long)n_rows * w < want && steps / (2 * w) >= 4.0) w <<= 1;
+  return w;
+}
+
 // A sparse operator with its SpMV strategy: SELL-32 thread-per-row (lpr == 0)
 // or LPR lanes per row (over the interleaved store L when built, else over the
 // Bsr arrays).
@@ -609,6 +728,7 @@ struct SpOp {
   bool df = true;  // use the storage's split copy when it has one
   const LprStore* L = nullptr;
   int tpr = 0;     // > 0: lpr_rows_kernel with tpr threads per row over L (an 8-lane store)
+  int brw = 0;     // > 0: blockrow_spmv_kernel with brw warps per row over B (lpr and L unused)
 };
 
 // Threads that fill the GPU (1,024 per SM) for the SpMV layout choices.
@@ -713,8 +833,33 @@ void rows_launch(const SpOp& op, const LprView& v, const double* x, Epi epi, cud
   TAM_LAUNCH_CHECK();
 }
 
+template <int BR, int BC, class Epi, bool DF>
+void blockrow_launch(const SpOp& op, const BsrView& v, const double* x, Epi epi, cudaStream_t s) {
+  if constexpr (BC <= BR && BR >= 2) {
+    const unsigned g = grid_for(v.n_rows, (BLOCKROW_THREADS / 32) / op.brw);
+    switch (op.brw) {
+      case 1: blockrow_spmv_kernel<BR, BC, 1, Epi, DF><<<g, BLOCKROW_THREADS, 0, s>>>(v, x, epi); break;
+      case 2: blockrow_spmv_kernel<BR, BC, 2, Epi, DF><<<g, BLOCKROW_THREADS, 0, s>>>(v, x, epi); break;
+      case 4: blockrow_spmv_kernel<BR, BC, 4, Epi, DF><<<g, BLOCKROW_THREADS, 0, s>>>(v, x, epi); break;
+      case 8: blockrow_spmv_kernel<BR, BC, 8, Epi, DF><<<g, BLOCKROW_THREADS, 0, s>>>(v, x, epi); break;
+      default: throw Error(TAM_ERR_INTERNAL, "spmv: block-row lanes need 1, 2, 4 or 8 warps per row");
+    }
+    TAM_LAUNCH_CHECK();
+  } else {
+    throw Error(TAM_ERR_INTERNAL, "spmv: block-row lanes need a block at least as tall as wide");
+  }
+}
+
 template <int BR, int BC, class Epi>
 void spop_apply(const SpOp& op, const double* x, Epi epi, cudaStream_t s) {
+  if (op.brw) {
+    const BsrView v{op.B->n_rows, op.B->row_ptr.p, op.B->col_idx.p, op.B->vals.p, op.B->vals_df.p};
+    if (op.df && v.v_df)
+      blockrow_launch<BR, BC, Epi, true>(op, v, x, epi, s);
+    else
+      blockrow_launch<BR, BC, Epi, false>(op, v, x, epi, s);
+    return;
+  }
   if (op.lpr == 0) {
     sell_spmv<BR, BC>(*op.S, x, epi, s, op.df);
     return;

@@ -94,10 +94,12 @@ def test_full_box_vcycle_matches_oracle_on_gpu_operators(full_box, full_box_orac
     plans = {(lev, w): tam.amg_level_spmv_plan(H, lev, w)
              for lev in range(info["n_levels"] - 1) for w in (0, 1, 2)}
     kinds = {p["kind"] for p in plans.values()}
-    assert {0, 1, 3} <= kinds, plans                         # SELL, 8-lane store, whole-warp rows
-    assert plans[(0, 0)]["kind"] == 0                        # K: SELL-32
-    assert plans[(1, 0)] ["kind"] == 1 and plans[(1, 0)]["lanes"] == 8, plans[(1, 0)]
-    assert any(p["kind"] == 3 and p["lanes"] >= 32 for p in plans.values())
+    assert kinds == {0, 1, 4}, plans                         # SELL-32, 8-lane store, block-row lanes
+    assert plans[(0, 0)]["kind"] == 0 and plans[(0, 1)]["kind"] == 0   # K and P_0: SELL-32
+    assert plans[(0, 2)]["kind"] == 1 and plans[(0, 2)]["lanes"] == 8  # R_0 (6x3): 8-lane store
+    assert plans[(1, 0)]["kind"] == 1 and plans[(1, 0)]["lanes"] == 8  # A_1: 8-lane store
+    assert plans[(1, 1)]["kind"] == 4                        # P_1 (short rows): block-row lanes
+    assert any(p["kind"] == 4 and p["lanes"] >= 64 for p in plans.values())   # coarse long rows: several warps
     if spmv_fp64 == 0:
         assert plans[(0, 0)]["df"] and plans[(1, 0)]["df"]   # >= 2^20 blocks: double-float products
     else:
