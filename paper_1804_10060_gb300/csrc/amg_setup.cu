@@ -475,12 +475,16 @@ ptent_qr_kernel(const int* __restrict__ ap, const int* __restrict__ mem, int n_a
   };
   if (rows <= QR_CAP) {
     double* t = tile[wid];
-    for (int r = lane; r < rows; r += 32)
-      for (int c = 0; c < k; ++c) t[r * k + c] = *gaddr(r, c);
+    for (int r = lane; r < rows; r += 32) {
+      const double* src = gaddr(r, 0);  // the row's k values are contiguous
+      for (int c = 0; c < k; ++c) t[r * k + c] = src[c];
+    }
     __syncwarp();
     mgs_columns(rows, k, lane, droptol, R, [&](int r, int c) -> double& { return t[r * k + c]; });
-    for (int r = lane; r < rows; r += 32)
-      for (int c = 0; c < k; ++c) *gaddr(r, c) = t[r * k + c];
+    for (int r = lane; r < rows; r += 32) {
+      double* dst = gaddr(r, 0);
+      for (int c = 0; c < k; ++c) dst[c] = t[r * k + c];
+    }
   } else {
     mgs_columns(rows, k, lane, droptol, R, [&](int r, int c) -> double& { return *gaddr(r, c); });
   }
@@ -1048,7 +1052,7 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       if (arith == SpgemmArith::kDoubleFloat) As = split_values(*L.A, s);
       SpgemmSplit spA;
       spA.x = As.p;
-      bsr_spgemm(*L.A, L.Pt, L.P, s, arith, spA);
+      if (!bsr_spgemm_tentative(*L.A, L.Pt, L.agg.p, L.P, s, arith, As.p)) bsr_spgemm(*L.A, L.Pt, L.P, s, arith, spA);
       T.mark(0, s);  // waiting for lambda_max counts as its phase
       side.join(s);
       T.mark(3, s);

@@ -209,6 +209,12 @@ DBuf<float2> split_values(const Bsr& B, cudaStream_t s);
 // C = X Y (block shapes 3/6).
 void bsr_spgemm(const Bsr& X, const Bsr& Y, Bsr& C, cudaStream_t s, SpgemmArith arith = SpgemmArith::kDoubleFloat,
                 const SpgemmSplit& sp = SpgemmSplit());
+// C = X P_tent for a tentative prolongator (one block per aggregated row k, in
+// column agg[k]; agg[k] < 0: an empty row), xs: X's split values or NULL.
+// Returns false, with C untouched, for block shapes other than 3x3.3x6,
+// 6x6.6x6, 1x1.1x1 or a row of X longer than 256 blocks (use bsr_spgemm).
+bool bsr_spgemm_tentative(const Bsr& X, const Bsr& Pt, const int* agg, Bsr& C, cudaStream_t s, SpgemmArith arith,
+                          const float2* xs);
 
 // ---------------------------------------------------------------------------
 // Thread-per-row SELL SpMV with a fused epilogue.
@@ -454,16 +460,29 @@ lpr_spmv_kernel(LprView A, const double* __restrict__ x, Epi epi) {
       float2 ad[BR];
 #pragma unroll
       for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
+      // the x gather runs one group ahead: the next group's column and x
+      // entries are requested before this group's products, so that they
+      // arrive together with the next group's values (one memory round trip
+      // per group instead of values, then column and gather)
+      double xg[BC];
+      if (g0 < g1) {
+        const int c = __ldg(A.cols + (size_t)g0 * LPR + sub);
+#pragma unroll
+        for (int j = 0; j < BC; ++j) xg[j] = __ldg(x + (size_t)c * BC + j);
+      }
       for (int g = g0; g < g1; ++g) {
-        // the group's values first (all BB loads in flight), then the gather
         const float2* __restrict__ vb = A.v_df + (size_t)g * BB * LPR + sub;
         float2 vv[BB];
 #pragma unroll
         for (int e = 0; e < BB; ++e) vv[e] = __ldg(vb + e * LPR);
-        const int c = __ldg(A.cols + (size_t)g * LPR + sub);
         float2 xv[BC];
 #pragma unroll
-        for (int j = 0; j < BC; ++j) xv[j] = split_bits(__ldg(x + (size_t)c * BC + j));
+        for (int j = 0; j < BC; ++j) xv[j] = split_bits(xg[j]);
+        if (g + 1 < g1) {
+          const int c = __ldg(A.cols + (size_t)(g + 1) * LPR + sub);
+#pragma unroll
+          for (int j = 0; j < BC; ++j) xg[j] = __ldg(x + (size_t)c * BC + j);
+        }
 #pragma unroll
         for (int r = 0; r < BR; ++r)
 #pragma unroll
