@@ -748,8 +748,9 @@ def learned_variant(tam, meshgen, stream, world, n_train=16, train_steps=1500, e
 
     with torch.cuda.stream(stream):
         guess_ms = t_ms(lambda: tam.tam_learned_guess(net, H, F, rhs, bf16=True, stream=stream))
-        infer_bf16_ms = t_ms(lambda: net.forward(F, bf16=True, stream=stream))
-        infer_fp32_ms = t_ms(lambda: net.forward(F, bf16=False, stream=stream))
+        infer_bf16_ms = t_ms(lambda: net.forward(F, bf16=1, stream=stream))
+        infer_bf16_layered_ms = t_ms(lambda: net.forward(F, bf16=2, stream=stream))
+        infer_fp32_ms = t_ms(lambda: net.forward(F, bf16=0, stream=stream))
     nx0 = float(torch.linalg.norm(x0))
     out = {"workload": LEARNED_WORKLOAD.format(n_train=n_train, n_eval=pb.n_dof), "n_dof": pb.n_dof,
            "value": world * pb.n_dof / (ms1 * 1e-3), "unit": "DOF/s", "ms_per_solve": ms1,
@@ -765,8 +766,10 @@ def learned_variant(tam, meshgen, stream, world, n_train=16, train_steps=1500, e
                          "iterations": it0, "final_rel_resid": rel0},
            "speedup_vs_zero_start": ms0 / ms1,
            "guess_ms": guess_ms,
-           "inference_ms": {"bf16_tensor_core_mma": infer_bf16_ms, "fp32_cuda_core": infer_fp32_ms,
-                            "rows": int(F.shape[0])},
+           "inference_ms": {"bf16_tensor_core_one_kernel": infer_bf16_ms,
+                            "bf16_tensor_core_layer_by_layer": infer_bf16_layered_ms,
+                            "fp32_cuda_core": infer_fp32_ms, "rows": int(F.shape[0])},
+           "training_data_ms_per_solve": 1e3 * (t1 - t0) / n_train,
            "training": {"solves": n_train, "rows": int(X.shape[0]), "steps": train_steps,
                         "data_ms": 1e3 * (t1 - t0), "train_ms": 1e3 * (t2 - t1),
                         "loss_first": hist[0], "loss_last": hist[-1]}}

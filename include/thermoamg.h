@@ -351,7 +351,12 @@ int tam_mlp_set_normalization(tam_mlp mlp, const float* shift_host, const float*
 /* copy all parameters out of / into host memory (n_params floats) */
 int tam_mlp_get_params(tam_mlp mlp, float* theta_host);
 int tam_mlp_set_params(tam_mlp mlp, const float* theta_host);
-/* Y[n x n_out] = net(X[n x n_in]); bf16 != 0 reads BF16 copies of the weights */
+/* Y[n x n_out] = net(X[n x n_in]) (device arrays, row-major).  bf16 = 0: FP32
+ * weights and activations, one kernel per layer; 1: BF16 weights and
+ * BF16-rounded activations on the tensor cores with FP32 accumulation, the
+ * whole network in one kernel (activations never leave the SM; nets of at
+ * most 8 layers of width <= 128, else layer by layer); 2: the same BF16
+ * arithmetic one kernel per layer (bitwise the same results as 1). */
 int tam_mlp_forward(tam_mlp mlp, long long n, const float* X, float* Y, int bf16, void* stream);
 /* mean squared error of net(X) against Yt and its gradient (grad_host: n_params
  * floats, may be NULL); synchronising */

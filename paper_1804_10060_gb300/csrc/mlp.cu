@@ -300,6 +300,159 @@ dense_mma_kernel(const float* __restrict__ A, long long n, int K, int N, const _
   }
 }
 
+// ---------------------------------------------------------------------------
+// The whole network in one kernel (BF16 inference): every layer's transposed
+// BF16 weights and FP32 biases sit in shared memory for the kernel's life;
+// each warp takes 16 rows at a time through all layers with the activations
+// in registers -- the FP32 accumulators of one layer's 16 x 8 output tiles,
+// biased, passed through tanh and rounded to BF16, are exactly the A
+// fragments of the next layer's m16n8k16 products (tiles 2m and 2m+1 form
+// k-chunk m).  Per row only the n_in inputs are read and the n_out outputs
+// written.  Same roundings, products and summation order as the layer-by-
+// layer kernel above, so the results are bitwise the same.
+// ---------------------------------------------------------------------------
+constexpr int FUSED_WARPS = 8;
+constexpr int FUSED_MAX_LAYERS = 8;
+constexpr int FUSED_WMAX = 128;  // widest layer (inputs and outputs)
+
+struct FusedNet {
+  int L;
+  int K[FUSED_MAX_LAYERS], N[FUSED_MAX_LAYERS];    // true fan-in / fan-out
+  int Kp[FUSED_MAX_LAYERS], Np[FUSED_MAX_LAYERS];  // padded: K to 16, N to 16 (hidden) or 8 (last)
+  int wsm[FUSED_MAX_LAYERS], bsm[FUSED_MAX_LAYERS];  // shared-memory offsets (bf16 / float elements)
+  long long woff[FUSED_MAX_LAYERS];                // W_l in theta (bias follows)
+  int w_elems, b_elems;
+};
+
+__device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+__global__ void __launch_bounds__(FUSED_WARPS * 32, 2)
+mlp_fused_kernel(const float* __restrict__ X, long long n, FusedNet net, const __nv_bfloat16* __restrict__ th16,
+                 const float* __restrict__ th, const float* __restrict__ shift, const float* __restrict__ scale,
+                 const float* __restrict__ out_scale, float* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(sm_raw);
+  float* Bs = reinterpret_cast<float*>(sm_raw + (((size_t)net.w_elems * 2 + 15) & ~(size_t)15));
+  // W_l^T [Np][Kp + 8] (zero-padded) and b_l [Np]
+  for (int l = 0; l < net.L; ++l) {
+    const int K = net.K[l], N = net.N[l], Kp = net.Kp[l], Np = net.Np[l], ld = Kp + 8;
+    const __nv_bfloat16* W = th16 + net.woff[l];
+    for (int e = threadIdx.x; e < Np * ld; e += blockDim.x) {
+      const int nn = e / ld, k = e - nn * ld;
+      Ws[net.wsm[l] + e] = (nn < N && k < K) ? W[(size_t)k * N + nn] : __float2bfloat16(0.f);
+    }
+    const float* b = th + net.woff[l] + (long long)K * N;
+    for (int e = threadIdx.x; e < Np; e += blockDim.x) Bs[net.bsm[l] + e] = e < N ? b[e] : 0.f;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int n_in = net.K[0], n_out = net.N[net.L - 1];
+  for (long long r0 = ((long long)blockIdx.x * FUSED_WARPS + warp) * 16; r0 < n;
+       r0 += (long long)gridDim.x * FUSED_WARPS * 16) {
+    unsigned af[FUSED_WMAX / 16][4];
+    // layer 0's A fragments from the standardised inputs of rows r0+g, r0+g+8
+    {
+      const long long ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll
+      for (int m = 0; m < FUSED_WMAX / 16; ++m) {
+        if (m * 16 >= net.Kp[0]) break;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          // q: 0,1 (ra, 2t..), 2,3 (rb, 2t..), 4,5 (ra, 2t+8..), 6,7 (rb, 2t+8..)
+          const long long row = (q & 2) ? rb : ra;
+          const int k = m * 16 + 2 * t + (q & 1) + ((q & 4) ? 8 : 0);
+          float a = 0.f;
+          if (row < n && k < n_in) a = (X[row * n_in + k] - shift[k]) * scale[k];
+          v[q] = a;
+        }
+        af[m][0] = pack_bf16x2(v[0], v[1]);
+        af[m][1] = pack_bf16x2(v[2], v[3]);
+        af[m][2] = pack_bf16x2(v[4], v[5]);
+        af[m][3] = pack_bf16x2(v[6], v[7]);
+      }
+    }
+    for (int l = 0; l < net.L; ++l) {
+      const int Kp = net.Kp[l], Np = net.Np[l], ld = Kp + 8;
+      const __nv_bfloat16* Wt = Ws + net.wsm[l];
+      float acc[FUSED_WMAX / 8][4];
+#pragma unroll
+      for (int j = 0; j < FUSED_WMAX / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+      for (int m = 0; m < FUSED_WMAX / 16; ++m) {
+        if (m * 16 >= Kp) break;
+#pragma unroll
+        for (int j = 0; j < FUSED_WMAX / 8; ++j) {
+          if (j * 8 >= Np) break;
+          const __nv_bfloat16* wb = Wt + (j * 8 + g) * ld + m * 16 + 2 * t;
+          mma_bf16_16x8x16(acc[j], af[m][0], af[m][1], af[m][2], af[m][3], *reinterpret_cast<const unsigned*>(wb),
+                           *reinterpret_cast<const unsigned*>(wb + 8));
+        }
+      }
+      const float* bl = Bs + net.bsm[l];
+      if (l + 1 < net.L) {
+        // hidden layer: tanh(acc + b), rounded to BF16, becomes the next A
+#pragma unroll
+        for (int m = 0; m < FUSED_WMAX / 16; ++m) {
+          if (m * 16 >= Np) break;
+          float z[2][4];
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) z[u][h] = tanhf(acc[2 * m + u][h] + bl[(2 * m + u) * 8 + 2 * t + (h & 1)]);
+          af[m][0] = pack_bf16x2(z[0][0], z[0][1]);
+          af[m][1] = pack_bf16x2(z[0][2], z[0][3]);
+          af[m][2] = pack_bf16x2(z[1][0], z[1][1]);
+          af[m][3] = pack_bf16x2(z[1][2], z[1][3]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < FUSED_WMAX / 8; ++j) {
+          if (j * 8 >= Np) break;
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const long long row = r0 + g + (h >= 2 ? 8 : 0);
+            const int c = j * 8 + 2 * t + (h & 1);
+            if (row < n && c < n_out) Y[row * n_out + c] = (acc[j][h] + bl[c]) * out_scale[c];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Shapes the fused kernel takes: at most FUSED_MAX_LAYERS layers, every fan-in
+// and fan-out at most FUSED_WMAX; false otherwise (layer-by-layer kernels).
+bool fused_net(const tam_mlp_s* M, FusedNet& f, size_t& smem) {
+  const int L = (int)M->shapes.size();
+  if (L < 1 || L > FUSED_MAX_LAYERS) return false;
+  f = FusedNet{};
+  f.L = L;
+  int w = 0, b = 0;
+  for (int l = 0; l < L; ++l) {
+    const int K = M->shapes[l].first, N = M->shapes[l].second;
+    if (K > FUSED_WMAX || N > FUSED_WMAX) return false;
+    f.K[l] = K;
+    f.N[l] = N;
+    f.Kp[l] = (K + 15) & ~15;
+    f.Np[l] = l + 1 < L ? (N + 15) & ~15 : (N + 7) & ~7;
+    if (l > 0 && f.Kp[l] != f.Np[l - 1]) return false;  // chained widths
+    f.wsm[l] = w;
+    f.bsm[l] = b;
+    f.woff[l] = M->offset[l];
+    w += f.Np[l] * (f.Kp[l] + 8);
+    b += f.Np[l];
+  }
+  f.w_elems = w;
+  f.b_elems = b;
+  smem = (((size_t)w * 2 + 15) & ~(size_t)15) + (size_t)b * 4;
+  return smem <= 200 * 1024;
+}
+
 size_t dense_mma_smem(int N) {
   return sizeof(__nv_bfloat16) * ((size_t)((N + 7) & ~7) * MMA_LD + (size_t)MMA_ROWS * MMA_LD);
 }
@@ -418,19 +571,40 @@ double loss_and_grad(tam_mlp_s* M, const float* X, const float* Y, long long n, 
   return read_back_double(loss.p, s);
 }
 
-float* forward_any(tam_mlp_s* M, const float* X, long long n, int bf16, cudaStream_t s) {
-  if (!bf16) return forward<float>(M, X, n, M->theta.p, false, s);
+void ensure_bf16(tam_mlp_s* M, cudaStream_t s) {
   if (!M->theta16_valid) {
     to_bf16_kernel<<<ew_grid(M->n_par), 256, 0, s>>>(M->theta.p, M->theta16.p, M->n_par);
     TAM_LAUNCH_CHECK();
     M->theta16_valid = true;
   }
+}
+
+float* forward_any(tam_mlp_s* M, const float* X, long long n, int bf16, cudaStream_t s) {
+  if (!bf16) return forward<float>(M, X, n, M->theta.p, false, s);
+  ensure_bf16(M, s);
   return forward<__nv_bfloat16>(M, X, n, M->theta16.p, false, s);
 }
 
 }  // namespace
 
+// bf16: 0 FP32 layer by layer; 1 BF16 tensor cores, the whole network in one
+// kernel when its shapes allow (else layer by layer); 2 BF16 layer by layer.
 void mlp_forward_device(tam_mlp_s* M, long long n, const float* X, float* Y, int bf16, cudaStream_t s) {
+  FusedNet f;
+  size_t smem = 0;
+  if (bf16 == 1 && fused_net(M, f, smem)) {
+    ensure_bf16(M, s);
+    if (n > 0) {
+      TAM_CUDA(cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const long long tiles = (n + 15) / 16;
+      const unsigned grid = (unsigned)std::min<long long>((tiles + FUSED_WARPS - 1) / FUSED_WARPS,
+                                                          (long long)sm_count() * 2);
+      mlp_fused_kernel<<<std::max(1u, grid), FUSED_WARPS * 32, smem, s>>>(
+          X, n, f, M->theta16.p, M->theta.p, M->shift.p, M->scale.p, M->out_scale.p, Y);
+      TAM_LAUNCH_CHECK();
+    }
+    return;
+  }
   float* out = forward_any(M, X, n, bf16, s);
   TAM_CUDA(cudaMemcpyAsync(Y, out, 4 * (size_t)n * M->n_out, cudaMemcpyDeviceToDevice, s));
 }

@@ -51,6 +51,23 @@ def test_forward_and_gradient_match_oracle(width, depth):
     assert np.linalg.norm(g_g - g_o) <= 1e-4 * np.linalg.norm(g_o)
 
 
+@pytest.mark.parametrize("width,depth,n", [(16, 2, 3000), (128, 3, 4099), (128, 3, 7)])
+def test_fused_bf16_inference_equals_layer_by_layer(width, depth, n):
+    """The one-kernel BF16 network (activations kept in registers between
+    layers) makes the same roundings, products and sums as the layer-by-layer
+    BF16 kernels: bitwise equal outputs, ragged last tile included."""
+    tam = need_gpu()
+    net, shapes, shift, scale, out_scale = _net(tam, width, depth)
+    rng = np.random.default_rng(2)
+    Xg = torch.from_numpy(rng.standard_normal((n, 8)).astype(np.float32)).cuda()
+    fused = net.forward(Xg, bf16=1).cpu().numpy()
+    layered = net.forward(Xg, bf16=2).cpu().numpy()
+    assert np.array_equal(fused, layered)
+    theta = net.get_params().astype(np.float64)
+    ref, _ = omlp.forward(theta, shapes, Xg.cpu().numpy().astype(np.float64), shift, scale, out_scale)
+    assert np.abs(fused - ref).max() <= 3e-2 * np.abs(ref).max()
+
+
 def test_adam_step_matches_oracle():
     tam = need_gpu()
     net, shapes, shift, scale, out_scale = _net(tam)
