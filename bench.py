@@ -524,6 +524,8 @@ def disc_variant(tam, meshgen, stream, flush, world, reps=2):
             ref = x
         rec["rel_l2_vs_fp64_path"] = float(torch.linalg.norm(x - ref) / torch.linalg.norm(ref))
         out[name] = {"value": job_value(pb.n_dof, ms, world), "unit": "DOF/s", "ms_per_step": ms, **rec}
+        if prec == 2:
+            out[name]["note"] = "requested BF16 finest values; the library keeps FP32 for a P2 K"
     return out
 
 

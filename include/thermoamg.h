@@ -180,7 +180,9 @@ typedef struct amg_params {
   int max_levels;          /* including the finest; default 10                                       */
   int use_rotations;       /* 1: six rigid-body modes; 0: three translations only; default 1         */
   int level_precision;     /* V-cycle storage/arithmetic: 0 FP64; 1 FP32; 2 FP32 with BF16 finest-level
-                              values.  The outer CG and the coarsest dense solve stay FP64; default 0 */
+                              values (P1 meshes; a P2 K keeps FP32 there, as BF16's 8-bit mantissa
+                              doubles its iterations).  The outer CG and the coarsest dense solve stay
+                              FP64; default 0 */
   double strength_theta_scale; /* level l uses strength_theta * strength_theta_scale^l; default 0.5    */
   int setup_fp64;          /* products of the setup (A P_tent, A P, R (A P)) in plain FP64 arithmetic (1)
                               or in double-float, two FP32 values per operand with error-free transforms,
@@ -238,6 +240,15 @@ int amg_level_aggregates(tam_amg amg, int level, int* agg, void* stream);
  * row_ptr[n_rows+1], col_idx[nnzb], vals[nnzb*br*bc].  Synchronising. */
 int amg_level_export(tam_amg amg, int level, int which, int* n_rows, int* n_cols, int* br, int* bc,
                      long long* nnzb, int* row_ptr, int* col_idx, double* vals, void* stream);
+
+/* Residual history of the last amg_pcg_solve with this hierarchy (not the
+ * batched solve): hist_host[k] = ||r_k||_2, the recursively updated residual
+ * the stopping test reads (Sec. 2.1; r_0 = b - K x_0), for k = 0 .. iters, in
+ * the caller's units; at most cap entries are written (host array), *n_host
+ * (may be NULL) = iters + 1, or 0 before the first solve.  Recorded on the
+ * device by the iteration kernels (one store per iteration) and copied out
+ * here; synchronising.  Errors: INVALID_ARG. */
+int amg_residual_history(tam_amg amg, double* hist_host, int cap, int* n_host, void* stream);
 
 /* SpMV layout the setup chose for one operator of `level` (which = 0 A_level,
  * 1 P, 2 R), host ints: *kind 0 = SELL-32, one thread per block row; 1 =

@@ -606,11 +606,13 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
                                   const int* mat, int n_mat, const double* props, const double* T,
                                   double T_ref, const double* body, const unsigned char* dmask,
                                   const double* ud, double* rhs, cudaStream_t s) {
+  NvtxRange nvtx("tam: assemble K and f");
   TAM_CHECK(n_nodes > 0 && n_cells >= 0 && n_mat > 0, TAM_ERR_INVALID_ARG, "fem_assemble: bad sizes");
   TAM_CHECK(npc == 4 || npc == 10, TAM_ERR_INVALID_ARG, "fem_assemble: nodes_per_cell must be 4 or 10");
   TAM_CHECK(coords && (cells || n_cells == 0) && (mat || n_cells == 0) && props && dmask && rhs,
             TAM_ERR_INVALID_ARG, "fem_assemble: null pointer");
   auto M = new tam_matrix_s();
+  M->nodes_per_cell = npc;
   try {
     M->n_nodes = n_nodes;
     const long long n_entries = (long long)n_cells * npc;
@@ -673,6 +675,7 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
 void assemble_loads(tam_matrix_s* K, const double* coords, int n_cells, int npc, const int* cells, const int* mat,
                     int n_mat, const double* props, const double* T, double T_ref, const double* body,
                     const double* ud, double* rhs, cudaStream_t s) {
+  NvtxRange nvtx("tam: assemble f");
   TAM_CHECK(K && coords && props && rhs && n_mat > 0 && n_cells >= 0 && (npc == 4 || npc == 10) &&
                 (cells || n_cells == 0) && (mat || n_cells == 0),
             TAM_ERR_INVALID_ARG, "fem_assemble_load: bad argument");

@@ -188,6 +188,22 @@ int amg_setup_stats(tam_amg amg, double* phase_ms_host) {
   });
 }
 
+int amg_residual_history(tam_amg amg, double* hist_host, int cap, int* n_host, void* stream) {
+  return guarded([&] {
+    TAM_CHECK(amg && cap >= 0 && (hist_host || cap == 0), TAM_ERR_INVALID_ARG, "amg_residual_history: bad argument");
+    const long long n = std::min<long long>(amg->hist_len, cap);
+    if (n_host) *n_host = (int)amg->hist_len;
+    if (n > 0) {
+      cudaStream_t s = as_stream(stream);
+      TAM_CUDA(cudaMemcpyAsync(hist_host, amg->hist.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+      TAM_CUDA(cudaStreamSynchronize(s));
+      const double f = std::ldexp(1.0, amg->hist_scale_exp);
+      for (long long k = 0; k < n; ++k) hist_host[k] = std::sqrt(hist_host[k]) * f;
+    }
+    return TAM_OK;
+  });
+}
+
 int amg_level_aggregates(tam_amg amg, int level, int* agg, void* stream) {
   return guarded([&] {
     TAM_CHECK(amg && agg && level >= 0 && level < (int)amg->levels.size(), TAM_ERR_INVALID_ARG,

@@ -11,6 +11,7 @@
 #include <stdexcept>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
 #include "thermoamg.h"
 
 namespace tam {
@@ -86,6 +87,16 @@ struct DBuf {
   }
   void zero() { if (p) TAM_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s)); }
   T* get() const { return p; }
+};
+
+// A named NVTX range for the lifetime of the object (host side: what a
+// profiler's timeline shows for the library's phases; costs nothing when no
+// tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // Small pinned host staging area for synchronous scalar read-backs.

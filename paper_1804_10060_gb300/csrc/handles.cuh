@@ -10,6 +10,7 @@
 
 struct tam_matrix_s {
   int n_nodes = 0;
+  int nodes_per_cell = 0;              // 4 (P1) or 10 (P2) tetrahedra
   // floor(log2 max |K_ij|) over the rows with off-diagonal blocks, and whether
   // K is finite and within the double-float range (|exponent| <= kDfExpLimit):
   // else every product with K is plain FP64
@@ -118,6 +119,9 @@ struct tam_amg_s {
   // PCG workspace
   tam::DBuf<double> r, z, p, q;
   tam::DBuf<double> bs, xs;              // b and x scaled by the solve's power of two
+  tam::DBuf<double> hist;                // ||r_k||^2 of the last solve (scaled), k = 0 .. hist_len - 1
+  long long hist_len = 0;
+  int hist_scale_exp = 0;
   tam::DBuf<tam::PcgScalars> sc;
   tam::DBuf<double> partials;            // grid-reduction partials
   tam::DBuf<unsigned int> ticket;

@@ -125,6 +125,7 @@ extern "C" int tam_node_features(int n_nodes, const double* coords, int n_cells,
 extern "C" int tam_learned_guess(tam_mlp_s* M, tam_amg H, const float* features, const double* rhs, int bf16,
                                  int smooth_degree, double* x, int* used_host, double* energy_ratio_host,
                                  void* stream) {
+  NvtxRange nvtx("tam: learned initial guess");
   try {
     set_last_error("");
     TAM_CHECK(M && H && features && rhs && x, TAM_ERR_INVALID_ARG, "tam_learned_guess: NULL argument");

@@ -590,6 +590,7 @@ float* forward_any(tam_mlp_s* M, const float* X, long long n, int bf16, cudaStre
 // bf16: 0 FP32 layer by layer; 1 BF16 tensor cores, the whole network in one
 // kernel when its shapes allow (else layer by layer); 2 BF16 layer by layer.
 void mlp_forward_device(tam_mlp_s* M, long long n, const float* X, float* Y, int bf16, cudaStream_t s) {
+  NvtxRange nvtx("tam: network inference");
   FusedNet f;
   size_t smem = 0;
   if (bf16 == 1 && fused_net(M, f, smem)) {

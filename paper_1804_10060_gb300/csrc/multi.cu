@@ -857,6 +857,7 @@ __global__ void all_stop_kernel(int* const* __restrict__ flags, int n, int* __re
 
 int pcg_solve_batch(int n_sys, tam_amg_s* const* H, const int* m, const double* const* B, double* const* X,
                     double rtol, double atol, int max_iter, int* iters, double* rel, cudaStream_t s) {
+  NvtxRange nvtx("tam: batched AMG-PCG solve");
   TAM_CHECK(n_sys >= 1 && n_sys <= 64 && rtol >= 0 && atol >= 0 && max_iter >= 0, TAM_ERR_INVALID_ARG,
             "batch solve: bad argument");
   for (int i = 0; i < n_sys; ++i)

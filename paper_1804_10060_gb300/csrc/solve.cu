@@ -138,6 +138,7 @@ struct EpiInitResidual {
   int n_rows;
   GridReduce gr;
   PcgScalars* sc;
+  double* hist;  // residual history (||r_k||^2 in the solve's scaling), entry 0
   __device__ bool skip() const { return false; }
   __device__ void operator()(int row, const double (&acc)[BR], double* sh) const {
     double s[1] = {0.0};
@@ -152,6 +153,7 @@ struct EpiInitResidual {
     double tot[1];
     if (grid_reduce<1>(gr, s, tot, sh) && threadIdx.x == 0) {
       sc->rr = tot[0];
+      hist[0] = tot[0];
       if (!isfinite(tot[0])) { sc->status = TAM_ERR_NAN; sc->stop = 1; }
       else if (tot[0] <= sc->tol2) sc->stop = 1;
       else if (sc->max_iter <= 0) { sc->status = TAM_ERR_NOT_CONVERGED; sc->stop = 1; }
@@ -209,7 +211,8 @@ struct EpiPq {
 
 // x += alpha p; r -= alpha q; ||r||^2; convergence / cap
 __global__ void pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                                  const double* __restrict__ q, long long N, GridReduce gr, PcgScalars* sc) {
+                                  const double* __restrict__ q, long long N, GridReduce gr, PcgScalars* sc,
+                                  double* __restrict__ hist, int hist_cap) {
   __shared__ double sh[32];
   if (sc->stop) return;
   const double a = sc->alpha;
@@ -224,6 +227,7 @@ __global__ void pcg_update_kernel(double* __restrict__ x, double* __restrict__ r
   if (grid_reduce<1>(gr, acc, tot, sh) && threadIdx.x == 0) {
     sc->rr = tot[0];
     sc->iter += 1;
+    if (sc->iter < hist_cap) hist[sc->iter] = tot[0];
     if (!isfinite(tot[0])) { sc->status = TAM_ERR_NAN; sc->stop = 1; }
     else if (tot[0] <= sc->tol2) sc->stop = 1;
     else if (sc->iter >= sc->max_iter) { sc->status = TAM_ERR_NOT_CONVERGED; sc->stop = 1; }
@@ -388,7 +392,8 @@ void enqueue_iteration(tam_amg_s* H, double* x, cudaStream_t s) {
   GridReduce gr{H->partials.p, H->ticket.p};
   const int* stop = &H->sc.p->stop;
   spmv_outer_pq(H, s);
-  pcg_update_kernel<<<vec_grid(N), TPB, 0, s>>>(x, H->r.p, H->p.p, H->q.p, N, gr, H->sc.p);
+  pcg_update_kernel<<<vec_grid(N), TPB, 0, s>>>(x, H->r.p, H->p.p, H->q.p, N, gr, H->sc.p, H->hist.p,
+                                                (int)H->hist.n);
   TAM_LAUNCH_CHECK();
   precondition(H, H->r.p, H->z.p, stop, s);
   pcg_rz_kernel<<<vec_grid(N), TPB, 0, s>>>(H->r.p, H->z.p, H->p.p, N, gr, H->sc.p, 0);
@@ -474,12 +479,22 @@ void vcycle_apply(tam_amg_s* H, const double* r, double* z, const int* stop, cud
 
 int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol, int max_iter, int* iters,
               double* rel, cudaStream_t s) {
+  NvtxRange nvtx("tam: AMG-PCG solve");
   TAM_CHECK(b && x && rtol >= 0.0 && atol >= 0.0 && max_iter >= 0, TAM_ERR_INVALID_ARG, "amg_pcg_solve: bad argument");
   const long long N = (long long)H->K->n_nodes * H->K->A.br;
   GridReduce gr{H->partials.p, H->ticket.p};
   PcgScalars* sc = H->sc.p;
   if (!H->bs.p) H->bs = DBuf<double>((size_t)N, s);
   if (!H->xs.p) H->xs = DBuf<double>((size_t)N, s);
+  // residual history: ||r_k||^2 for k = 0 .. iterations (its pointer and size
+  // are captured in the iteration graph: a longer one rebuilds the graph)
+  if ((long long)H->hist.n < (long long)max_iter + 1) {
+    H->hist = DBuf<double>((size_t)std::max(max_iter + 1, 1024), s);
+    if (H->iter_exec) {
+      cudaGraphExecDestroy(H->iter_exec);
+      H->iter_exec = nullptr;
+    }
+  }
   // the solve runs on its own copies b 2^-e and x 2^-e (e from ||b|| and K's
   // range, see centering_exp), so the iteration graph never depends on the
   // caller's buffers
@@ -494,7 +509,8 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   x = H->xs.p;
   by_block(H->K->A.br, [&](auto B) {
     constexpr int BR = decltype(B)::value;
-    sell_spmv<BR, BR>(H->K->S, x, EpiInitResidual<BR>{b, H->r.p, H->K->n_nodes, gr, sc}, s, H->levels[0].Aop.df,
+    sell_spmv<BR, BR>(H->K->S, x, EpiInitResidual<BR>{b, H->r.p, H->K->n_nodes, gr, sc, H->hist.p}, s,
+                      H->levels[0].Aop.df,
                       /*acc=*/true);
   });
   precondition(H, H->r.p, H->z.p, &sc->stop, s);
@@ -518,6 +534,8 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   TAM_CUDA(cudaMemcpyAsync(&host, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   double rr = read_back_double(rn.p, s);  // synchronises the stream
   count_graph_launch(H->graph_kernels * host.loops);
+  H->hist_len = std::min<long long>((long long)host.iter + 1, (long long)H->hist.n);
+  H->hist_scale_exp = host.scale_exp;
   if (iters) *iters = host.iter;
   double nb = std::sqrt(host.bb);
   if (rel) *rel = nb > 0 ? std::sqrt(rr) / nb : std::sqrt(rr);

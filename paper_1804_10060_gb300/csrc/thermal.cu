@@ -674,6 +674,7 @@ int tam_thermal_newton(tam_thermal th, double* T, const double* T_old, double dt
                        const double* T_bc, const double* T_dirichlet, double rtol, int max_newton, double lin_rtol,
                        int lin_max_iter, int reuse, int* newton_iters, int* linear_iters, int* setups,
                        double* rel_resid, void* stream) {
+  NvtxRange nvtx("tam: thermal Newton");
   try {
     set_last_error("");
     TAM_CHECK(th && T && rtol >= 0.0 && max_newton >= 0 && lin_rtol > 0.0 && lin_max_iter > 0,

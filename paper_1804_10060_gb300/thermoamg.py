@@ -73,6 +73,7 @@ _SIGNATURES = {
     "amg_level_aggregates": ([_vp, _i, _vp, _vp], _i),
     "amg_level_export": ([_vp, _i, _i, _pi, _pi, _pi, _pi, _pll, _vp, _vp, _vp, _vp], _i),
     "amg_level_spmv_plan": ([_vp, _i, _i, _pi, _pi, _pi], _i),
+    "amg_residual_history": ([_vp, _vp, _i, _pi, _vp], _i),
     "amg_smooth": ([_vp, _vp, _vp, _i, _vp], _i),
     "amg_solve_bytes": ([_vp, _pd, _pd], _i),
     "amg_vcycle": ([_vp, _vp, _vp, _vp], _i),
@@ -311,6 +312,15 @@ def amg_level_export(amg: Amg, level: int, which: int, stream=None) -> dict:
                                 _vp(v.data_ptr()), _stream(stream)))
     return {"n_rows": nr.value, "n_cols": nc.value, "br": br.value, "bc": bc.value, "nnzb": nnzb.value,
             "row_ptr": rp, "col_idx": ci[:nnzb.value], "vals": v[:nnzb.value]}
+
+
+def amg_residual_history(amg: Amg, stream=None) -> np.ndarray:
+    """||r_k||_2, k = 0 .. iterations, of the hierarchy's last single-system solve."""
+    n = ctypes.c_int()
+    _check(lib.amg_residual_history(amg.handle, None, 0, ctypes.byref(n), _stream(stream)))
+    h = np.empty(max(n.value, 1), np.float64)
+    _check(lib.amg_residual_history(amg.handle, _vp(h.ctypes.data), n.value, None, _stream(stream)))
+    return h[:n.value]
 
 
 def amg_level_spmv_plan(amg: Amg, level: int, which: int) -> dict:

@@ -161,3 +161,45 @@ def test_underestimated_lambda_does_not_hang():
     x = torch.zeros_like(rhs)
     it, rel, st = tam.amg_pcg_solve(H, rhs, x, rtol=1e-8, max_iter=200, raise_on_error=False)
     assert st in (0, -5, -6, -7)
+
+
+def test_residual_history_matches_oracle_pcg():
+    """amg_residual_history: ||r_k||, k = 0 .. iterations, of the last solve, in
+    the caller's units (the solve runs on scaled copies).  Compared with CG on
+    the oracle's own hierarchy of the same matrix (its V-cycle agrees with the
+    GPU's to 1e-9), recording the same recursively updated residual."""
+    pb = meshgen.unit_cube_problem(8)
+    tam, d, K, rhs, H = _setup(pb, coarse_max_dofs=60)
+    assert tam.amg_residual_history(H).size == 0          # before any solve
+    b = 1e-7 * rhs                                        # units far from 1: the history is scaled back
+    x = torch.zeros_like(b)
+    it, rel, st = tam.amg_pcg_solve(H, b, x, rtol=1e-8, max_iter=200)
+    assert st == 0
+    hist = tam.amg_residual_history(H)
+    assert hist.size == it + 1
+    Ko, _ = fem.assemble_system(pb)
+    Ho = oamg.setup(Ko, fem.rigid_body_modes(pb.coords, pb.dirichlet_mask), 3, coarse_max_dofs=60)
+    bo = b.cpu().numpy().ravel()
+    xo = np.zeros_like(bo)
+    r = bo.copy()
+    z = oamg.vcycle(Ho, r)
+    p = z.copy()
+    rz = r @ z
+    ref = [np.linalg.norm(r)]
+    for _ in range(it):
+        q = Ko @ p
+        a = rz / (p @ q)
+        xo += a * p
+        r -= a * q
+        ref.append(np.linalg.norm(r))
+        z = oamg.vcycle(Ho, r)
+        rz, rz_old = r @ z, rz
+        p = z + (rz / rz_old) * p
+    ref = np.array(ref)
+    assert abs(hist[0] - np.linalg.norm(bo)) <= 1e-12 * np.linalg.norm(bo)
+    assert np.all(np.abs(hist - ref) <= 1e-6 * ref), np.max(np.abs(hist - ref) / ref)
+    assert hist[-1] <= 1e-8 * hist[0] < hist[-2]
+    # a longer cap than the first solve's reallocates the record and still works
+    x.zero_()
+    it2, _, st2 = tam.amg_pcg_solve(H, b, x, rtol=1e-10, max_iter=5000)
+    assert st2 == 0 and tam.amg_residual_history(H).size == it2 + 1

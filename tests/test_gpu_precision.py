@@ -136,3 +136,16 @@ def test_double_float_spmv_matches_fp64_spmv():
     u = linsolve.direct_solve(Ko, fo)
     for x in (xdf, x64):
         assert np.linalg.norm(x.cpu().numpy().ravel() - u) <= 1e-6 * np.linalg.norm(u)
+
+
+def test_bf16_request_on_p2_keeps_fp32():
+    """BF16 finest-level values double the iterations on P2 matrices (their
+    8-bit mantissa weakens the fine smoother), so level_precision 2 on a P2 K
+    builds the FP32 hierarchy: the same V-cycle, bit for bit, as level 1."""
+    pb = meshgen.unit_cube_problem(5, 2)
+    tam = need_gpu()
+    d = tam.problem_to_device(pb)
+    K, rhs = tam.fem_assemble_elasticity(**d)
+    z = [tam.amg_vcycle(tam.amg_setup(K, d["coords"], tam.amg_params_default(level_precision=p)), rhs.reshape(-1))
+         for p in (1, 2)]
+    assert torch.equal(z[0], z[1])
