@@ -103,6 +103,18 @@ int fem_assemble_elasticity(int n_nodes, const double* coords, int n_cells, int 
                             const double* u_dirichlet, tam_matrix* K_out, double* rhs_out,
                             void* stream);
 
+/* Assembly mode for fem_assemble_elasticity / fem_assemble_load (process-wide,
+ * default 0).  0: element blocks and loads are scattered with FP64 atomics
+ * (fastest; the summation order, hence the last bits of K and f, may differ
+ * between runs).  1: deterministic -- every element block and load is stored
+ * in its own slot (n_cells * npc^2 * 9 + n_cells * npc * 3 doubles of
+ * temporary device memory) and each node's warp sums its cells' slots in
+ * increasing cell id, so two runs give bitwise equal K and f (the element
+ * contributions are the same; only the order of the sums is fixed).  Nodes in
+ * more than 1024 cells return UNSUPPORTED in mode 1.  *previous (may be NULL)
+ * receives the old mode.  Not tied to a stream; set it between calls. */
+int tam_set_deterministic_assembly(int on, int* previous);
+
 /* Load vector of another load case on the mesh of an existing K (same
  * coords/cells/materials/Dirichlet mask as K was assembled with): thermal and
  * body loads of Eq. wf_elastic plus the lifting of u_dirichlet, Dirichlet

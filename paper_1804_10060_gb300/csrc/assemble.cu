@@ -15,6 +15,8 @@
 // nodes become identity rows -- the symmetric elimination of Eq. u-dbc.
 #include <cstdlib>
 
+#include <atomic>
+
 #include "handles.cuh"
 #include "tet.cuh"
 
@@ -245,6 +247,12 @@ struct AsmArgs {
   int n_cells;
   int* bad_cell;
   int loads_only;  // 1: only the load vector (K of this mesh exists already)
+  // deterministic mode (non-null): every element block and load goes to its
+  // own slot, ck[((c npc + a) npc + b) 9 + e] and cf[(c npc + a) 3 + d], and
+  // gather_kernel sums them per node in cell order (no atomics)
+  double* ck = nullptr;
+  double* cf = nullptr;
+  int npc = 0;
 };
 
 // Does the element block (row na, column nb) contribute anything?  In
@@ -253,8 +261,16 @@ __device__ __forceinline__ bool block_needed(const AsmArgs& A, int nb) {
   return !A.loads_only || (A.dmask[nb] && A.ud);
 }
 
-// Scatter one 3x3 block (row node na, col node nb) or lift it into the load.
-__device__ __forceinline__ void scatter_block(const AsmArgs& A, int na, int nb, const double k[9]) {
+// Scatter one 3x3 block (row node na, col node nb; local a, b of cell c) or
+// lift it into the load; in deterministic mode store it in its slot.
+__device__ __forceinline__ void scatter_block(const AsmArgs& A, int c, int a, int b, int na, int nb,
+                                              const double k[9]) {
+  if (A.ck) {
+    double* dst = A.ck + (((size_t)c * A.npc + a) * A.npc + b) * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) dst[e] = k[e];
+    return;
+  }
   if (A.dmask[nb]) {
     if (A.ud) {
       const double* u = A.ud + 3 * (size_t)nb;
@@ -316,10 +332,10 @@ __global__ void __launch_bounds__(128) assemble_p1_kernel(AsmArgs A) {
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) k[3 * i + j] = fma(lg[a][i], g[b][j], mg[a][j] * g[b][i]) + (i == j ? mgg : 0.0);
-      if (ab) scatter_block(A, v[a], v[b], k);
+      if (ab) scatter_block(A, c, a, b, v[a], v[b], k);
       if (ba) {
         const double kt[9] = {k[0], k[3], k[6], k[1], k[4], k[7], k[2], k[5], k[8]};
-        scatter_block(A, v[b], v[a], kt);
+        scatter_block(A, c, b, a, v[b], v[a], kt);
       }
     }
   }
@@ -330,7 +346,8 @@ __global__ void __launch_bounds__(128) assemble_p1_kernel(AsmArgs A) {
     for (int i = 0; i < 3; ++i) {
       double f = cT * g[a][i];
       if (A.body) f += vol / 20.0 * (fsum[i] + A.body[3 * (size_t)na + i]);
-      atomicAdd(&A.rhs[3 * (size_t)na + i], f);
+      if (A.cf) A.cf[((size_t)c * 4 + a) * 3 + i] = f;
+      else atomicAdd(&A.rhs[3 * (size_t)na + i], f);
     }
   }
 }
@@ -465,10 +482,10 @@ __global__ void __launch_bounds__(P2_WARPS * 32) assemble_p2_kernel(AsmArgs A) {
         for (int jj = 0; jj < 3; ++jj)
           k[3 * ii + jj] += fma(lga[ii], gbv[jj], mga[jj] * gbv[ii]) + (ii == jj ? mgg : 0.0);
     }
-    if (ab) scatter_block(A, na, nb, k);
+    if (ab) scatter_block(A, c, a, b, na, nb, k);
     if (ba) {
       const double kt[9] = {k[0], k[3], k[6], k[1], k[4], k[7], k[2], k[5], k[8]};
-      scatter_block(A, nb, na, kt);
+      scatter_block(A, c, b, a, nb, na, kt);
     }
   }
   // loads, Keast 11-point rule: lane 3a + d sums component d of node a over the points
@@ -485,9 +502,77 @@ __global__ void __launch_bounds__(P2_WARPS * 32) assemble_p2_kernel(AsmArgs A) {
         if (A.T) f += wq * kT * sq[wid][q][0] * gr[d];
         if (A.body) f += wq * p2_phi(a, l) * sq[wid][q][1 + d];
       }
-      atomicAdd(&A.rhs[3 * (size_t)na + d], f);
+      if (A.cf) A.cf[((size_t)c * 10 + a) * 3 + d] = f;
+      else atomicAdd(&A.rhs[3 * (size_t)na + d], f);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic assembly: the element kernels store every block and load in
+// its own slot; per node, a warp sums its cells' slots in increasing cell id
+// order into the node's row of K and its load (Dirichlet columns lifted) --
+// the same sums as the atomic scatter, in an order fixed by the mesh, so two
+// runs give bitwise equal K and f.
+// ---------------------------------------------------------------------------
+constexpr int DET_WARPS = 4;
+constexpr int DET_CAP = 1024;  // cells per node the sorting pass handles
+
+// each node's incident cells in increasing id (warp per node, shared-memory
+// bitonic sort); a node in more than DET_CAP cells sets *bad
+__global__ void __launch_bounds__(DET_WARPS * 32)
+incidence_sort_kernel(int n_nodes, const int* __restrict__ ptr, int* __restrict__ inc, int* __restrict__ bad) {
+  __shared__ int tab[DET_WARPS][DET_CAP];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v = blockIdx.x * DET_WARPS + wid;
+  if (v >= n_nodes) return;  // warp-uniform
+  const int p0 = ptr[v], len = ptr[v + 1] - p0;
+  if (len > DET_CAP) {
+    if (lane == 0) atomicExch(bad, 1);
+    return;
+  }
+  int* t = tab[wid];
+  const int n2 = next_pow2(len);
+  for (int i = lane; i < n2; i += 32) t[i] = i < len ? inc[p0 + i] : 0x7fffffff;
+  __syncwarp();
+  warp_bitonic_sort<false>(t, nullptr, n2);
+  for (int i = lane; i < len; i += 32) inc[p0 + i] = t[i];
+}
+
+__global__ void __launch_bounds__(DET_WARPS * 32)
+gather_kernel(int n_nodes, int npc, const int* __restrict__ cells, const int* __restrict__ ptr,
+              const int* __restrict__ inc, const unsigned char* __restrict__ dmask, const double* __restrict__ ud,
+              const int* __restrict__ rp, const int* __restrict__ ci, double* __restrict__ vals,
+              double* __restrict__ rhs, const double* __restrict__ ck, const double* __restrict__ cf, int has_loads) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * DET_WARPS + wid;
+  if (i >= n_nodes || dmask[i]) return;  // warp-uniform; Dirichlet rows: dirichlet_rows_kernel
+  double f = 0.0;  // lane d < 3: component d of the node's load
+  for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int c = inc[p];
+    const int* cn = cells + (size_t)c * npc;
+    const unsigned m = __ballot_sync(0xffffffffu, lane < npc && cn[lane] == i);
+    const int a = __ffs(m) - 1;  // the node's local index in cell c
+    const double* kc = ck + ((size_t)c * npc + a) * npc * 9;
+    if (has_loads && lane < 3) f += cf[((size_t)c * npc + a) * 3 + lane];
+    if (vals)
+      for (int it = lane; it < npc * 9; it += 32) {
+        const int b = it / 9, e = it - b * 9, j = cn[b];
+        if (dmask[j]) continue;
+        const int slot = bsearch_i32(ci, rp[i], rp[i + 1], j);
+        vals[(size_t)slot * 9 + e] += kc[it];
+      }
+    if (ud && lane < 3)
+      for (int b = 0; b < npc; ++b) {
+        const int j = cn[b];
+        if (!dmask[j]) continue;
+        const double* kb = kc + b * 9;
+        const double* u = ud + 3 * (size_t)j;
+        f -= kb[3 * lane] * u[0] + kb[3 * lane + 1] * u[1] + kb[3 * lane + 2] * u[2];
+      }
+    __syncwarp();
+  }
+  if (lane < 3) rhs[3 * (size_t)i + lane] = f;
 }
 
 // Dirichlet (and cell-less) rows: identity diagonal block, load = u_D.
@@ -602,6 +687,25 @@ void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, con
   }
 }
 
+std::atomic<int> g_deterministic_assembly{0};
+
+// Deterministic assembly's second pass: sort the incidence lists, sum the
+// slots per node (vals may be null: loads only).
+static void gather_assembly(const AsmArgs& args, int n_nodes, int npc, const int* cells, const int* inc_ptr,
+                            int* inc, const unsigned char* dmask, double* vals, double* rhs, bool has_loads,
+                            cudaStream_t s) {
+  DBuf<int> bad(1, s);
+  bad.zero();
+  incidence_sort_kernel<<<grid_for(n_nodes, DET_WARPS), DET_WARPS * 32, 0, s>>>(n_nodes, inc_ptr, inc, bad.p);
+  TAM_LAUNCH_CHECK();
+  TAM_CHECK(read_back_int(bad.p, s) == 0, TAM_ERR_UNSUPPORTED,
+            "fem_assemble: deterministic assembly handles nodes in at most 1024 cells");
+  gather_kernel<<<grid_for(n_nodes, DET_WARPS), DET_WARPS * 32, 0, s>>>(
+      n_nodes, npc, cells, inc_ptr, inc, dmask, args.ud, args.row_ptr, args.col_idx, vals, rhs, args.ck, args.cf,
+      has_loads ? 1 : 0);
+  TAM_LAUNCH_CHECK();
+}
+
 tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells, int npc, const int* cells,
                                   const int* mat, int n_mat, const double* props, const double* T,
                                   double T_ref, const double* body, const unsigned char* dmask,
@@ -637,6 +741,15 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
     TAM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * (size_t)n_nodes, s));
     AsmArgs args{coords, cells, mat, props, T, T_ref, body, dmask, ud, A.row_ptr.p, A.col_idx.p,
                  A.vals.p, rhs, n_cells, flag.p, 0};
+    const bool det = g_deterministic_assembly.load() != 0 && n_cells > 0;
+    DBuf<double> ck, cf;
+    if (det) {
+      ck = DBuf<double>((size_t)n_cells * npc * npc * 9, s);
+      cf = DBuf<double>((size_t)n_cells * npc * 3, s);
+      args.ck = ck.p;
+      args.cf = cf.p;
+      args.npc = npc;
+    }
     if (n_cells > 0) {
       if (npc == 4)
         assemble_p1_kernel<<<grid_for(n_cells, 128), 128, 0, s>>>(args);
@@ -644,6 +757,7 @@ tam_matrix_s* assemble_elasticity(int n_nodes, const double* coords, int n_cells
         assemble_p2_kernel<<<grid_for(n_cells, P2_WARPS), P2_WARPS * 32, 0, s>>>(args);
       TAM_LAUNCH_CHECK();
     }
+    if (det) gather_assembly(args, n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.vals.p, rhs, T || body, s);
     dirichlet_rows_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, dmask, inc_ptr.p, ud, A.row_ptr.p,
                                                                  A.col_idx.p, A.vals.p, rhs);
     TAM_LAUNCH_CHECK();
@@ -692,6 +806,27 @@ void assemble_loads(tam_matrix_s* K, const double* coords, int n_cells, int npc,
   TAM_CUDA(cudaMemsetAsync(rhs, 0, sizeof(double) * 3 * (size_t)n_nodes, s));
   AsmArgs args{coords, cells, mat, props, T, T_ref, body, K->dmask.p, ud, K->A.row_ptr.p, K->A.col_idx.p,
                nullptr, rhs, n_cells, flag.p + 1, 1};
+  const bool det = g_deterministic_assembly.load() != 0 && n_cells > 0;
+  DBuf<double> ck, cf;
+  DBuf<int> inc_ptr, inc;
+  if (det) {
+    ck = DBuf<double>((size_t)n_cells * npc * npc * 9, s);
+    cf = DBuf<double>((size_t)n_cells * npc * 3, s);
+    args.ck = ck.p;
+    args.cf = cf.p;
+    args.npc = npc;
+    inc_ptr = DBuf<int>((size_t)n_nodes + 1, s);
+    inc = DBuf<int>((size_t)n_entries, s);
+    DBuf<int> cursor((size_t)n_nodes, s);
+    inc_ptr.zero();
+    cursor.zero();
+    incidence_count_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, inc_ptr.p);
+    TAM_LAUNCH_CHECK();
+    exclusive_scan_i32(inc_ptr.p, inc_ptr.p, n_nodes, s);
+    incidence_fill_kernel<<<grid_for(n_entries, 256), 256, 0, s>>>(cells, n_entries, npc, inc_ptr.p, cursor.p,
+                                                                   inc.p);
+    TAM_LAUNCH_CHECK();
+  }
   if (n_cells > 0) {
     if (npc == 4)
       assemble_p1_kernel<<<grid_for(n_cells, 128), 128, 0, s>>>(args);
@@ -699,6 +834,7 @@ void assemble_loads(tam_matrix_s* K, const double* coords, int n_cells, int npc,
       assemble_p2_kernel<<<grid_for(n_cells, P2_WARPS), P2_WARPS * 32, 0, s>>>(args);
     TAM_LAUNCH_CHECK();
   }
+  if (det) gather_assembly(args, n_nodes, npc, cells, inc_ptr.p, inc.p, K->dmask.p, nullptr, rhs, T || body, s);
   dirichlet_rows_kernel<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, K->dmask.p, nullptr, ud, nullptr, nullptr,
                                                                nullptr, rhs);
   TAM_LAUNCH_CHECK();

@@ -72,6 +72,14 @@ int fem_assemble_elasticity(int n_nodes, const double* coords, int n_cells, int 
   });
 }
 
+int tam_set_deterministic_assembly(int on, int* previous) {
+  return guarded([&] {
+    const int old = g_deterministic_assembly.exchange(on ? 1 : 0);
+    if (previous) *previous = old;
+    return TAM_OK;
+  });
+}
+
 int fem_assemble_load(tam_matrix K, const double* coords, int n_cells, int nodes_per_cell, const int* cells,
                       const int* cell_material, int n_mat, const double* mat_props, const double* T, double T_ref,
                       const double* body_force, const double* u_dirichlet, double* rhs_out, void* stream) {

@@ -2,6 +2,7 @@
 // the C ABI wraps.
 #pragma once
 
+#include <atomic>
 #include <functional>
 #include <memory>
 #include <vector>
@@ -142,6 +143,10 @@ struct tam_amg_s {
 namespace tam {
 
 // Mesh topology shared by the elastic and the thermal assembly (assemble.cu).
+// Process-wide assembly mode: nonzero sums element contributions per node in
+// cell order (bitwise reproducible) instead of scattering them with atomics.
+extern std::atomic<int> g_deterministic_assembly;
+
 void validate_mesh(int n_nodes, int n_cells, int npc, const int* cells, const int* mat, int n_mat, const char* who,
                    cudaStream_t s);
 void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, const unsigned char* dmask, Bsr& A,

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "amg_level_export": ([_vp, _i, _i, _pi, _pi, _pi, _pi, _pll, _vp, _vp, _vp, _vp], _i),
     "amg_level_spmv_plan": ([_vp, _i, _i, _pi, _pi, _pi], _i),
     "amg_residual_history": ([_vp, _vp, _i, _pi, _vp], _i),
+    "tam_set_deterministic_assembly": ([_i, _pi], _i),
     "amg_smooth": ([_vp, _vp, _vp, _i, _vp], _i),
     "amg_solve_bytes": ([_vp, _pd, _pd], _i),
     "amg_vcycle": ([_vp, _vp, _vp, _vp], _i),
@@ -312,6 +313,13 @@ def amg_level_export(amg: Amg, level: int, which: int, stream=None) -> dict:
                                 _vp(v.data_ptr()), _stream(stream)))
     return {"n_rows": nr.value, "n_cols": nc.value, "br": br.value, "bc": bc.value, "nnzb": nnzb.value,
             "row_ptr": rp, "col_idx": ci[:nnzb.value], "vals": v[:nnzb.value]}
+
+
+def set_deterministic_assembly(on: bool) -> bool:
+    """Process-wide assembly mode (True: bitwise reproducible sums); returns the previous mode."""
+    prev = ctypes.c_int()
+    _check(lib.tam_set_deterministic_assembly(int(bool(on)), ctypes.byref(prev)))
+    return bool(prev.value)
 
 
 def amg_residual_history(amg: Amg, stream=None) -> np.ndarray:

@@ -154,3 +154,39 @@ def test_residual_norm_entry_point():
     got = tam.tam_matrix_residual_norm(K, rhs, x)
     ref = np.linalg.norm(rhs.cpu().numpy().ravel() - Kg @ x.cpu().numpy().ravel())
     assert abs(got - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+def test_deterministic_assembly_is_bitwise_reproducible(degree):
+    """tam_set_deterministic_assembly(1): per-node sums of the element slots in
+    cell order -- two runs bitwise equal (K and f, loads-only path included),
+    the same operator as the atomic scatter to rounding and the oracle's to 1e-12;
+    prescribed displacements exercise the lifting."""
+    tam = need_gpu()
+    pb = meshgen.slab_box_problem(12, 4, 4) if degree == 1 else meshgen.unit_cube_problem(4, 2)
+    rng = np.random.default_rng(9)
+    pb.u_dirichlet = 1e-3 * rng.standard_normal((pb.n_nodes, 3)) * pb.dirichlet_mask[:, None]
+    d = tam.problem_to_device(pb)
+    prev = tam.set_deterministic_assembly(True)
+    try:
+        runs = []
+        for _ in range(2):
+            K, rhs = tam.fem_assemble_elasticity(**d)
+            rp, ci, v = tam.tam_matrix_export_bsr(K)
+            b2 = tam.fem_assemble_load(K, **d)
+            runs.append((rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy(), rhs.cpu().numpy(), b2.cpu().numpy()))
+    finally:
+        tam.set_deterministic_assembly(prev)
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b)
+    K0, rhs0 = tam.fem_assemble_elasticity(**d)
+    rp0, ci0, v0 = tam.tam_matrix_export_bsr(K0)
+    assert np.array_equal(rp0.cpu().numpy(), runs[0][0]) and np.array_equal(ci0.cpu().numpy(), runs[0][1])
+    scale = np.abs(runs[0][2]).max()
+    assert np.abs(v0.cpu().numpy() - runs[0][2]).max() <= 1e-13 * scale
+    fs = np.abs(runs[0][3]).max()
+    assert np.abs(rhs0.cpu().numpy() - runs[0][3]).max() <= 1e-13 * fs
+    assert np.abs(runs[0][4] - runs[0][3]).max() <= 1e-13 * fs
+    Ko, fo = fem.assemble_system(pb)
+    assert sparse_rel(bsr_to_csr(*[torch.from_numpy(x) for x in runs[0][:3]], pb.n_nodes), Ko) <= 1e-12
+    assert np.abs(runs[0][3].ravel() - fo).max() <= 1e-12 * np.abs(fo).max()
