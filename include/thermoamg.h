@@ -315,7 +315,10 @@ int amg_vcycle(tam_amg amg, const double* r, double* z, void* stream);
  * device-side loop over one captured iteration, ended by the stopping test),
  * so the host waits once per solve.  Synchronising.
  * Errors: NOT_CONVERGED (x holds the last iterate), BREAKDOWN,
- * INDEFINITE_PRECOND, NAN, INVALID_ARG, CUDA. */
+ * INDEFINITE_PRECOND, NAN, INVALID_ARG, CUDA.  (With TAM_PCG_HOST_LOOP=1 in
+ * the environment the same iterations run as plain launches from a host loop
+ * that reads the stop flag after each one: for profilers that do not trace
+ * kernels inside conditional graph nodes.) */
 int amg_pcg_solve(tam_amg amg, const double* b, double* x, double rtol, double atol, int max_iter,
                   int* iters_out, double* final_rel_resid_out, void* stream);
 

@@ -15,6 +15,7 @@
 // breakdown, NaN, iteration cap) return at entry, so a fixed-length CUDA
 // graph of one iteration can be replayed without host round trips.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <functional>
 #include <type_traits>
@@ -518,10 +519,24 @@ int pcg_solve(tam_amg_s* H, const double* b, double* x, double rtol, double atol
   TAM_LAUNCH_CHECK();
   // the iterations as one graph: a device-side WHILE loop over one iteration,
   // built on the first solve with this hierarchy, one launch per solve
-  if (!H->iter_exec)
-    H->iter_exec = build_loop_graph([&](cudaStream_t cs) { enqueue_iteration(H, x, cs); }, &sc->stop, &sc->loops,
-                                    &sc->max_iter, 2, &H->graph_kernels);
-  TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
+  // (TAM_PCG_HOST_LOOP=1 in the environment: the same iterations as plain
+  // launches from a host loop that reads the stop flag after each -- for
+  // profilers that do not trace kernels inside conditional graph nodes)
+  static const bool host_loop = [] {
+    const char* e = std::getenv("TAM_PCG_HOST_LOOP");
+    return e && std::atoi(e) != 0;
+  }();
+  if (host_loop) {
+    for (int k = 0; k < max_iter + 2; ++k) {
+      enqueue_iteration(H, x, s);
+      if (read_back_int(&sc->stop, s)) break;
+    }
+  } else {
+    if (!H->iter_exec)
+      H->iter_exec = build_loop_graph([&](cudaStream_t cs) { enqueue_iteration(H, x, cs); }, &sc->stop,
+                                      &sc->loops, &sc->max_iter, 2, &H->graph_kernels);
+    TAM_CUDA(cudaGraphLaunch(H->iter_exec, s));
+  }
   // final true residual, always a plain FP64 product; then x back to the caller's scale
   DBuf<double> rn(1, s);
   by_block(H->K->A.br, [&](auto B) {
