@@ -616,6 +616,15 @@ void validate_mesh(int n_nodes, int n_cells, int npc, const int* cells, const in
 // incidence (inc_ptr[n_nodes + 1], inc) that the pattern came from.  flag[1]
 // is set when a node has too many incident cells for the shared-memory
 // builder.  Synchronising.
+// 64-bit sum of per-row counts (overflow check before an int32 scan)
+__global__ void count_sum_kernel(const int* __restrict__ cnt, int n, unsigned long long* __restrict__ out) {
+  unsigned long long v = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v += (unsigned long long)(unsigned)cnt[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
 void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, const unsigned char* dmask, Bsr& A,
                         DBuf<int>& inc_ptr, DBuf<int>& inc, int* flag, cudaStream_t s) {
   const long long n_entries = (long long)n_cells * npc;
@@ -676,6 +685,15 @@ void build_node_pattern(int n_nodes, int n_cells, int npc, const int* cells, con
     pattern_kernel<false><<<pg, PAT_WARPS * 32, 0, s>>>(n_nodes, npc, cells, inc_ptr.p, inc.p, dmask, A.row_ptr.p,
                                                        nullptr, nullptr, flag + 1);
     TAM_LAUNCH_CHECK();
+    {
+      // block counts are int32 (K's arrays): refuse a pattern of 2^31 blocks or more
+      DBuf<unsigned long long> tot(1, s);
+      tot.zero();
+      count_sum_kernel<<<stride_grid(n_nodes, 256, 8), 256, 0, s>>>(A.row_ptr.p, n_nodes, tot.p);
+      TAM_LAUNCH_CHECK();
+      TAM_CHECK(read_back_ll(reinterpret_cast<const long long*>(tot.p), s) < (1LL << 31), TAM_ERR_UNSUPPORTED,
+                "fem_assemble: K would have 2^31 or more 3x3 blocks (int32 indices)");
+    }
     exclusive_scan_i32(A.row_ptr.p, A.row_ptr.p, n_nodes, s);
     A.nnzb = read_back_int(A.row_ptr.p + n_nodes, s);
     TAM_CHECK(read_back_int(flag + 1, s) == 0, TAM_ERR_UNSUPPORTED,
