@@ -66,6 +66,8 @@ def parse():
                     help="assemble K and launch only the level-0 SpMV this many times (profiling target)")
     ap.add_argument("--smooth-only", type=int, default=0, metavar="STEPS",
                     help="assemble K, build the AMG and run only this many level-0 Chebyshev steps (profiling target)")
+    ap.add_argument("--mlp-only", type=int, default=0, metavar="ROWS",
+                    help="time only the one-kernel BF16 network inference on ROWS rows (profiling target)")
     ap.add_argument("--fma", action="store_true", help="print the device's measured FP64/FP32 FMA throughput and exit")
     ap.add_argument("--summarize-ncu", default=None, metavar="CSV",
                     help="print a per-kernel summary (launches, time, share) of an ncu --csv launch list and exit")
@@ -904,6 +906,30 @@ def smooth_only(args):
     print(json.dumps({"smooth_only": args.smooth_only, "n": n, "nnzb": nnzb, "dims": dims}))
 
 
+def mlp_only(args):
+    """The learned guess's network (8->128->128->128->3, seed 7) on N rows of seeded features:
+    3 warm-up and 5 timed one-kernel BF16 inferences (profiling target)."""
+    import numpy as np
+    import torch
+
+    from paper_1804_10060_gb300 import thermoamg as tam
+    n = args.mlp_only
+    net = tam.Mlp(8, 128, 3, 3, seed=7)
+    net.set_normalization(np.zeros(8, np.float32), np.ones(8, np.float32), np.ones(3, np.float32))
+    X = torch.from_numpy(np.random.default_rng(0).standard_normal((n, 8)).astype(np.float32)).cuda()
+    for _ in range(3):
+        net.forward(X, bf16=1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        net.forward(X, bf16=1)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mlp_only": n, "fused_bf16_ms": a.elapsed_time(b) / 5}))
+    net.destroy()
+
+
 def one_step(args):
     """Exactly one assemble + setup + solve of the workload (launch-list profiling target)."""
     import torch
@@ -929,6 +955,9 @@ def main():
         return
     if args.spmv_only:
         spmv_only(args)
+        return
+    if args.mlp_only:
+        mlp_only(args)
         return
     if args.smooth_only:
         smooth_only(args)
