@@ -121,6 +121,26 @@ __device__ __forceinline__ void df_add(float2& a, float2 b) {
 
 __device__ __forceinline__ double df_to_double(float2 a) { return f2d_bits(a.x) + f2d_bits(a.y); }
 
+// a += b for two double-float values, the accurate form: TwoSum of the high
+// parts and of the low parts, the errors folded in with two renormalisations
+// (Fast2Sum), relative error a few 2^-48 whatever the magnitudes' order --
+// the double-word addition with the tight bound of Joldes, Muller and
+// Popescu (2017).  The accurate SpMV folds each slot's products in with it.
+__device__ __forceinline__ void df_add_accurate(float2& a, float2 b) {
+  float sh = __fadd_rn(a.x, b.x);
+  float t = __fadd_rn(sh, -a.x);
+  float sl = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(sh, -t)), __fadd_rn(b.x, -t));
+  const float th = __fadd_rn(a.y, b.y);
+  t = __fadd_rn(th, -a.y);
+  const float tl = __fadd_rn(__fadd_rn(a.y, -__fadd_rn(th, -t)), __fadd_rn(b.y, -t));
+  sl = __fadd_rn(sl, th);
+  float h = __fadd_rn(sh, sl);
+  sl = __fadd_rn(sl, -__fadd_rn(h, -sh));
+  sl = __fadd_rn(sl, tl);
+  a.x = __fadd_rn(h, sl);
+  a.y = __fadd_rn(sl, -__fadd_rn(a.x, -h));
+}
+
 // Largest |binary exponent| of a matrix's largest entry for which the
 // double-float products are used (amg_params.spmv_fp64 / setup_fp64 fall back
 // to FP64 outside it).
@@ -241,9 +261,9 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
     const int* __restrict__ cp = A.cols + (size_t)k0 * 32 + lane;
     if constexpr (DF) {
       const float2* __restrict__ vp = A.vals_df + (size_t)k0 * 32 * BR * BC + lane;
-      float2 ad[BR];
+      float2 ad[BR], run[BR];
 #pragma unroll
-      for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
+      for (int r = 0; r < BR; ++r) ad[r] = run[r] = make_float2(0.f, 0.f);
 #pragma unroll 2
       for (int k = k0; k < k1; ++k) {
         float2 vv[BR * BC];  // the slot's values first, then the gather
@@ -261,24 +281,28 @@ sell_spmv_kernel(SellView A, const double* __restrict__ x, Epi epi) {
             else df_fma(ad[r], vv[r * BC + j], xv[j]);
           }
         if constexpr (ACC) {
-          // ACC: the double-float sum restarts every 2 slots and is added
-          // into an FP64 sum, so that the low part never carries more than 2
-          // slots' rounding: a few 2^-48 of sum_j |A_ij x_j| per row whatever
-          // the row's length (the running double-float sum drifts to ~2^-45 on
-          // long P2 rows), for 1.5 FP64 adds per row and slot pair
-          if ((k - k0) & 1) {  // uniform over the warp (one slice)
+          // ACC: each slot's double-float partial sum (its BC products) is
+          // added into the row's running sum with the accurate double-word
+          // addition, so that the low part never carries more than one
+          // slot's rounding: a few 2^-48 of sum_j |A_ij x_j| per row whatever
+          // the row's length (the plain running double-float sum drifts to
+          // ~2^-45 on long P2 rows); FP32 work only (an FP64 sum every two
+          // slots cost 1.5 FP64 adds per row and slot pair on GB300's slow
+          // FP64 pipe)
 #pragma unroll
-            for (int r = 0; r < BR; ++r) {
-              acc[r] += df_to_double(ad[r]);
-              ad[r] = make_float2(0.f, 0.f);
-            }
+          for (int r = 0; r < BR; ++r) {
+            df_add_accurate(run[r], ad[r]);
+            ad[r] = make_float2(0.f, 0.f);
           }
         }
         cp += 32;
         vp += 32 * BR * BC;
       }
 #pragma unroll
-      for (int r = 0; r < BR; ++r) acc[r] += df_to_double(ad[r]);
+      for (int r = 0; r < BR; ++r) {
+        if constexpr (ACC) acc[r] = df_to_double(run[r]);
+        else acc[r] += df_to_double(ad[r]);
+      }
     } else {
       const double* __restrict__ vp = A.vals + (size_t)k0 * 32 * BR * BC + lane;
 #pragma unroll 2
