@@ -478,12 +478,12 @@ lpr_spmv_kernel(LprView A, const double* __restrict__ x, Epi epi) {
   double acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = 0.0;
+  [[maybe_unused]] float2 ad[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
   if (row < A.n_rows) {
     const int g0 = A.gp[row], g1 = A.gp[row + 1];
     if constexpr (DF) {
-      float2 ad[BR];
-#pragma unroll
-      for (int r = 0; r < BR; ++r) ad[r] = make_float2(0.f, 0.f);
       // the x gather runs one group ahead: the next group's column and x
       // entries are requested before this group's products, so that they
       // arrive together with the next group's values (one memory round trip
@@ -512,8 +512,6 @@ lpr_spmv_kernel(LprView A, const double* __restrict__ x, Epi epi) {
 #pragma unroll
           for (int j = 0; j < BC; ++j) df_fma(ad[r], vv[r * BC + j], xv[j]);
       }
-#pragma unroll
-      for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
     } else {
       for (int g = g0; g < g1; ++g) {
         const double* __restrict__ vb = A.v + (size_t)g * BB * LPR + sub;
@@ -531,10 +529,22 @@ lpr_spmv_kernel(LprView A, const double* __restrict__ x, Epi epi) {
       }
     }
   }
+  if constexpr (DF) {
+    // the lanes' partial sums combined in double-float (FP32 work: an FP64
+    // butterfly costs every lane log2(LPR) FP64 adds per row component)
 #pragma unroll
-  for (int o = LPR / 2; o > 0; o >>= 1)
+    for (int o = LPR / 2; o > 0; o >>= 1)
 #pragma unroll
-    for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+      for (int r = 0; r < BR; ++r)
+        df_add(ad[r], make_float2(__shfl_xor_sync(0xffffffffu, ad[r].x, o), __shfl_xor_sync(0xffffffffu, ad[r].y, o)));
+#pragma unroll
+    for (int r = 0; r < BR; ++r) acc[r] = df_to_double(ad[r]);
+  } else {
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  }
   epi((sub == 0 && row < A.n_rows) ? row : A.n_rows, acc, sh);
 }
 
