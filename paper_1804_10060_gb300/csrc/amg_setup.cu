@@ -1134,12 +1134,20 @@ void amg_refresh_finest(tam_amg_s* H, cudaStream_t s) {
   point_dinv_kernel<<<grid_for(L.n_rows, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, A.vals.p, L.n_rows, L.bs,
                                                             L.dinv.p);
   TAM_LAUNCH_CHECK();
+  // the iteration graph reads the level's arrays through their pointers: it
+  // stays valid unless a layout is rebuilt in new memory (the lanes-per-row
+  // store); the SELL values (refreshed in place by the caller), D^-1 and the
+  // block-CSR split copy (same size, same buffer) keep theirs
+  bool moved = false;
   if (L.Aop.L) {
     build_lpr_store(A, L.Aop.L->lpr, L.Aop.df, L.AL, s);
+    moved = true;
   } else if (L.Aop.lpr != 0 && L.Aop.df) {
+    const float2* before = H->K->A.vals_df.p;
     build_df_values(H->K->A, s);
+    moved = H->K->A.vals_df.p != before;
   }
-  if (H->iter_exec) {
+  if (moved && H->iter_exec) {
     cudaGraphExecDestroy(H->iter_exec);
     H->iter_exec = nullptr;
   }

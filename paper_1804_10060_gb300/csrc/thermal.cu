@@ -132,18 +132,47 @@ double face_phi(int deg, int a, const double* m) {
 
 // ---------------------------------------------------------------------------
 // Constant tables (filled once per device by thermal_tables()):
-//   c_T3p2[a][b][c] = int phi_a phi_b phi_c / |K| (P2), c_M2p2 = int phi_a phi_b / |K|,
+//   d_T3p2[a][b][c] = int phi_a phi_b phi_c / |K| (P2), d_M2p2 = int phi_a phi_b / |K|,
 //   the same for P1, the face mass matrices int psi_a psi_b / |F|, and the P2
-//   conduction rule (27 points: barycentrics and weights / |K|).
+//   conduction rule (11 points: barycentrics and weights / |K|) with the P2
+//   basis values there.  The P2 tables the kernel indexes per lane live in
+//   global memory (read through L1): constant memory serialises a warp's
+//   accesses to different addresses.
 // ---------------------------------------------------------------------------
-constexpr int NQ2 = 27;
-__constant__ double c_T3p2[10][10][10];
-__constant__ double c_M2p2[10][10];
+constexpr int NQ2 = 11;
+__device__ double d_T3p2[10][10][10];
+__device__ double d_M2p2[10][10];
 __constant__ double c_T3p1[4][4][4];
 __constant__ double c_M2p1[4][4];
 __constant__ double c_F2p2[6][6];
 __constant__ double c_F2p1[3][3];
-__constant__ double c_q27[NQ2][5];  // l0..l3, weight (sum 1)
+__device__ double d_qc[NQ2][5];  // l0..l3, weight (sum 1)
+
+// Keast's 11-point rule on the tetrahedron: exact for every polynomial of
+// degree <= 4 (one negative weight); barycentrics and weights normalised to
+// sum 1.  Degree 4 is what the P2 conduction integrands reach (kappa(T_theta)
+// grad phi_i . grad phi_j: 2 + 1 + 1; k1 phi_j grad T_theta . grad phi_i: the same).
+void keast11(std::vector<double>& p, std::vector<double>& w) {
+  p.clear();
+  w.clear();
+  auto add = [&](const double (&l)[4], double wt) {
+    p.insert(p.end(), l, l + 4);
+    w.push_back(wt);
+  };
+  add({0.25, 0.25, 0.25, 0.25}, -6.0 * 74.0 / 5625.0);
+  for (int k = 0; k < 4; ++k) {
+    double l[4] = {1.0 / 14.0, 1.0 / 14.0, 1.0 / 14.0, 1.0 / 14.0};
+    l[k] = 11.0 / 14.0;
+    add(l, 6.0 * 343.0 / 45000.0);
+  }
+  const double a = (1.0 + std::sqrt(5.0 / 14.0)) / 4.0, b = (1.0 - std::sqrt(5.0 / 14.0)) / 4.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j) {
+      double l[4] = {b, b, b, b};
+      l[i] = l[j] = a;
+      add(l, 6.0 * 56.0 / 2250.0);
+    }
+}
 
 std::mutex g_tab_mutex;
 bool g_tab_ready[64] = {};
@@ -184,33 +213,33 @@ void thermal_tables() {
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) F1[a][b] += fw[q] * face_phi(1, a, m) * face_phi(1, b, m);
   }
-  tet_rule(3, p, w);  // degree 5 >= 4 (kappa(T_theta) grad phi . grad phi on P2)
-  double q27[NQ2][5];
+  keast11(p, w);  // degree 4 (kappa(T_theta) grad phi . grad phi on P2)
+  double qc[NQ2][5];
   for (int q = 0; q < NQ2; ++q) {
-    for (int k = 0; k < 4; ++k) q27[q][k] = p[4 * q + k];
-    q27[q][4] = w[q];
+    for (int k = 0; k < 4; ++k) qc[q][k] = p[4 * q + k];
+    qc[q][4] = w[q];
   }
-  TAM_CUDA(cudaMemcpyToSymbol(c_T3p2, T3, sizeof(T3)));
-  TAM_CUDA(cudaMemcpyToSymbol(c_M2p2, M2, sizeof(M2)));
+  TAM_CUDA(cudaMemcpyToSymbol(d_T3p2, T3, sizeof(T3)));
+  TAM_CUDA(cudaMemcpyToSymbol(d_M2p2, M2, sizeof(M2)));
   TAM_CUDA(cudaMemcpyToSymbol(c_T3p1, T3a, sizeof(T3a)));
   TAM_CUDA(cudaMemcpyToSymbol(c_M2p1, M2a, sizeof(M2a)));
   TAM_CUDA(cudaMemcpyToSymbol(c_F2p2, F2, sizeof(F2)));
   TAM_CUDA(cudaMemcpyToSymbol(c_F2p1, F1, sizeof(F1)));
-  TAM_CUDA(cudaMemcpyToSymbol(c_q27, q27, sizeof(q27)));
+  TAM_CUDA(cudaMemcpyToSymbol(d_qc, qc, sizeof(qc)));
   thermal_point_values();
   g_tab_ready[dev] = true;
 }
 
-// P2 basis values at the 27 conduction points (cell-independent)
-__constant__ double c_phi27[NQ2][10];
+// P2 basis values at the conduction points (cell-independent)
+__device__ double d_phic[NQ2][10];
 
 void thermal_point_values() {
   std::vector<double> p, w;
-  tet_rule(3, p, w);
+  keast11(p, w);
   double ph[NQ2][10];
   for (int q = 0; q < NQ2; ++q)
     for (int a = 0; a < 10; ++a) ph[q][a] = cell_phi(2, a, &p[4 * q]);
-  TAM_CUDA(cudaMemcpyToSymbol(c_phi27, ph, sizeof(ph)));
+  TAM_CUDA(cudaMemcpyToSymbol(d_phic, ph, sizeof(ph)));
 }
 
 // ---------------------------------------------------------------------------
@@ -297,7 +326,7 @@ __global__ void thermal_p1_kernel(ThArgs A) {
   }
 }
 
-// P2: a warp per cell.  The lanes first evaluate, at the 27 conduction points,
+// P2: a warp per cell.  The lanes first evaluate, at the 11 conduction points,
 // the basis gradients, grad T_theta and kappa(T_theta) (into shared memory),
 // then take the 100 Jacobian and 10 residual entries (3-4 each).
 constexpr int P2T_WARPS = 4;
@@ -330,7 +359,7 @@ __global__ void __launch_bounds__(P2T_WARPS * 32) thermal_p2_kernel(ThArgs A) {
   __syncwarp();
   if (lane < NQ2) {
     const int q = lane;
-    const double* l = c_q27[q];
+    const double* l = d_qc[q];
     double tq = 0.0, gt[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 10; ++a) {
       double gr[3];
@@ -343,7 +372,7 @@ __global__ void __launch_bounds__(P2T_WARPS * 32) thermal_p2_kernel(ThArgs A) {
         for (int d = 0; d < 3; ++d) gr[d] = 4.0 * (l[p1] * g[p0][d] + l[p0] * g[p1][d]);
       }
       const double ta = st[wid][0][a];
-      tq += ta * c_phi27[q][a];
+      tq += ta * __ldg(&d_phic[q][a]);
       for (int d = 0; d < 3; ++d) {
         sg[wid][q][a][d] = gr[d];
         gt[d] += ta * gr[d];
@@ -365,14 +394,14 @@ __global__ void __launch_bounds__(P2T_WARPS * 32) thermal_p2_kernel(ThArgs A) {
         const double* s = sq[wid][q];
         const double tgi = s[2] * gi[0] + s[3] * gi[1] + s[4] * gi[2];
         const double gg = gj[0] * gi[0] + gj[1] * gi[1] + gj[2] * gi[2];
-        acc += s[1] * c_phi27[q][j] * tgi + s[0] * gg;
+        acc += s[1] * __ldg(&d_phic[q][j]) * tgi + s[0] * gg;
       }
       acc *= th;
       if (!steady) {
-        double m = 0.0, cm = c0 * c_M2p2[j][i];
+        double m = 0.0, cm = c0 * __ldg(&d_M2p2[j][i]);
         for (int b = 0; b < 10; ++b) {
-          m += c1 * th * st[wid][1][b] * c_T3p2[j][b][i];
-          cm += c1 * st[wid][0][b] * c_T3p2[b][j][i];
+          m += c1 * th * st[wid][1][b] * __ldg(&d_T3p2[j][b][i]);
+          cm += c1 * st[wid][0][b] * __ldg(&d_T3p2[b][j][i]);
         }
         acc += rho * vol * (m + cm / A.dt);
       }
@@ -388,8 +417,8 @@ __global__ void __launch_bounds__(P2T_WARPS * 32) thermal_p2_kernel(ThArgs A) {
       if (!steady) {
         double m = 0.0;
         for (int b = 0; b < 10; ++b) {
-          double cb = c0 * c_M2p2[b][i];
-          for (int a = 0; a < 10; ++a) cb += c1 * st[wid][0][a] * c_T3p2[a][b][i];
+          double cb = c0 * __ldg(&d_M2p2[b][i]);
+          for (int a = 0; a < 10; ++a) cb += c1 * st[wid][0][a] * __ldg(&d_T3p2[a][b][i]);
           m += st[wid][1][b] * cb;
         }
         f += rho * vol * m;
