@@ -668,19 +668,22 @@ spgemm_numeric_rs_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
     for (int p = xs + p0; p < xe; p += pstep) {
       const int j = xci[p];
       int qs = yrp[j], qe = yrp[j + 1];
-      if (upper || wn < ce - cs) {  // restrict Y's row to the window's column range
-        int lo = qs, hi = qe;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (yci[mid] < clo) lo = mid + 1; else hi = mid;
+      if (upper || wn < ce - cs) {
+        // restrict Y's row to the window's column range: the warp reads the
+        // (short, sorted) row 32 columns at a time and ballots, one memory
+        // round trip per 32 entries instead of two dependent binary searches
+        int first = qe, last = qs - 1;
+        for (int b0 = qs; b0 < qe; b0 += 32) {
+          const int q = b0 + lane;
+          const int cq = q < qe ? yci[q] : 0x7fffffff;
+          const unsigned ge = __ballot_sync(0xffffffffu, q < qe && cq >= clo);
+          const unsigned le = __ballot_sync(0xffffffffu, q < qe && cq <= chi);
+          if (first == qe && ge) first = b0 + __ffs(ge) - 1;
+          if (le) last = b0 + 31 - __clz(le);
+          if (le != 0xffffffffu) break;  // the columns <= chi form a prefix
         }
-        qs = lo;
-        hi = qe;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (yci[mid] <= chi) lo = mid + 1; else hi = mid;
-        }
-        qe = lo;
+        qs = first;
+        qe = last + 1 > first ? last + 1 : first;
       }
       const V* __restrict__ xb = xv + (size_t)p * M * K;
       // G groups of M lanes: group g takes Y entry qs + q0 + g, lane r of the
