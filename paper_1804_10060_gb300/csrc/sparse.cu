@@ -562,9 +562,19 @@ spgemm_numeric_os_kernel(const int* __restrict__ xrp, const int* __restrict__ xc
     const int j = xci[p];
     int lo = yrp[j], hi = yrp[j + 1];
     const int end = hi;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (yci[mid] < c) lo = mid + 1; else hi = mid;
+    if (hi - lo <= 8) {
+      // short Y rows (prolongators): all candidates loaded at once, one
+      // memory round trip instead of a chain of dependent probes
+      int f = end;
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (lo + t < end && yci[lo + t] == c) f = lo + t;
+      lo = f;
+    } else {
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (yci[mid] < c) lo = mid + 1; else hi = mid;
+      }
     }
     if (lo < end && yci[lo] == c) {
       const V* __restrict__ xb = xv + (size_t)p * M * K;
