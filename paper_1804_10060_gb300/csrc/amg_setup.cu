@@ -298,16 +298,23 @@ __global__ void mis_init_kernel(const unsigned char* __restrict__ isolated, int 
 
 // A round whose predecessor left no node undecided (prev_und, null for the
 // first round) does nothing, so the host can launch several rounds per check.
+// tup[i] = mis_tuple(state[i], level, i), kept current by mis_round2_kernel
+// (so the rounds read each neighbour's tuple instead of rehashing its id)
+__global__ void mis_tuple_init_kernel(const unsigned char* __restrict__ state, int n, int level,
+                                      unsigned long long* __restrict__ tup) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) tup[i] = mis_tuple(state[i], level, i);
+}
+
 __global__ void mis_round1_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
-                                  const unsigned char* __restrict__ state, int n, int level, unsigned long long* __restrict__ m1,
+                                  const unsigned long long* __restrict__ tup, int n, unsigned long long* __restrict__ m1,
                                   const int* __restrict__ prev_und) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || (prev_und && *prev_und == 0)) return;
-  unsigned long long m = mis_tuple(state[i], level, i);
+  unsigned long long m = tup[i];
   for (int p = rp[i]; p < rp[i + 1]; ++p)
     if (strong[p]) {
-      int j = ci[p];
-      unsigned long long t = mis_tuple(state[j], level, j);
+      const unsigned long long t = tup[ci[p]];
       m = t > m ? t : m;
     }
   m1[i] = m;
@@ -316,7 +323,7 @@ __global__ void mis_round1_kernel(const int* __restrict__ rp, const int* __restr
 __global__ void mis_round2_kernel(const int* __restrict__ rp, const int* __restrict__ ci, const unsigned char* __restrict__ strong,
                                   unsigned char* __restrict__ state, const unsigned long long* __restrict__ m1, int n,
                                   int level, int distance, const int* __restrict__ prev_und,
-                                  int* __restrict__ undecided) {
+                                  int* __restrict__ undecided, unsigned long long* __restrict__ tup) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || (prev_und && *prev_und == 0)) return;
   if (state[i] != ST_UND) return;
@@ -327,10 +334,16 @@ __global__ void mis_round2_kernel(const int* __restrict__ rp, const int* __restr
         unsigned long long t = m1[ci[p]];
         m = t > m ? t : m;
       }
-  const unsigned long long mine = mis_tuple(ST_UND, level, i);
-  if (m == mine) state[i] = ST_ROOT;
-  else if ((m >> 62) == 2ull) state[i] = ST_OUT;
-  else atomicAdd(undecided, 1);
+  const unsigned long long mine = tup[i];  // mis_tuple(ST_UND, level, i)
+  if (m == mine) {
+    state[i] = ST_ROOT;
+    tup[i] = mis_tuple(ST_ROOT, level, i);
+  } else if ((m >> 62) == 2ull) {
+    state[i] = ST_OUT;
+    tup[i] = 0ull;
+  } else {
+    atomicAdd(undecided, 1);
+  }
 }
 
 __global__ void root_flag_kernel(const unsigned char* __restrict__ state, const unsigned char* __restrict__ isolated, int n,
@@ -780,7 +793,9 @@ static int aggregate(Level& L, int level, double theta, int distance, cudaStream
   TAM_LAUNCH_CHECK();
   mis_init_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(isolated.p, n, state.p);
   TAM_LAUNCH_CHECK();
-  DBuf<unsigned long long> m1(n, s);
+  DBuf<unsigned long long> m1(n, s), tup(n, s);
+  mis_tuple_init_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(state.p, n, level, tup.p);
+  TAM_LAUNCH_CHECK();
   // und[it]: nodes still undecided after round it; rounds launched 8 at a
   // time between host checks (a round after one that left none is a no-op)
   constexpr int kMaxRounds = 1024, kBatch = 8;
@@ -788,11 +803,10 @@ static int aggregate(Level& L, int level, double theta, int distance, cudaStream
   und.zero();
   for (int it = 0;; ++it) {
     const int* prev = it > 0 ? und.p + it - 1 : nullptr;
-    mis_round1_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, n, level, m1.p,
-                                                       prev);
+    mis_round1_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, tup.p, n, m1.p, prev);
     TAM_LAUNCH_CHECK();
     mis_round2_kernel<<<grid_for(n, TPB), TPB, 0, s>>>(A.row_ptr.p, A.col_idx.p, strong.p, state.p, m1.p, n, level,
-                                                       distance, prev, und.p + it);
+                                                       distance, prev, und.p + it, tup.p);
     TAM_LAUNCH_CHECK();
     if ((it + 1) % kBatch == 0 || it + 1 == kMaxRounds) {
       if (read_back_int(und.p + it, s) == 0) break;
