@@ -1052,12 +1052,16 @@ aptent_numeric_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, 
   using A = typename Ar::A;
   constexpr int MN = M * N;
   __shared__ int pos[AT_WARPS][AT_CAP];
+  __shared__ int ord[AT_WARPS][AT_CAP];
+  __shared__ int qst[AT_WARPS][AT_CAP + 1];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * AT_WARPS + wid;
   if (row >= n_rows) return;  // warp-uniform
   const int p0 = xrp[row], len = xrp[row + 1] - p0;
   const int c0 = crp[row], nc = crp[row + 1] - c0;
   int* ps = pos[wid];
+  int* od = ord[wid];
+  int* qs = qst[wid];
   // the output position of each entry's aggregate (-1: an unaggregated column)
   for (int i = lane; i < len; i += 32) {
     const int a = agg[xci[p0 + i]];
@@ -1073,11 +1077,27 @@ aptent_numeric_kernel(const int* __restrict__ xrp, const int* __restrict__ xci, 
     ps[i] = q;
   }
   __syncwarp();
+  // the entries grouped by output position, each group in row order: qs[q] =
+  // entries with a smaller position, then each entry's rank in its group
+  for (int q = lane; q <= nc; q += 32) {
+    int c = 0;
+    for (int i = 0; i < len; ++i) c += (ps[i] >= 0 && ps[i] < q) ? 1 : 0;
+    qs[q] = c;
+  }
+  __syncwarp();
+  for (int i = lane; i < len; i += 32) {
+    const int q = ps[i];
+    if (q < 0) continue;
+    int rank = 0;
+    for (int j = 0; j < i; ++j) rank += ps[j] == q ? 1 : 0;
+    od[qs[q] + rank] = i;
+  }
+  __syncwarp();
   for (int it = lane; it < nc * MN; it += 32) {
     const int q = it / MN, e = it - q * MN, r = e / N, s2 = e - r * N;
     A acc = Ar::zero();
-    for (int i = 0; i < len; ++i) {
-      if (ps[i] != q) continue;
+    for (int t = qs[q]; t < qs[q + 1]; ++t) {
+      const int i = od[t];
       const V* __restrict__ xb = xv + (size_t)(p0 + i) * M * K + r * K;
       const V* __restrict__ yb = ptv + (size_t)ptrp[xci[p0 + i]] * K * N + s2;
 #pragma unroll
