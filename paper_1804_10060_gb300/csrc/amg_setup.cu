@@ -509,10 +509,12 @@ ptent_qr_kernel(const int* __restrict__ ap, const int* __restrict__ mem, int n_a
 // P = (I - omega D^-1 A) P_tent, in place on the values of A*P_tent
 // One warp per row: a row's blocks are contiguous, so the lanes stride its
 // bs * k values (coalesced) instead of one thread walking them.
+template <int BS, int KD>
 __global__ void smooth_prolongator_kernel(const int* __restrict__ rp, const int* __restrict__ ci, double* __restrict__ v,
-                                          int n, int bs, int k, const double* __restrict__ dinv,
+                                          int n, const double* __restrict__ dinv,
                                           const double* __restrict__ consts, const int* __restrict__ agg,
                                           const int* __restrict__ ptrp, const double* __restrict__ ptv) {
+  constexpr int bs = BS, k = KD;  // constants: the index divisions below become multiplications
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= n) return;
   const double omega = consts[1];
@@ -1083,10 +1085,19 @@ tam_amg_s* amg_build(tam_matrix_s* K, const double* coords, const amg_params& pr
       T.mark(0, s);  // waiting for lambda_max counts as its phase
       side.join(s);
       T.mark(3, s);
-      smooth_prolongator_kernel<<<grid_for((long long)L.n_rows * 32, TPB), TPB, 0, s>>>(
-          L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p, L.n_rows, L.bs, k, L.dinv.p, L.consts.p, L.agg.p, L.Pt.row_ptr.p,
-          L.Pt.vals.p);
-      TAM_LAUNCH_CHECK();
+      {
+        const unsigned g = grid_for((long long)L.n_rows * 32, TPB);
+        auto launch = [&](auto kern) {
+          kern<<<g, TPB, 0, s>>>(L.P.row_ptr.p, L.P.col_idx.p, L.P.vals.p, L.n_rows, L.dinv.p, L.consts.p, L.agg.p,
+                                 L.Pt.row_ptr.p, L.Pt.vals.p);
+        };
+        if (L.bs == 3 && k == 6) launch(smooth_prolongator_kernel<3, 6>);
+        else if (L.bs == 6 && k == 6) launch(smooth_prolongator_kernel<6, 6>);
+        else if (L.bs == 1 && k == 1) launch(smooth_prolongator_kernel<1, 1>);
+        else if (L.bs == 3 && k == 3) launch(smooth_prolongator_kernel<3, 3>);
+        else throw Error(TAM_ERR_UNSUPPORTED, "amg_setup: prolongator block shape not instantiated");
+        TAM_LAUNCH_CHECK();
+      }
       T.mark(4, s);
       bsr_transpose(L.P, L.R, s);
       {

@@ -282,15 +282,18 @@ __global__ void transpose_rank_kernel(const int* __restrict__ rt_ptr, int n_rt, 
   }
 }
 
-__global__ void transpose_vals_kernel(const double* __restrict__ vals, const int* __restrict__ src,
-                                      long long nnzb, int br, int bc, double* __restrict__ out) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long bb = (long long)br * bc;
-  if (t >= nnzb * bb) return;
-  long long b = t / bb;
-  int e = (int)(t % bb);
-  int r = e / br, c = e % br;  // output block is bc x br: element (r, c) = input (c, r)
-  out[t] = vals[(size_t)src[b] * bb + (size_t)c * bc + r];
+// the block shape as template parameters: the index arithmetic divides by
+// constants (a 64-bit division by a runtime value costs ~100 instructions)
+template <int BR, int BC>
+__global__ void transpose_vals_kernel(const double* __restrict__ vals, const int* __restrict__ src, long long nnzb,
+                                      double* __restrict__ out) {
+  constexpr int BB = BR * BC;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzb * BB) return;
+  const long long b = t / BB;
+  const int e = (int)(t - b * BB);
+  const int r = e / BR, c = e - r * BR;  // output block is BC x BR: element (r, c) = input (c, r)
+  out[t] = vals[(size_t)src[b] * BB + (size_t)c * BC + r];
 }
 
 }  // namespace
@@ -316,8 +319,13 @@ void bsr_transpose(const Bsr& A, Bsr& R, cudaStream_t s) {
                                                                                 tsrc.p, R.col_idx.p, src.p);
   TAM_LAUNCH_CHECK();
   R.vals = DBuf<double>((size_t)A.nnzb * A.block_elems(), s);
-  transpose_vals_kernel<<<grid_for(A.nnzb * (long long)A.block_elems(), 256), 256, 0, s>>>(
-      A.vals.p, src.p, A.nnzb, A.br, A.bc, R.vals.p);
+  const unsigned g = grid_for(A.nnzb * (long long)A.block_elems(), 256);
+  if (A.br == 3 && A.bc == 6) transpose_vals_kernel<3, 6><<<g, 256, 0, s>>>(A.vals.p, src.p, A.nnzb, R.vals.p);
+  else if (A.br == 6 && A.bc == 6) transpose_vals_kernel<6, 6><<<g, 256, 0, s>>>(A.vals.p, src.p, A.nnzb, R.vals.p);
+  else if (A.br == 1 && A.bc == 1) transpose_vals_kernel<1, 1><<<g, 256, 0, s>>>(A.vals.p, src.p, A.nnzb, R.vals.p);
+  else if (A.br == 3 && A.bc == 3) transpose_vals_kernel<3, 3><<<g, 256, 0, s>>>(A.vals.p, src.p, A.nnzb, R.vals.p);
+  else if (A.br == 6 && A.bc == 3) transpose_vals_kernel<6, 3><<<g, 256, 0, s>>>(A.vals.p, src.p, A.nnzb, R.vals.p);
+  else throw Error(TAM_ERR_UNSUPPORTED, "transpose: block shape not instantiated");
   TAM_LAUNCH_CHECK();
 }
 
