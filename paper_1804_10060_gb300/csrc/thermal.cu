@@ -328,13 +328,19 @@ __global__ void thermal_p1_kernel(ThArgs A) {
 
 // P2: a warp per cell.  The lanes first evaluate, at the 11 conduction points,
 // the basis gradients, grad T_theta and kappa(T_theta) (into shared memory),
-// then take the 100 Jacobian and 10 residual entries (3-4 each).
+// then grad T_theta . grad phi_i per point, the symmetric conduction sums
+// once per pair i <= j, and finally the 100 Jacobian and 10 residual entries
+// (FP64 is GB300's slow pipe: the symmetric part and the mass sums are not
+// recomputed per entry).
 constexpr int P2T_WARPS = 4;
 
 __global__ void __launch_bounds__(P2T_WARPS * 32) thermal_p2_kernel(ThArgs A) {
   __shared__ double sg[P2T_WARPS][NQ2][10][3];
   __shared__ double sq[P2T_WARPS][NQ2][5];   // kappa w vol, k1 w vol, grad T_theta
   __shared__ double st[P2T_WARPS][2][10];    // T_theta, (T - T_old)/dt
+  __shared__ double stg[P2T_WARPS][NQ2][10]; // grad T_theta . grad phi_i per point
+  __shared__ double ssym[P2T_WARPS][55];     // symmetric conduction part, pairs i <= j
+  __shared__ double sw[P2T_WARPS][10];       // mass weights
   __shared__ int sv[P2T_WARPS][10];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * P2T_WARPS + wid;
@@ -384,42 +390,57 @@ __global__ void __launch_bounds__(P2T_WARPS * 32) thermal_p2_kernel(ThArgs A) {
     for (int d = 0; d < 3; ++d) sq[wid][q][2 + d] = gt[d];
   }
   __syncwarp();
+  // per point and basis function: tg[q][i] = grad T_theta . grad phi_i
+  for (int e = lane; e < NQ2 * 10; e += 32) {
+    const int q = e / 10, i = e - q * 10;
+    const double* gi = sg[wid][q][i];
+    const double* sp = sq[wid][q];
+    stg[wid][q][i] = sp[2] * gi[0] + sp[3] * gi[1] + sp[4] * gi[2];
+  }
+  // mass weights: (T3 is symmetric in its three indices) the mass part of
+  // J_ij is rho vol (c0 M_ij / dt + sum_b T3_ijb w_b), w_b = c1 (theta dT_b/dt + T_theta,b / dt)
+  if (!steady && lane < 10) sw[wid][lane] = c1 * (th * st[wid][1][lane] + st[wid][0][lane] / A.dt);
+  __syncwarp();
+  // the symmetric conduction part, sum_q kappa w vol grad phi_i . grad phi_j, once per pair i <= j
+  for (int e = lane; e < 55; e += 32) {
+    int i = 0, r = e;
+    while (r >= 10 - i) {
+      r -= 10 - i;
+      ++i;
+    }
+    const int j = i + r;
+    double acc = 0.0;
+    for (int q = 0; q < NQ2; ++q) {
+      const double* gi = sg[wid][q][i];
+      const double* gj = sg[wid][q][j];
+      acc += sq[wid][q][0] * (gj[0] * gi[0] + gj[1] * gi[1] + gj[2] * gi[2]);
+    }
+    ssym[wid][e] = acc;
+  }
+  __syncwarp();
   for (int e = lane; e < 110; e += 32) {
     if (e < 100) {
       const int i = e / 10, j = e % 10;
-      double acc = 0.0;
-      for (int q = 0; q < NQ2; ++q) {
-        const double* gi = sg[wid][q][i];
-        const double* gj = sg[wid][q][j];
-        const double* s = sq[wid][q];
-        const double tgi = s[2] * gi[0] + s[3] * gi[1] + s[4] * gi[2];
-        const double gg = gj[0] * gi[0] + gj[1] * gi[1] + gj[2] * gi[2];
-        acc += s[1] * __ldg(&d_phic[q][j]) * tgi + s[0] * gg;
-      }
+      const int lo = i < j ? i : j, hi = i < j ? j : i;
+      double acc = ssym[wid][lo * 10 - lo * (lo - 1) / 2 + (hi - lo)];
+      for (int q = 0; q < NQ2; ++q) acc += sq[wid][q][1] * __ldg(&d_phic[q][j]) * stg[wid][q][i];
       acc *= th;
       if (!steady) {
-        double m = 0.0, cm = c0 * __ldg(&d_M2p2[j][i]);
-        for (int b = 0; b < 10; ++b) {
-          m += c1 * th * st[wid][1][b] * __ldg(&d_T3p2[j][b][i]);
-          cm += c1 * st[wid][0][b] * __ldg(&d_T3p2[b][j][i]);
-        }
-        acc += rho * vol * (m + cm / A.dt);
+        double m = c0 * __ldg(&d_M2p2[i][j]) / A.dt;
+        for (int b2 = 0; b2 < 10; ++b2) m += sw[wid][b2] * __ldg(&d_T3p2[i][j][b2]);
+        acc += rho * vol * m;
       }
       scatter_J(A, sv[wid][i], sv[wid][j], acc);
     } else {
       const int i = e - 100;
       double f = 0.0;
-      for (int q = 0; q < NQ2; ++q) {
-        const double* gi = sg[wid][q][i];
-        const double* s = sq[wid][q];
-        f += s[0] * (s[2] * gi[0] + s[3] * gi[1] + s[4] * gi[2]);
-      }
+      for (int q = 0; q < NQ2; ++q) f += sq[wid][q][0] * stg[wid][q][i];
       if (!steady) {
         double m = 0.0;
-        for (int b = 0; b < 10; ++b) {
-          double cb = c0 * __ldg(&d_M2p2[b][i]);
-          for (int a = 0; a < 10; ++a) cb += c1 * st[wid][0][a] * __ldg(&d_T3p2[a][b][i]);
-          m += st[wid][1][b] * cb;
+        for (int b2 = 0; b2 < 10; ++b2) {
+          double cb = c0 * __ldg(&d_M2p2[b2][i]);
+          for (int a2 = 0; a2 < 10; ++a2) cb += c1 * st[wid][0][a2] * __ldg(&d_T3p2[a2][b2][i]);
+          m += st[wid][1][b2] * cb;
         }
         f += rho * vol * m;
       }
