@@ -693,11 +693,22 @@ blockrow_spmv_kernel(BsrView A, const double* __restrict__ x, Epi epi) {
     if constexpr (DF) ad1 = make_float2(0.f, 0.f);
     else ad1 = 0.0;
     const int p1 = A.rp[row + 1];
+    // x entry one step ahead: the next step's column and x are requested
+    // before this step's products
+    double xn = 0.0;
+    {
+      const int pf = A.rp[row] + wr * G + g;
+      if (act && pf < p1 && r < BC) xn = __ldg(x + (size_t)__ldg(A.ci + pf) * BC + r);
+    }
     for (int base = A.rp[row] + wr * G; base < p1; base += WPR * G) {
       const int p = base + g;
       const bool has = act && p < p1;
-      double xr = 0.0;
-      if (has && r < BC) xr = __ldg(x + (size_t)__ldg(A.ci + p) * BC + r);
+      const double xr = xn;
+      {
+        const int pf = p + WPR * G;
+        xn = 0.0;
+        if (act && pf < p1 && r < BC) xn = __ldg(x + (size_t)__ldg(A.ci + pf) * BC + r);
+      }
       if constexpr (DF) {
         float2 v[BC];
         if (has) block_load<BC>(A.v_df + (size_t)p * BB + r * BC, v);
